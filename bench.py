@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Throughput of the FFT Lippmann-Schwinger iteration on GB300 (voxel-iterations/s).
+
+Workload (default): 512^3 periodised Boolean model of spheres (radius 8 voxels,
+inclusion fraction 0.25, seed 1), matrix E = 1, nu = 0.3, inclusions E = 1000,
+nu = 0.2, rotated-grid Green operator G^R with the accelerated scheme, FP32
+bulk with FP64 reductions and FP64 refinement, stop at eta <= 1e-6.  One step
+is one load case solved to tolerance; steps cycle through the six Mandel unit
+loads of the full effective stiffness.  Inputs (3.2 GB of fields) are larger
+than L2, so no flush is inserted between steps.
+
+value    : total voxel-iterations of the timed steps / their device time
+e2e      : the same metric through the public API with the phase image copied
+           from pinned host memory and the result read back every step
+roofline : the dominant kernel's algorithmic bytes per launch / its mean launch
+           time (CUDA events on the solver stream) against the measured HBM peak
+cpu_baseline: the FP64 CPU oracle on a bounded sample of the workload
+
+--impl reference times the oracle itself (the reference arm of this repository).
+Multi-GPU (torchrun): every rank solves its own load cases (replicas, no
+collective on the data path); value = all ranks' voxel-iterations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iters/s at 512^3 (AS, G^R, FP32 bulk + FP64 refinement, eta <= 1e-6)"
+UNIT = "voxel-iter/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="grid size per axis (512 = the workload)")
+    ap.add_argument("--max-iter", type=int, default=3000)
+    ap.add_argument("--precision", default="fp32_refine64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=128)
+    ap.add_argument("--cpu-iters", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload(n):
+    """Synthetic microstructure and phases of the benchmark (radius scales with n / 512)."""
+    import numpy as np
+    from paper_1412_8398_gb300 import microstructure as MS
+    radius = 8.0 * n / 512.0
+    ph, info = MS.boolean_spheres((n, n, n), radius, 0.25, seed=1)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (1000.0, 0.2)])
+    return ph, lam, mu, info
+
+
+def mandel_load(J):
+    import numpy as np
+    e = np.zeros(6)
+    e[J] = 1.0 if J < 3 else 1.0 / math.sqrt(2.0)
+    return e
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, local, world
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce(vals, op, world):
+    if world == 1:
+        return vals
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return t.cpu().tolist()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# Algorithmic bytes per launch of each kernel (FP32 bulk; FP64 doubles the
+# scalar size).  The model counts every field read and written once by the pass:
+# fwd_x reads eps (n_c scalars) + phase (1 B) per voxel and writes 2 n_c half-spectrum
+# components (tau and sigma); mid_y_fwd reads and writes 2 n_c components;
+# fourier_z reads and writes the n_c tau components and reads the n_c sigma
+# components; mid_y_inv reads and writes n_c components; inv_x reads n_c
+# components, eps and phase and writes eps.
+def kernel_bytes(kind, n, nc=6):
+    prec = 8 if kind.endswith("f64") else 4
+    cplx = 2 * prec
+    N = n ** 3
+    half = n * n * (n // 2 + 1)
+    k = kind.rsplit("_", 1)[0]
+    if k == "fwd_x":
+        return N * (nc * prec + 1) + 2 * nc * half * cplx
+    if k == "mid_y_fwd":
+        return 2 * (2 * nc) * half * cplx
+    if k == "fourier_z":
+        return (2 * nc + nc) * half * cplx
+    if k == "mid_y_inv":
+        return 2 * nc * half * cplx
+    if k == "inv_x":
+        return nc * half * cplx + N * (2 * nc * prec + 1)
+    return None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1412_8398_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kind, n):
+    """dram bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = source_hash()
+    for line in open(path):
+        f = line.split()
+        if len(f) == 5 and f[0] == "traffic" and f[1] == kind and int(f[2]) == n and f[4] == src:
+            return float(f[3])
+    return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(n, iters):
+    """The oracle (as it stands) on a bounded sample, in a single-threaded subprocess."""
+    code = f"""
+import sys, time, json, numpy as np
+sys.path.insert(0, {ROOT!r})
+from oracle import fftls_oracle as O
+import bench
+ph, lam, mu, info = bench.workload({n})
+eb = O.from_mandel(np.eye(6)[0], 3)
+O.solve(ph, lam, mu, eb, O.ROTATED, O.ACCELERATED, tol=0.0, max_iter=1)
+t = time.perf_counter()
+O.solve(ph, lam, mu, eb, O.ROTATED, O.ACCELERATED, tol=0.0, max_iter={iters})
+dt = time.perf_counter() - t
+print(json.dumps({{"seconds": dt, "voxels": int(ph.size), "iters": {iters}}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if p.returncode != 0:
+        return {"error": p.stderr[-500:]}
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    return {"value": r["voxels"] * r["iters"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{r['iters']} AS/G^R iterations of the FP64 numpy oracle on the same recipe at {n}^3 "
+                      f"(radius scaled to {8.0 * n / 512:g}), single thread, {r['seconds']:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import fftls_oracle as O
+    n = args.cpu_n
+    ph, lam, mu, info = workload(n)
+    times, iters = [], 0
+    for i in range(args.warmup + args.steps):
+        eb = O.from_mandel(mandel_load(i % 6), 3)
+        t = time.perf_counter()
+        r = O.solve(ph, lam, mu, eb, O.ROTATED, O.ACCELERATED, tol=0.0, max_iter=1)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+            iters += r["iterations"]
+    total = sum(times)
+    value = ph.size * iters / total
+    cores = 1
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"boolean_spheres_{n}^3_sample_of_512^3_recipe", "green": "R", "scheme": "AS"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one oracle iteration per step on the {n}^3 sample of the recipe"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank, local, world = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    from paper_1412_8398_gb300 import build, fftls
+
+    build.build()
+    torch.cuda.set_device(local)
+    n = args.n
+    ph, lam, mu, info = workload(n)
+    N = ph.size
+    dph = torch.from_numpy(ph).cuda()
+    solver = fftls.Solver(local)
+    stream = torch.cuda.Stream(device=local)
+    kw = dict(green="R", scheme="AS", tol=1e-6, max_iter=args.max_iter, precision=args.precision,
+              want_strain=False, want_stress=False, history=False, device_outputs=True, stream=stream)
+
+    def step(i, **extra):
+        J = (rank + i * world) % 6
+        opts = dict(kw)
+        opts.update(extra)
+        r = solver.solve(dph, lam, mu, mandel_load(J), **opts)
+        if r.status not in (fftls.OK,):
+            raise RuntimeError(f"solve failed: {r.message}")
+        return r
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = ClockSampler(local)
+    clk.start()
+    k0, _ = solver.counters()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    iters = its32 = 0
+    for i in range(args.steps):
+        r = step(args.warmup + i)
+        iters += r.iterations
+        its32 += r.iterations_fp32
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    k1, _ = solver.counters()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = allreduce([ms], _max_op(world), world)[0]
+    vox_total = allreduce([float(N) * iters], _sum_op(world), world)[0]
+    value = vox_total / (ms_max / 1e3)
+
+    # roofline: the same steps again with per-kernel CUDA events
+    prof = {}
+    for i in range(min(args.steps, 2)):
+        step(args.warmup + i, profile=True, use_graphs=False)
+        for kname, (kms, cnt) in solver.profile().items():
+            a, b = prof.get(kname, (0.0, 0))
+            prof[kname] = (a + kms, b + cnt)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dname, (dms, dcnt) = dom
+    peak, peak_kind = peaks()
+    algo = kernel_bytes(dname, n)
+    achieved = algo / (dms / dcnt / 1e3) / 1e9 if algo else None
+    roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": measured_traffic(dname, n),
+                "bytes_per_launch": algo, "launch_ms": dms / dcnt, "peak_source": f"hbm_gbs ({peak_kind})",
+                "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                                "gbs": (kernel_bytes(k, n) / (v[0] / v[1] / 1e3) / 1e9) if kernel_bytes(k, n) else None}
+                            for k, v in sorted(prof.items())}}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(ph.shape, dtype=torch.uint8, pin_memory=True)
+        pinned.numpy()[...] = ph
+        hph = pinned.numpy()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        e_iters = 0
+        for i in range(args.steps):
+            J = (rank + i * world) % 6
+            r = solver.solve(hph, lam, mu, mandel_load(J), green="R", scheme="AS", tol=1e-6,
+                             max_iter=args.max_iter, precision=args.precision, want_strain=False,
+                             want_stress=False, history=False, device_outputs=False)
+            e_iters += r.iterations
+        dt = time.perf_counter() - t
+        dt_max = allreduce([dt], _max_op(world), world)[0]
+        e_tot = allreduce([float(N) * e_iters], _sum_op(world), world)[0]
+        e2e = {"value": e_tot / dt_max, "unit": UNIT, "h2d_bytes_per_step": int(N),
+               "d2h_bytes_per_step": 2 * 6 * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_n, args.cpu_iters)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32_refine64" else args.precision,
+            "data": "synthetic",
+            "config": {"workload": f"boolean_spheres_{n}^3_R{8.0 * n / 512:g}_f0.25_chi1000_AS_R_{args.precision}_eta1e-6",
+                       "grid": [n, n, n], "realised_fraction": info["fraction"], "load_cases": "Mandel unit loads, cycled",
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "single GPU"},
+            "iterations_per_step": iters / args.steps, "fp32_iterations_per_step": its32 / args.steps,
+            "time_to_tol_s": ms_max / 1e3 / args.steps,
+            "gpu_launches": k1 - k0,
+            "clocks": clocks,
+            "roofline": roofline,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    solver.close()
+
+
+def _max_op(world):
+    if world == 1:
+        return None
+    import torch.distributed as dist
+    return dist.ReduceOp.MAX
+
+
+def _sum_op(world):
+    if world == 1:
+        return None
+    import torch.distributed as dist
+    return dist.ReduceOp.SUM
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * fftls.h - C ABI of the GB300 (sm_103a) FFT Lippmann-Schwinger solver for
+ * periodic 2D/3D voxel composites in linear elasticity, after
+ * F. Willot, "Fourier-based schemes for computing the mechanical response of
+ * composites with accurate local fields" (arXiv:1412.8398).
+ *
+ * Problem (Sec. 2, eq. a1-a2): on a periodic grid of n1 x n2 x n3 voxels
+ * (n3 = 1 in 2D), each voxel holds a phase id; each phase is isotropic with
+ * Lame coefficients (lambda, mu), C = lambda dd + mu (dd + dd).  Given the
+ * macroscopic strain eps_bar, find the strain eps(x) with <eps> = eps_bar,
+ * discrete compatibility and equilibrium (Sec. 4, eq. discFour) under one of
+ * four discrete Green operators:
+ *   FFTLS_GREEN_MS : G of Moulinec and Suquet, k = i q (eq. green0b) with the
+ *                    even-L rule G = C0^{-1} at q_i = pi (eq. hfreq);
+ *   FFTLS_GREEN_C  : centered differences, k_i = i sin q_i (eq. mul2, mulfix);
+ *   FFTLS_GREEN_W  : forward/backward differences, k_i = e^{iq_i} - 1 (eq. wil072);
+ *   FFTLS_GREEN_R  : the paper's rotated scheme, k^R of eq. wil14 (2D) /
+ *                    wil14b (3D), G^R = 0 where k^R = 0 (eq. mysymgr).
+ * Schemes: FFTLS_DIRECT (eq. ds) and FFTLS_ACCELERATED (eq. as), iterated
+ * until the equilibrium norm eta of eq. criterion is <= tol.
+ *
+ * Conventions
+ *  - Fields are structure-of-arrays, component-major: component c of voxel
+ *    v = x1 + n1 (x2 + n2 x3) is at [c * N + v], N = n1 n2 n3.  Components
+ *    are tensor components (not engineering shear) in the order
+ *    11, 22, 33, 23, 13, 12 (3D) or 11, 22, 12 (2D): n_c = 6 or 3.
+ *  - eta = sqrt(sum_q |k*(q) . sigma_hat(q)|^2) / (N ||<sigma>||_F), with the
+ *    unnormalised DFT of eq. ft2, ||.||_F counting off-diagonal entries twice,
+ *    0/0 = 0.  Under FFTLS_ACCELERATED the eta test also requires
+ *    |<eps> - eps_bar|_F <= tol |eps_bar|_F (accelerated iterates need not
+ *    have the prescribed mean).
+ *  - `iterations` counts evaluations of eta, i.e. stresses sigma^k computed.
+ *    A homogeneous medium returns 1.
+ *  - All buffers are owned by the caller.  The context owns its device
+ *    workspaces and reuses them across calls.  Calls on one context must not
+ *    overlap; each call is synchronous with respect to the host.
+ *  - No C++ exception crosses the ABI.  On error the call returns a status
+ *    and fftls_last_error() holds a message for that context.
+ */
+#ifndef FFTLS_H
+#define FFTLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fftls_ctx fftls_ctx;
+
+typedef enum {
+  FFTLS_OK = 0,
+  FFTLS_E_INVALID_ARG = 1,      /* bad dimension, size, moduli, enum or pointer */
+  FFTLS_E_UNSUPPORTED_SIZE = 2, /* a grid length with a prime factor other than 2, 3, 5, or > 1024 */
+  FFTLS_E_OOM = 3,              /* device allocation failed */
+  FFTLS_E_CUDA = 4,             /* a CUDA runtime call failed (message in fftls_last_error) */
+  FFTLS_E_NOT_CONVERGED = 5,    /* max_iter reached; outputs hold the last iterate */
+  FFTLS_E_DIVERGED = 6          /* eta non-finite or > 1e4 eta_0; outputs hold the last iterate */
+} fftls_status;
+
+enum { FFTLS_GREEN_MS = 0, FFTLS_GREEN_C = 1, FFTLS_GREEN_W = 2, FFTLS_GREEN_R = 3 };
+enum { FFTLS_DIRECT = 0, FFTLS_ACCELERATED = 1 };
+/* FP64: every pass in double.  FP32_REFINE64: FFT passes, G' and the
+ * constitutive update in float with FP64 reductions until eta <= refine_switch
+ * (or eta stalls), then double until eta <= tol.  FP32: float only. */
+enum { FFTLS_FP64 = 0, FFTLS_FP32_REFINE64 = 1, FFTLS_FP32 = 2 };
+/* ETA: eq. criterion.  MAXDELTA: max over voxels and components of
+ * |eps^{k+1} - eps^k| and |sigma^{k+1} - sigma^k| below tol (Sec. 5.1, 5.3);
+ * the field returned is eps^{k+1} and `iterations` = k + 1. */
+enum { FFTLS_STOP_ETA = 0, FFTLS_STOP_MAXDELTA = 1 };
+
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int n[3];                 /* n1 (x1, fastest), n2, n3; n3 = 1 when dim == 2; each in 1..1024, factors 2,3,5 */
+  const uint8_t* phase;     /* N phase ids in 0..n_phases-1, x1 fastest */
+  int phase_on_device;      /* 1: `phase` is a device pointer on the context's device */
+  int n_phases;             /* 1..256 */
+  const double* lambda;     /* host, [n_phases]; 2D uses these (plane strain) values directly */
+  const double* mu;         /* host, [n_phases]; mu >= 0, lambda + (2/d) mu >= 0 */
+  double lambda0, mu0;      /* reference medium; NaN selects the default (fftls_reference_medium) */
+  int green;                /* FFTLS_GREEN_* */
+  int scheme;               /* FFTLS_DIRECT or FFTLS_ACCELERATED */
+  double eps_bar[6];        /* macroscopic strain, tensor components in field order */
+} fftls_problem;
+
+typedef struct {
+  double tol;               /* eta (or max-delta) tolerance, >= 0 */
+  int stop;                 /* FFTLS_STOP_* */
+  int max_iter;             /* >= 1; caps `iterations` over all precision phases */
+  int precision;            /* FFTLS_FP64, FFTLS_FP32_REFINE64, FFTLS_FP32 */
+  double refine_switch;     /* FP32_REFINE64: eta at which float hands over to double; <= 0 means tol */
+  const double* eps_init;   /* optional initial strain (n_c x N, FP64); NULL starts from eps_bar */
+  int eps_init_on_device;   /* 1: eps_init is a device pointer */
+  int fields_on_device;     /* 1: result->strain / stress are device pointers */
+  void* stream;             /* cudaStream_t to run on; NULL uses the context's own stream */
+  int use_graphs;           /* 1 (default): capture chunks of iterations as CUDA graphs */
+  int profile;              /* 1: time every kernel with CUDA events (no graphs); see fftls_profile */
+} fftls_options;
+
+typedef struct {
+  double* strain;               /* optional out, n_c x N FP64 (host or device, see fields_on_device) */
+  double* stress;               /* optional out, n_c x N FP64 */
+  double mean_stress[6];        /* <sigma> of the returned field */
+  double mean_strain[6];        /* <eps> of the returned field */
+  int iterations;               /* eta evaluations, all phases */
+  int iterations_fp32;          /* of which in float */
+  double final_eta;             /* last eta evaluated */
+  double final_delta;           /* last max |delta| (MAXDELTA stop), else 0 */
+  double* eta_history;          /* optional out (host), [history_capacity] */
+  double* mean_stress_history;  /* optional out (host), [history_capacity x n_c] */
+  int history_capacity;         /* entries available in the two histories */
+  int history_len;              /* entries written (= iterations, capped by capacity) */
+} fftls_result;
+
+/* Fill *opt with defaults: tol 1e-8, STOP_ETA, max_iter 1000, FP64, graphs on. */
+void fftls_default_options(fftls_options* opt);
+
+/* Create a context on CUDA device `device`.  Returns FFTLS_E_CUDA if the
+ * device cannot be used. */
+fftls_status fftls_create(fftls_ctx** ctx, int device);
+
+/* Free every device workspace and graph of the context.  NULL is ignored. */
+void fftls_destroy(fftls_ctx* ctx);
+
+/* Solve one load case (Sec. 3, eq. ds / eq. as with the chosen operator of Sec. 4).
+ * Returns FFTLS_OK, FFTLS_E_NOT_CONVERGED or FFTLS_E_DIVERGED with the outputs
+ * filled, or an error status with the outputs untouched. */
+fftls_status fftls_solve(fftls_ctx* ctx, const fftls_problem* prob, const fftls_options* opt, fftls_result* res);
+
+/* Effective stiffness C~ from <sigma> = C~ eps_bar (Sec. 2), as a symmetric
+ * Mandel matrix (shear rows and columns scaled by sqrt 2), n_c x n_c row-major
+ * in the first n_c^2 entries of C_eff.  Runs n_c unit Mandel loads; prob->eps_bar
+ * is ignored.  iterations[n_c] (optional) receives each solve's count. */
+fftls_status fftls_effective_stiffness(fftls_ctx* ctx, const fftls_problem* prob, const fftls_options* opt,
+                                       double* C_eff, int* iterations);
+
+/* Default reference medium (lambda0, mu0) for prob->scheme: eq. refAcc for the
+ * accelerated scheme (kappa0 = sqrt(k_min k_max), mu0 = sqrt(mu_min mu_max)),
+ * eq. ref with beta = 1/2 for the direct scheme; kappa = lambda + (2/d) mu.
+ * FFTLS_E_INVALID_ARG if the default degenerates (mu0 <= 0 or kappa0 <= 0). */
+fftls_status fftls_reference_medium(const fftls_problem* prob, double* lambda0, double* mu0);
+
+/* FFTLS_OK if the GPU transforms support a grid length L. */
+fftls_status fftls_supported_length(int L);
+
+/* Per-kernel device time of the last fftls_solve run with opt->profile = 1.
+ * names[i] (static strings), total_ms[i], launches[i] for i < *count;
+ * *count is the capacity on entry and the number of kernels on return. */
+fftls_status fftls_profile(const fftls_ctx* ctx, const char** names, double* total_ms, int* launches, int* count);
+
+/* Kernels launched on this context since creation (nodes of CUDA graphs
+ * counted one by one, including kernels that exit early once the solve has
+ * stopped) and the number of graph launches. */
+fftls_status fftls_counters(const fftls_ctx* ctx, long long* kernel_launches, long long* graph_launches);
+
+/* Message of the last error on this context ("" if none). */
+const char* fftls_last_error(const fftls_ctx* ctx);
+
+/* Static name of a status code. */
+const char* fftls_status_string(fftls_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTLS_H */

@@ -322,6 +322,8 @@ def solve(phase, lam, mu, eps_bar, green, scheme, lam0=None, mu0=None,
     With stop=STOP_MAXDELTA the test is max over voxels and components of
     |eps^{k+1} - eps^k| and |sigma^{k+1} - sigma^k| below tol (Sec. 5.1, 5.3);
     the field returned is then eps^{k+1} and `iterations` = k + 1.
+    The iteration is declared diverged (and stops, no update) when eta_k is
+    not finite or exceeds 1e4 eta_0.
     """
     phase = np.asarray(phase)
     d = phase.ndim
@@ -350,6 +352,7 @@ def solve(phase, lam, mu, eps_bar, green, scheme, lam0=None, mu0=None,
         eps = np.array(eps_init, dtype=np.float64, copy=True)
     eta_hist, mean_hist = [], []
     converged = False
+    diverged = False
     iterations = 0
     final_eta = math.nan
     sig = _contract(Cs, phase, eps)
@@ -359,7 +362,8 @@ def solve(phase, lam, mu, eps_bar, green, scheme, lam0=None, mu0=None,
         mean_hist.append(mean)
         iterations = it + 1
         final_eta = eta
-        if not np.isfinite(eta):
+        if not np.isfinite(eta) or (eta_hist[0] > 0 and eta > 1e4 * eta_hist[0]):
+            diverged = True
             break
         if stop == STOP_ETA and eta <= tol and mean_strain_error(eps, eb) <= tol:
             converged = True
@@ -396,6 +400,7 @@ def solve(phase, lam, mu, eps_bar, green, scheme, lam0=None, mu0=None,
         "mean_stress_history": np.array(mean_hist),
         "iterations": iterations,
         "converged": converged,
+        "diverged": diverged,
         "final_eta": final_eta,
         "lambda0": lam0,
         "mu0": mu0,

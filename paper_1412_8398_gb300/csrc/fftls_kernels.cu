@@ -1,0 +1,830 @@
+// CUDA kernels of the FFT Lippmann-Schwinger iteration (Willot 2015), sm_103a.
+//
+// One iteration is five passes over the fields in HBM:
+//   K1 fwd_x     : sigma = C(x):eps (and tau = sigma - C0:eps) per voxel,
+//                  fused with the x1 real-to-complex transform; FP64 sums of
+//                  <sigma>, <eps>                            (eq. ls, a1)
+//   K2 mid_y     : complex transform along x2 (forward)
+//   K3 fourier_z : transform along x3, then per mode the equilibrium norm
+//                  |k* . sigma_hat|^2 and e_hat = -G'(k):x_hat, the mean mode,
+//                  the 1/N of eq. ft, then the inverse transform along x3
+//                                                            (eq. discFour2, criterion)
+//   R  reduce_eta: eta, <sigma> history and the stop decision (one block)
+//   K2 mid_y     : inverse transform along x2
+//   K5 inv_x     : complex-to-real along x1 fused with the scheme update
+//                  (eq. ds or eq. as), optional max |delta| for the max-delta stop
+// The half spectrum is stored [comp][x3][x2][P] with x1 fastest, P >= n1/2 + 1.
+#include <math.h>
+
+#include "fftls_kernels.cuh"
+
+namespace fftls {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+template <int DIM> struct Comp;
+template <> struct Comp<3> {
+  static constexpr int NC = 6;
+  __device__ static constexpr int I(int c) { return c < 3 ? c : (c == 3 ? 1 : 0); }
+  __device__ static constexpr int J(int c) { return c < 3 ? c : (c == 5 ? 1 : 2); }
+};
+template <> struct Comp<2> {
+  static constexpr int NC = 3;
+  __device__ static constexpr int I(int c) { return c < 2 ? c : 0; }
+  __device__ static constexpr int J(int c) { return c < 2 ? c : 1; }
+};
+
+// Block-wide FP64 sum of W values per thread; result valid in thread 0.
+template <int W>
+__device__ void block_sum(double (&v)[W]) {
+  __shared__ double red[32][W];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    double x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    v[i] = x;
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < W; ++i) red[warp][i] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      double x = lane < nw ? red[lane][i] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[i] = x;
+    }
+  }
+  __syncthreads();
+}
+
+template <int W>
+__device__ void block_max(double (&v)[W]) {
+  __shared__ double red[32][W];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    double x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    v[i] = x;
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < W; ++i) red[warp][i] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      double x = lane < nw ? red[lane][i] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+      v[i] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// K1: constitutive law + forward x1 transform (real -> half complex)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void k_fwd_x(IterArgs<T> a) {
+  typedef typename Cplx<T>::type T2;
+  constexpr int NC = Comp<DIM>::NC;
+  if (a.ctrl->state != kRunning) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* buf = reinterpret_cast<T2*>(smem_raw);
+  const Geom g = a.g;
+  const int L1 = g.n1, H = g.H;
+  const int nout = a.dual ? 2 * NC : NC;
+  const int NP = (nout + 1) / 2;
+  const long long nlines = (long long)g.n2 * g.n3;
+  const int G = a.x_lines;
+  double acc[2 * NC];
+#pragma unroll
+  for (int c = 0; c < 2 * NC; ++c) acc[c] = 0.0;
+
+  for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
+    const int nl = (int)min((long long)G, nlines - l0);
+    T accf[2 * NC];
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) accf[c] = (T)0;
+    for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
+      const int gl = idx / L1, x = idx - gl * L1;
+      const long long vox = (l0 + gl) * (long long)L1 + x;
+      const T* cf = a.coef + (int)a.phase[vox] * kCoef;
+      const T lam = cf[0], mu2 = cf[1], dlam = cf[2], dmu2 = cf[3];
+      T e[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) e[c] = a.eps[(long long)c * g.N + vox];
+      T tr = e[0] + e[1];
+      if (DIM == 3) tr += e[2];
+      T out[2 * NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const bool diag = c < DIM;
+        const T s = mu2 * e[c] + (diag ? lam * tr : (T)0);
+        accf[c] += s;
+        accf[NC + c] += e[c];
+        if (a.dual) {
+          out[c] = dmu2 * e[c] + (diag ? dlam * tr : (T)0);
+          out[NC + c] = s;
+        } else {
+          out[c] = s;
+        }
+      }
+      T2* line = buf + (size_t)gl * NP * L1;
+#pragma unroll
+      for (int p = 0; p < NC; ++p) {
+        if (p < NP) {
+          T2 v;
+          v.x = out[2 * p];
+          v.y = (2 * p + 1 < nout) ? out[2 * p + 1] : (T)0;
+          line[p * L1 + x] = v;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) acc[c] += (double)accf[c];
+    __syncthreads();
+    smem_fft(buf, a.px, nl * NP, 1, L1, 0, 1, a.twx, false);
+    for (int idx = threadIdx.x; idx < nl * NP * H; idx += blockDim.x) {
+      const int line = idx / H, k = idx - line * H;
+      const int gl = line / NP, p = line - gl * NP;
+      const T2 Z = buf[line * L1 + k];
+      const T2 Zm = buf[line * L1 + (k == 0 ? 0 : L1 - k)];
+      T2 A, B;
+      A.x = (T)0.5 * (Z.x + Zm.x);
+      A.y = (T)0.5 * (Z.y - Zm.y);
+      B.x = (T)0.5 * (Z.y + Zm.y);
+      B.y = (T)-0.5 * (Z.x - Zm.x);
+      const long long off = (l0 + gl) * (long long)g.P + k;
+      a.spec[(long long)(2 * p) * g.CS + off] = A;
+      if (2 * p + 1 < nout) a.spec[(long long)(2 * p + 1) * g.CS + off] = B;
+    }
+    __syncthreads();
+  }
+  block_sum<2 * NC>(acc);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) a.part_mean[(size_t)blockIdx.x * 2 * NC + c] = acc[c];
+}
+
+// ---------------------------------------------------------------------------
+// K2: complex transform along x2, in place, tiles of y_w columns
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_mid_y(IterArgs<T> a, int comp0, int inv) {
+  typedef typename Cplx<T>::type T2;
+  const int st = a.ctrl->state;
+  if (inv ? (st != kRunning && st != kLast) : (st != kRunning)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* buf = reinterpret_cast<T2*>(smem_raw);
+  const Geom g = a.g;
+  const int w = a.y_w;
+  const int x0 = blockIdx.x * w;
+  const int nx = min(w, g.H - x0);
+  const int n2 = g.n2;
+  const long long base = (long long)(comp0 + blockIdx.z) * g.CS + (long long)blockIdx.y * n2 * g.P + x0;
+  for (int idx = threadIdx.x; idx < n2 * w; idx += blockDim.x) {
+    const int y = idx / w, xc = idx - y * w;
+    T2 v;
+    if (xc < nx) v = a.spec[base + (long long)y * g.P + xc];
+    else { v.x = (T)0; v.y = (T)0; }
+    buf[idx] = v;
+  }
+  __syncthreads();
+  smem_fft(buf, a.py, w, w, 0, 1, w, a.twy, inv != 0);
+  for (int idx = threadIdx.x; idx < n2 * w; idx += blockDim.x) {
+    const int y = idx / w, xc = idx - y * w;
+    if (xc < nx) a.spec[base + (long long)y * g.P + xc] = buf[idx];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: transform along x3 + Fourier-space work + inverse along x3
+// ---------------------------------------------------------------------------
+// Per mode with x_hat the tensor held by this block:
+//   * eta: w_q |k* . x_hat|^2 (x_hat = sigma_hat), w_q = 2 for x1 modes with a
+//     conjugate partner outside the half spectrum, else 1 (eq. criterion, A3);
+//   * e_hat = -G'(k) : x_hat / N at q != 0, with
+//       MS/C/R (k = phase * i * kr, kr real): the continuum operator eq. green0b at
+//       direction kr (the phase cancels),
+//       W: the displacement form with a 2x2 solve in span{k, conj(k)},
+//       MS with some q_i = pi (even L): G = C0^{-1} (eq. hfreq),
+//       k = 0 at q != 0 (C, R): 0 (eq. mulfix, mysymgr, 3D rule);
+//   * q = 0: e_hat = eps_bar (tau form: N eps_bar / N) or 0 (sigma form).
+template <typename T, int DIM>
+__device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y, int z,
+                                             typename Cplx<T>::type* X, bool do_green, bool do_eta,
+                                             T& eta_acc) {
+  typedef typename Cplx<T>::type T2;
+  typedef Comp<DIM> CM;
+  constexpr int NC = CM::NC;
+  const KTab<T> kt[3] = {a.kx[x], a.ky[y], a.kz[z]};
+  const bool q0 = (x == 0 && y == 0 && z == 0);
+  const T wq = (x == 0 || 2 * x == a.g.n1) ? (T)1 : (T)2;
+  const T invN = (T)(1.0 / (double)a.g.N);
+  const T mu0 = (T)a.mu0, lam0 = (T)a.lam0;
+  // full symmetric tensor view
+  T2 M[DIM][DIM];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    M[CM::I(c)][CM::J(c)] = X[c];
+    M[CM::J(c)][CM::I(c)] = X[c];
+  }
+  T2 E[NC];
+  if (a.green != kWillot) {
+    T kr[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      if (a.green == kMS) kr[i] = kt[i].q;
+      else if (a.green == kCentered) kr[i] = kt[i].sn;
+      else {
+        T v = (T)2 * kt[i].sh;
+#pragma unroll
+        for (int m = 0; m < DIM; ++m)
+          if (m != i) v *= kt[m].ch;
+        kr[i] = v;
+      }
+    }
+    T2 V[DIM];
+    T K2 = (T)0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      T2 s;
+      s.x = (T)0; s.y = (T)0;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) { s.x += M[i][j].x * kr[i]; s.y += M[i][j].y * kr[i]; }
+      V[j] = s;
+      K2 += kr[j] * kr[j];
+    }
+    if (do_eta) {
+      T s = (T)0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) s += V[j].x * V[j].x + V[j].y * V[j].y;
+      // operator G uses q_i = +pi at an even-L Nyquist index on both sides of the
+      // spectrum, so the conjugate partner (-q) of a half-spectrum mode has k with
+      // the Nyquist components of x2, x3 not negated: add its term explicitly.
+      bool flip = false;
+      if (a.green == kMS && wq == (T)2) {
+#pragma unroll
+        for (int i = 1; i < DIM; ++i) flip = flip || (kt[i].nyq != (T)0);
+      }
+      if (flip) {
+        T sp = (T)0;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+          T2 u;
+          u.x = (T)0; u.y = (T)0;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            const T kk = (i > 0 && kt[i].nyq != (T)0) ? -kr[i] : kr[i];
+            u.x += M[i][j].x * kk;
+            u.y += M[i][j].y * kk;
+          }
+          sp += u.x * u.x + u.y * u.y;
+        }
+        eta_acc += s + sp;
+      } else {
+        eta_acc += wq * s;
+      }
+    }
+    if (!do_green) return;
+    bool nyq = false;
+    if (a.green == kMS) {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) nyq = nyq || (kt[i].nyq != (T)0);
+    }
+    if (q0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { E[c].x = a.dual ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
+    } else if (nyq) {
+      // -C0^{-1}:x / N,  C0^{-1} = I/(2 mu0) - lam0 / (2 mu0 (d lam0 + 2 mu0)) dd
+      T2 tr;
+      tr.x = (T)0; tr.y = (T)0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) { tr.x += X[c].x; tr.y += X[c].y; }
+      const T a1 = (T)(0.5 / a.mu0);
+      const T a2 = (T)(a.lam0 / (2.0 * a.mu0 * (DIM * a.lam0 + 2.0 * a.mu0)));
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const bool diag = c < DIM;
+        E[c].x = -invN * (a1 * X[c].x - (diag ? a2 * tr.x : (T)0));
+        E[c].y = -invN * (a1 * X[c].y - (diag ? a2 * tr.y : (T)0));
+      }
+    } else if (K2 == (T)0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { E[c].x = (T)0; E[c].y = (T)0; }
+    } else {
+      const T c0 = (lam0 + mu0) / (lam0 + (T)2 * mu0);
+      T2 S;
+      S.x = (T)0; S.y = (T)0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) { S.x += kr[j] * V[j].x; S.y += kr[j] * V[j].y; }
+      const T f = -invN / (mu0 * K2);
+      const T h = c0 / K2;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int i = CM::I(c), j = CM::J(c);
+        E[c].x = f * ((T)0.5 * (kr[i] * V[j].x + kr[j] * V[i].x) - h * kr[i] * kr[j] * S.x);
+        E[c].y = f * ((T)0.5 * (kr[i] * V[j].y + kr[j] * V[i].y) - h * kr[i] * kr[j] * S.y);
+      }
+    }
+  } else {
+    // Willot-Pellegrini k_i = e^{i q_i} - 1 (complex)
+    T2 k[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) { k[i].x = kt[i].cm1; k[i].y = kt[i].sn; }
+    // b_j = sum_i conj(k_i) x_ij
+    T2 b[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      T2 s;
+      s.x = (T)0; s.y = (T)0;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) s = cadd(s, cmul(cconj(k[i]), M[i][j]));
+      b[j] = s;
+    }
+    if (do_eta) {
+      T s = (T)0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) s += b[j].x * b[j].x + b[j].y * b[j].y;
+      eta_acc += wq * s;
+    }
+    if (!do_green) return;
+    if (q0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { E[c].x = a.dual ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
+    } else {
+      T K = (T)0;
+      T2 gk, p, r;
+      gk.x = gk.y = p.x = p.y = r.x = r.y = (T)0;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        K += k[i].x * k[i].x + k[i].y * k[i].y;
+        gk = cadd(gk, cmul(k[i], k[i]));
+        p = cadd(p, cmul(k[i], b[i]));
+        r = cadd(r, cmul(cconj(k[i]), b[i]));
+      }
+      // (lam0 + mu0) K alpha + mu0 g beta = p ;  lam0 conj(g) alpha + 2 mu0 K beta = r
+      const T det = (T)2 * mu0 * (lam0 + mu0) * K * K - lam0 * mu0 * (gk.x * gk.x + gk.y * gk.y);
+      const T idet = (T)1 / det;
+      T2 al = csub(cscale(p, (T)2 * mu0 * K), cscale(cmul(gk, r), mu0));
+      T2 be = csub(cscale(r, (lam0 + mu0) * K), cscale(cmul(cconj(gk), p), lam0));
+      al = cscale(al, idet);
+      be = cscale(be, idet);
+      const T iu = (T)1 / (mu0 * K);
+      T2 u[DIM];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        T2 t = csub(b[j], cscale(cmul(cconj(k[j]), al), lam0));
+        t = csub(t, cscale(cmul(k[j], be), mu0));
+        u[j] = cscale(t, iu);
+      }
+      const T f = (T)-0.5 * invN;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int i = CM::I(c), j = CM::J(c);
+        E[c] = cscale(cadd(cmul(k[i], u[j]), cmul(k[j], u[i])), f);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) X[c] = E[c];
+}
+
+template <typename T, int DIM>
+__global__ void k_fourier_z(IterArgs<T> a) {
+  typedef typename Cplx<T>::type T2;
+  constexpr int NC = Comp<DIM>::NC;
+  if (a.ctrl->state != kRunning) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* buf = reinterpret_cast<T2*>(smem_raw);
+  const Geom g = a.g;
+  const int w = a.z_w;
+  const int x0 = blockIdx.x * w;
+  const int y = blockIdx.y;
+  const int kind = blockIdx.z;
+  const int c0 = kind == 0 ? 0 : NC;
+  const bool do_green = kind == 0;
+  const bool do_eta = a.dual ? (kind == 1) : true;
+  const int n3 = g.n3;
+  const int nx = min(w, g.H - x0);
+  const int cs = n3 * w;
+  const long long rowz = (long long)g.n2 * g.P;
+  const long long base = (long long)y * g.P + x0;
+  for (int idx = threadIdx.x; idx < NC * cs; idx += blockDim.x) {
+    const int c = idx / cs, rem = idx - c * cs;
+    const int z = rem / w, xc = rem - z * w;
+    T2 v;
+    if (xc < nx) v = a.spec[(long long)(c0 + c) * g.CS + z * rowz + base + xc];
+    else { v.x = (T)0; v.y = (T)0; }
+    buf[idx] = v;
+  }
+  __syncthreads();
+  smem_fft(buf, a.pz, NC * w, w, cs, 1, w, a.twz, false);
+  T eta_acc = (T)0;
+  for (int idx = threadIdx.x; idx < cs; idx += blockDim.x) {
+    const int z = idx / w, xc = idx - z * w;
+    if (xc >= nx) continue;
+    T2 X[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) X[c] = buf[c * cs + idx];
+    fourier_mode<T, DIM>(a, x0 + xc, y, z, X, do_green, do_eta, eta_acc);
+    if (do_green)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) buf[c * cs + idx] = X[c];
+  }
+  __syncthreads();
+  if (do_green) {
+    smem_fft(buf, a.pz, NC * w, w, cs, 1, w, a.twz, true);
+    for (int idx = threadIdx.x; idx < NC * cs; idx += blockDim.x) {
+      const int c = idx / cs, rem = idx - c * cs;
+      const int z = rem / w, xc = rem - z * w;
+      if (xc < nx) a.spec[(long long)c * g.CS + z * rowz + base + xc] = buf[idx];
+    }
+  }
+  double e1[1] = {(double)eta_acc};
+  block_sum<1>(e1);
+  if (threadIdx.x == 0)
+    a.part_eta[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = e1[0];
+}
+
+// ---------------------------------------------------------------------------
+// R: eta, <sigma>, history and stop decision (single block)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts) {
+  constexpr int NC = Comp<DIM>::NC;
+  Ctrl* ctl = a.ctrl;
+  const int st = ctl->state;
+  if (st != kRunning || ctl->it >= ctl->max_it) {
+    if (threadIdx.x == 0 && (st == kLast || st == kRunning)) ctl->state = kStopped;
+    return;
+  }
+  double s[2 * NC + 1];
+#pragma unroll
+  for (int c = 0; c < 2 * NC + 1; ++c) s[c] = 0.0;
+  for (int b = threadIdx.x; b < a.x1_blocks; b += blockDim.x)
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) s[c] += a.part_mean[(size_t)b * 2 * NC + c];
+  for (int b = threadIdx.x; b < n_eta_parts; b += blockDim.x) s[2 * NC] += a.part_eta[b];
+  block_sum<2 * NC + 1>(s);
+  if (threadIdx.x != 0) return;
+  const double N = (double)a.g.N;
+  double fro2 = 0.0, eb2 = 0.0, d2 = 0.0;
+  const int it = ctl->it;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const double ms = s[c] / N, me = s[NC + c] / N;
+    const double wgt = c < DIM ? 1.0 : 2.0;
+    fro2 += wgt * ms * ms;
+    eb2 += wgt * a.eps_bar[c] * a.eps_bar[c];
+    d2 += wgt * (me - a.eps_bar[c]) * (me - a.eps_bar[c]);
+    a.ms_hist[(size_t)it * NC + c] = ms;
+  }
+  const double num = sqrt(fmax(s[2 * NC], 0.0));
+  const double den = N * sqrt(fro2);
+  double eta;
+  if (num == 0.0) eta = 0.0;
+  else if (den == 0.0) eta = INFINITY;
+  else eta = num / den;
+  const double merr = eb2 > 0.0 ? sqrt(d2 / eb2) : sqrt(d2);
+  a.eta_hist[it] = eta;
+  ctl->it = it + 1;
+  ctl->last_eta = eta;
+  ctl->last_mean_err = merr;
+  if (it == 0) { ctl->eta0 = eta; ctl->best = eta; }
+  int ns = kRunning;
+  if (!isfinite(eta) || (ctl->eta0 > 0.0 && eta > 1e4 * ctl->eta0)) {
+    ns = kDiverged;
+  } else if (ctl->stop_rule == 0 && eta <= ctl->tol && (!ctl->mean_guard || merr <= ctl->tol)) {
+    ns = ctl->switch_mode ? kSwitch : kConverged;
+  } else {
+    if (ctl->stall_window > 0) {
+      if (eta < 0.9 * ctl->best) { ctl->best = eta; ctl->stall = 0; }
+      else if (++ctl->stall >= ctl->stall_window) ns = kSwitch;
+    }
+    if (ns == kRunning && it + 1 >= ctl->max_it) ns = kLast;
+  }
+  ctl->state = ns;
+}
+
+// ---------------------------------------------------------------------------
+// K5: inverse x1 transform (half complex -> real) + scheme update
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void k_inv_x(IterArgs<T> a) {
+  typedef typename Cplx<T>::type T2;
+  constexpr int NC = Comp<DIM>::NC;
+  constexpr int NPI = (NC + 1) / 2;
+  const int st = a.ctrl->state;
+  if (st != kRunning && st != kLast) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* buf = reinterpret_cast<T2*>(smem_raw);
+  const Geom g = a.g;
+  const int L1 = g.n1, H = g.H;
+  const long long nlines = (long long)g.n2 * g.n3;
+  const int G = a.x_lines;
+  double dmax[2] = {0.0, 0.0};
+  for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
+    const int nl = (int)min((long long)G, nlines - l0);
+    for (int idx = threadIdx.x; idx < nl * NPI * H; idx += blockDim.x) {
+      const int line = idx / H, k = idx - line * H;
+      const int gl = line / NPI, p = line - gl * NPI;
+      const long long off = (l0 + gl) * (long long)g.P + k;
+      T2 A = a.spec[(long long)(2 * p) * g.CS + off];
+      T2 B;
+      if (2 * p + 1 < NC) B = a.spec[(long long)(2 * p + 1) * g.CS + off];
+      else { B.x = (T)0; B.y = (T)0; }
+      if (k == 0 || 2 * k == L1) { A.y = (T)0; B.y = (T)0; }
+      T2 z;
+      z.x = A.x - B.y;
+      z.y = A.y + B.x;
+      buf[line * L1 + k] = z;
+      if (k > 0 && L1 - k >= H) {
+        T2 zm;
+        zm.x = A.x + B.y;
+        zm.y = B.x - A.y;
+        buf[line * L1 + L1 - k] = zm;
+      }
+    }
+    __syncthreads();
+    smem_fft(buf, a.px, nl * NPI, 1, L1, 0, 1, a.twx, true);
+    for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
+      const int gl = idx / L1, x = idx - gl * L1;
+      const long long vox = (l0 + gl) * (long long)L1 + x;
+      T e[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T2 v = buf[(gl * NPI + c / 2) * L1 + x];
+        e[c] = (c & 1) ? v.y : v.x;
+      }
+      T o[NC], n[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) o[c] = a.eps[(long long)c * g.N + vox];
+      const T* cf = a.coef + (int)a.phase[vox] * kCoef;
+      if (a.update == kUpdDirectTau) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) n[c] = e[c];
+      } else if (a.update == kUpdDirectSig) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) n[c] = o[c] + e[c];
+      } else {
+        T d[NC];
+        T trd = (T)0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { d[c] = e[c] - o[c]; if (c < DIM) trd += d[c]; }
+        const T am = cf[4], av = cf[5];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) n[c] = o[c] + am * d[c] + (c < DIM ? av * trd : (T)0);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) a.eps[(long long)c * g.N + vox] = n[c];
+      if (a.want_delta) {
+        T dn[NC];
+        T trn = (T)0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { dn[c] = n[c] - o[c]; if (c < DIM) trn += dn[c]; }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const T ds = cf[1] * dn[c] + (c < DIM ? cf[0] * trn : (T)0);
+          dmax[0] = fmax(dmax[0], (double)fabs(dn[c]));
+          dmax[1] = fmax(dmax[1], (double)fabs(ds));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (a.want_delta) {
+    block_max<2>(dmax);
+    if (threadIdx.x == 0) {
+      a.part_delta[(size_t)blockIdx.x * 2] = dmax[0];
+      a.part_delta[(size_t)blockIdx.x * 2 + 1] = dmax[1];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_reduce_delta(IterArgs<T> a) {
+  Ctrl* ctl = a.ctrl;
+  const int st = ctl->state;
+  if (st != kRunning && st != kLast) return;
+  double m[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < a.x5_blocks; b += blockDim.x) {
+    m[0] = fmax(m[0], a.part_delta[(size_t)b * 2]);
+    m[1] = fmax(m[1], a.part_delta[(size_t)b * 2 + 1]);
+  }
+  block_max<2>(m);
+  if (threadIdx.x == 0) {
+    const double dl = fmax(m[0], m[1]);
+    ctl->last_delta = dl;
+    if (ctl->stop_rule == 1 && dl < ctl->tol) ctl->state = kConverged;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// elementwise helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fill_eps(T* eps, int nc, long long N, double e0, double e1, double e2, double e3, double e4,
+                           double e5) {
+  const double ev[6] = {e0, e1, e2, e3, e4, e5};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    for (int c = 0; c < nc; ++c) eps[(long long)c * N + i] = (T)ev[c];
+}
+
+template <typename TO, typename TI>
+__global__ void k_convert(TO* out, const TI* in, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+template <typename T, int DIM>
+__global__ void k_stress(const T* eps, const uint8_t* phase, const T* coef, long long N, double* stress,
+                         double* part) {
+  constexpr int NC = Comp<DIM>::NC;
+  double acc[2 * NC];
+#pragma unroll
+  for (int c = 0; c < 2 * NC; ++c) acc[c] = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x) {
+    const T* cf = coef + (int)phase[v] * kCoef;
+    double e[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) e[c] = (double)eps[(long long)c * N + v];
+    double tr = e[0] + e[1] + (DIM == 3 ? e[2] : 0.0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double s = (double)cf[1] * e[c] + (c < DIM ? (double)cf[0] * tr : 0.0);
+      if (stress) stress[(long long)c * N + v] = s;
+      acc[c] += s;
+      acc[NC + c] += e[c];
+    }
+  }
+  block_sum<2 * NC>(acc);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) part[(size_t)blockIdx.x * 2 * NC + c] = acc[c];
+}
+
+__global__ void k_phase_max(const uint8_t* phase, long long N, unsigned int* out) {
+  unsigned int m = 0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x)
+    m = max(m, (unsigned int)phase[v]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void k_sum_parts(const double* part, int blocks, int width, double* out) {
+  // one thread per output value, fixed order: deterministic
+  const int c = threadIdx.x;
+  if (c >= width) return;
+  double s = 0.0;
+  for (int b = 0; b < blocks; ++b) s += part[(size_t)b * width + c];
+  out[c] = s;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) {
+  if (a.dim == 3) k_fwd_x<T, 3><<<a.x1_blocks, a.x1_threads, a.x1_smem, s>>>(a);
+  else k_fwd_x<T, 2><<<a.x1_blocks, a.x1_threads, a.x1_smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mid_y(const IterArgs<T>& a, int ncomp, bool inv, cudaStream_t s) {
+  if (a.g.n2 == 1) return cudaSuccess;
+  dim3 grid((a.g.H + a.y_w - 1) / a.y_w, a.g.n3, ncomp);
+  k_mid_y<T><<<grid, a.y_threads, a.y_smem, s>>>(a, 0, inv ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s) {
+  dim3 grid((a.g.H + a.z_w - 1) / a.z_w, a.g.n2, a.dual ? 2 : 1);
+  if (a.dim == 3) k_fourier_z<T, 3><<<grid, a.z_threads, a.z_smem, s>>>(a);
+  else k_fourier_z<T, 2><<<grid, a.z_threads, a.z_smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaStream_t s) {
+  const int nparts = ((a.g.H + a.z_w - 1) / a.z_w) * a.g.n2 * (a.dual ? 2 : 1);
+  if (a.dim == 3) k_reduce_eta<T, 3><<<1, 512, 0, s>>>(a, nparts);
+  else k_reduce_eta<T, 2><<<1, 512, 0, s>>>(a, nparts);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_inv_x(const IterArgs<T>& a, cudaStream_t s) {
+  if (a.dim == 3) k_inv_x<T, 3><<<a.x5_blocks, a.x5_threads, a.x5_smem, s>>>(a);
+  else k_inv_x<T, 2><<<a.x5_blocks, a.x5_threads, a.x5_smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s) {
+  k_reduce_delta<T><<<1, 512, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+int kernel_max_threads(int dim, int which) {
+  cudaFuncAttributes at;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (dim == 3) {
+    if (which == 0) e = cudaFuncGetAttributes(&at, (const void*)k_fwd_x<T, 3>);
+    if (which == 1) e = cudaFuncGetAttributes(&at, (const void*)k_mid_y<T>);
+    if (which == 2) e = cudaFuncGetAttributes(&at, (const void*)k_fourier_z<T, 3>);
+    if (which == 3) e = cudaFuncGetAttributes(&at, (const void*)k_inv_x<T, 3>);
+  } else {
+    if (which == 0) e = cudaFuncGetAttributes(&at, (const void*)k_fwd_x<T, 2>);
+    if (which == 1) e = cudaFuncGetAttributes(&at, (const void*)k_mid_y<T>);
+    if (which == 2) e = cudaFuncGetAttributes(&at, (const void*)k_fourier_z<T, 2>);
+    if (which == 3) e = cudaFuncGetAttributes(&at, (const void*)k_inv_x<T, 2>);
+  }
+  return e == cudaSuccess ? at.maxThreadsPerBlock : 0;
+}
+
+template <typename T>
+cudaError_t set_kernel_attributes(const IterArgs<T>& a) {
+  cudaError_t e = cudaSuccess;
+#define FFTLS_ATTR(fn, bytes)                                                                    \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));
+  if (a.dim == 3) {
+    FFTLS_ATTR((k_fwd_x<T, 3>), a.x1_smem);
+    FFTLS_ATTR((k_inv_x<T, 3>), a.x5_smem);
+    FFTLS_ATTR((k_fourier_z<T, 3>), a.z_smem);
+  } else {
+    FFTLS_ATTR((k_fwd_x<T, 2>), a.x1_smem);
+    FFTLS_ATTR((k_inv_x<T, 2>), a.x5_smem);
+    FFTLS_ATTR((k_fourier_z<T, 2>), a.z_smem);
+  }
+  FFTLS_ATTR((k_mid_y<T>), a.y_smem);
+#undef FFTLS_ATTR
+  return e;
+}
+
+template <typename T>
+cudaError_t launch_fill_eps(T* eps, int nc, long long N, const double* e, cudaStream_t s) {
+  const int blocks = (int)min((N + 255) / 256, (long long)152 * 16);
+  k_fill_eps<T><<<blocks, 256, 0, s>>>(eps, nc, N, e[0], e[1], e[2], e[3], e[4], e[5]);
+  return cudaGetLastError();
+}
+
+template <typename TO, typename TI>
+cudaError_t launch_convert(TO* out, const TI* in, long long n, cudaStream_t s) {
+  const int blocks = (int)min((n + 255) / 256, (long long)152 * 16);
+  k_convert<TO, TI><<<blocks, 256, 0, s>>>(out, in, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stress(const T* eps, const uint8_t* phase, const T* coef, int dim, long long N, double* stress_out,
+                          double* part, int blocks, cudaStream_t s) {
+  if (dim == 3) k_stress<T, 3><<<blocks, 256, 0, s>>>(eps, phase, coef, N, stress_out, part);
+  else k_stress<T, 2><<<blocks, 256, 0, s>>>(eps, phase, coef, N, stress_out, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_max(const uint8_t* phase, long long N, unsigned int* out, int blocks, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  k_phase_max<<<blocks, 256, 0, s>>>(phase, N, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_parts(const double* part, int blocks, int width, double* out, cudaStream_t s) {
+  k_sum_parts<<<1, 32, 0, s>>>(part, blocks, width, out);
+  return cudaGetLastError();
+}
+
+#define FFTLS_INST(T)                                                                                   \
+  template cudaError_t launch_fwd_x<T>(const IterArgs<T>&, cudaStream_t);                              \
+  template cudaError_t launch_mid_y<T>(const IterArgs<T>&, int, bool, cudaStream_t);                   \
+  template cudaError_t launch_fourier_z<T>(const IterArgs<T>&, cudaStream_t);                          \
+  template cudaError_t launch_reduce_eta<T>(const IterArgs<T>&, cudaStream_t);                         \
+  template cudaError_t launch_inv_x<T>(const IterArgs<T>&, cudaStream_t);                              \
+  template cudaError_t launch_reduce_delta<T>(const IterArgs<T>&, cudaStream_t);                       \
+  template cudaError_t set_kernel_attributes<T>(const IterArgs<T>&);                                    \
+  template int kernel_max_threads<T>(int, int);                                                         \
+  template cudaError_t launch_fill_eps<T>(T*, int, long long, const double*, cudaStream_t);            \
+  template cudaError_t launch_stress<T>(const T*, const uint8_t*, const T*, int, long long, double*,   \
+                                        double*, int, cudaStream_t);
+FFTLS_INST(float)
+FFTLS_INST(double)
+template cudaError_t launch_convert<double, float>(double*, const float*, long long, cudaStream_t);
+template cudaError_t launch_convert<float, double>(float*, const double*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, double>(double*, const double*, long long, cudaStream_t);
+
+}  // namespace fftls

@@ -1,0 +1,894 @@
+// Host driver and C ABI of the FFT Lippmann-Schwinger solver (see include/fftls.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "fftls.h"
+#include "fftls_kernels.cuh"
+
+using namespace fftls;
+
+namespace {
+
+constexpr int kMaxL = 1024;
+constexpr int kNumKinds = 7;
+const char* const kKindNames[2][kNumKinds] = {
+    {"fwd_x_f32", "mid_y_fwd_f32", "fourier_z_f32", "reduce_eta_f32", "mid_y_inv_f32", "inv_x_f32",
+     "reduce_delta_f32"},
+    {"fwd_x_f64", "mid_y_fwd_f64", "fourier_z_f64", "reduce_eta_f64", "mid_y_inv_f64", "inv_x_f64",
+     "reduce_delta_f64"}};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned char> key;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key.clear();
+  }
+};
+
+bool factor_plan(int L, AxisPlan* p) {
+  if (L < 1 || L > kMaxL) return false;
+  int n = L, twos = 0, threes = 0, fives = 0;
+  while (n % 2 == 0) { n /= 2; ++twos; }
+  while (n % 3 == 0) { n /= 3; ++threes; }
+  while (n % 5 == 0) { n /= 5; ++fives; }
+  if (n != 1) return false;
+  std::vector<int> r;
+  int n8 = twos / 3, rem = twos % 3;
+  if (rem == 1 && n8 > 0) { --n8; r.push_back(4); r.push_back(4); }
+  else if (rem == 2) r.push_back(4);
+  else if (rem == 1) r.push_back(2);
+  for (int i = 0; i < n8; ++i) r.push_back(8);
+  for (int i = 0; i < threes; ++i) r.push_back(3);
+  for (int i = 0; i < fives; ++i) r.push_back(5);
+  if ((int)r.size() > kMaxStages) return false;
+  p->L = L;
+  p->nst = (int)r.size();
+  for (int i = 0; i < kMaxStages; ++i) p->radix[i] = i < p->nst ? r[i] : 1;
+  return true;
+}
+
+int min_radix(const AxisPlan& p) {
+  int m = 1 << 30;
+  for (int i = 0; i < p.nst; ++i) m = std::min(m, p.radix[i]);
+  return p.nst ? m : 1 << 30;
+}
+
+long long bfly(const AxisPlan& p, long long lines) {
+  return p.nst ? lines * p.L / min_radix(p) : 0;
+}
+
+}  // namespace
+
+struct fftls_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  size_t smem_optin = 0;
+  int num_sms = 0;
+  DevBuf phase, eps32, eps64, spec, coef32, coef64, tw32, tw64, kt32, kt64;
+  DevBuf part_mean, part_eta, part_delta, sums, ctrl, eta_hist, ms_hist, scratch;
+  GraphCache graphs[2];
+  Ctrl* h_ctrl = nullptr;  // pinned
+  double* h_sums = nullptr;
+  // profiling
+  double prof_ms[2][kNumKinds];
+  int prof_n[2][kNumKinds];
+  long long launches = 0;        // kernels launched (graph nodes counted one by one)
+  long long graph_launches = 0;
+  struct ProfEv { cudaEvent_t a, b; int kind; };
+  std::vector<ProfEv> ev;
+};
+
+namespace {
+
+fftls_status set_err(fftls_ctx* c, fftls_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CUDA_TRY(ctx, ...)                                                                                      \
+  do {                                                                                                          \
+    cudaError_t e_ = (__VA_ARGS__);                                                                             \
+    if (e_ != cudaSuccess)                                                                                      \
+      return set_err(ctx, e_ == cudaErrorMemoryAllocation ? FFTLS_E_OOM : FFTLS_E_CUDA, "%s: %s (line %d)",      \
+                     #__VA_ARGS__, cudaGetErrorString(e_), __LINE__);                                           \
+  } while (0)
+
+int ncomp(int dim) { return dim == 3 ? 6 : 3; }
+
+bool default_medium(const fftls_problem* p, double* l0, double* m0) {
+  const int d = p->dim;
+  double kmin = INFINITY, kmax = -INFINITY, mmin = INFINITY, mmax = -INFINITY;
+  for (int a = 0; a < p->n_phases; ++a) {
+    const double k = p->lambda[a] + 2.0 / d * p->mu[a];
+    kmin = std::min(kmin, k);
+    kmax = std::max(kmax, k);
+    mmin = std::min(mmin, p->mu[a]);
+    mmax = std::max(mmax, p->mu[a]);
+  }
+  double k0, mu0;
+  if (p->scheme == FFTLS_ACCELERATED) {
+    k0 = sqrt(kmin * kmax);
+    mu0 = sqrt(mmin * mmax);
+  } else {
+    k0 = 0.5 * (kmin + kmax);
+    mu0 = 0.5 * (mmin + mmax);
+  }
+  *l0 = k0 - 2.0 / d * mu0;
+  *m0 = mu0;
+  return mu0 > 0.0 && k0 > 0.0 && isfinite(k0) && isfinite(mu0);
+}
+
+fftls_status validate(fftls_ctx* c, const fftls_problem* p, const fftls_options* o) {
+  if (!p || !o) return set_err(c, FFTLS_E_INVALID_ARG, "null problem or options");
+  if (p->dim != 2 && p->dim != 3) return set_err(c, FFTLS_E_INVALID_ARG, "dim must be 2 or 3 (got %d)", p->dim);
+  for (int i = 0; i < 3; ++i)
+    if (p->n[i] < 1) return set_err(c, FFTLS_E_INVALID_ARG, "n[%d] = %d must be >= 1", i, p->n[i]);
+  if (p->dim == 2 && p->n[2] != 1) return set_err(c, FFTLS_E_INVALID_ARG, "dim 2 needs n[2] == 1");
+  for (int i = 0; i < 3; ++i) {
+    AxisPlan ap;
+    if (!factor_plan(p->n[i], &ap))
+      return set_err(c, FFTLS_E_UNSUPPORTED_SIZE, "n[%d] = %d: lengths must be <= %d with prime factors 2, 3, 5", i,
+                     p->n[i], kMaxL);
+  }
+  if (!p->phase) return set_err(c, FFTLS_E_INVALID_ARG, "phase is null");
+  if (p->n_phases < 1 || p->n_phases > 256) return set_err(c, FFTLS_E_INVALID_ARG, "n_phases must be 1..256");
+  if (!p->lambda || !p->mu) return set_err(c, FFTLS_E_INVALID_ARG, "lambda / mu are null");
+  for (int a = 0; a < p->n_phases; ++a) {
+    const double l = p->lambda[a], m = p->mu[a];
+    if (!isfinite(l) || !isfinite(m) || m < 0.0 || l + 2.0 / p->dim * m < 0.0)
+      return set_err(c, FFTLS_E_INVALID_ARG, "phase %d: need finite mu >= 0 and kappa >= 0", a);
+  }
+  if (p->green < 0 || p->green > 3) return set_err(c, FFTLS_E_INVALID_ARG, "unknown green %d", p->green);
+  if (p->scheme != FFTLS_DIRECT && p->scheme != FFTLS_ACCELERATED)
+    return set_err(c, FFTLS_E_INVALID_ARG, "unknown scheme %d", p->scheme);
+  for (int i = 0; i < ncomp(p->dim); ++i)
+    if (!isfinite(p->eps_bar[i])) return set_err(c, FFTLS_E_INVALID_ARG, "eps_bar[%d] not finite", i);
+  const bool l0nan = isnan(p->lambda0), m0nan = isnan(p->mu0);
+  if (l0nan != m0nan) return set_err(c, FFTLS_E_INVALID_ARG, "lambda0 and mu0 must both be NaN or both set");
+  if (!l0nan) {
+    if (!(p->mu0 > 0.0) || !(p->lambda0 + 2.0 / p->dim * p->mu0 > 0.0) || !isfinite(p->lambda0) || !isfinite(p->mu0))
+      return set_err(c, FFTLS_E_INVALID_ARG, "reference medium must be positive definite (mu0 > 0, kappa0 > 0)");
+  } else {
+    double l0, m0;
+    if (!default_medium(p, &l0, &m0))
+      return set_err(c, FFTLS_E_INVALID_ARG,
+                     "default reference medium degenerates (a phase with mu = 0 or kappa = 0): pass lambda0, mu0");
+  }
+  if (!(o->tol >= 0.0) || !isfinite(o->tol)) return set_err(c, FFTLS_E_INVALID_ARG, "tol must be finite and >= 0");
+  if (o->stop != FFTLS_STOP_ETA && o->stop != FFTLS_STOP_MAXDELTA)
+    return set_err(c, FFTLS_E_INVALID_ARG, "unknown stop rule %d", o->stop);
+  if (o->max_iter < 1) return set_err(c, FFTLS_E_INVALID_ARG, "max_iter must be >= 1");
+  if (o->precision < 0 || o->precision > 2) return set_err(c, FFTLS_E_INVALID_ARG, "unknown precision %d", o->precision);
+  return FFTLS_OK;
+}
+
+// Per-axis tables in FP64, then converted.
+void axis_tables(int L, std::vector<double>& tw, std::vector<double>& kt) {
+  tw.resize(2 * (size_t)L);
+  for (int t = 0; t < L; ++t) {
+    const double ang = -2.0 * M_PI * (double)t / (double)L;
+    double cs = cos(ang), sn = sin(ang);
+    if ((4 * t) % L == 0) {  // exact values at multiples of pi/2
+      const int qd = (4 * t) / L;
+      const double cq[4] = {1, 0, -1, 0}, sq[4] = {0, -1, 0, 1};
+      cs = cq[qd % 4];
+      sn = sq[qd % 4];
+    }
+    tw[2 * t] = cs;
+    tw[2 * t + 1] = sn;
+  }
+  kt.resize(6 * (size_t)L);
+  for (int m = 0; m < L; ++m) {
+    const int s = m <= L / 2 ? m : m - L;
+    const double q = 2.0 * M_PI * s / L;
+    double sn = sin(q), sh = sin(0.5 * q), ch = cos(0.5 * q);
+    if ((2 * s) % L == 0) sn = 0.0;        // q = 0, pi
+    if (s == 0) sh = 0.0;
+    if (2 * s == L) ch = 0.0;               // q = pi
+    if (4 * s == L) sn = 1.0;
+    if (4 * s == -L) sn = -1.0;
+    const double cm1 = -2.0 * sh * sh;     // cos q - 1 without cancellation
+    double* e = &kt[6 * (size_t)m];
+    e[0] = q;
+    e[1] = sn;
+    e[2] = cm1;
+    e[3] = sh;
+    e[4] = ch;
+    e[5] = (L % 2 == 0 && 2 * m == L) ? 1.0 : 0.0;
+  }
+}
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<float> {
+  static constexpr int idx = 0;
+};
+template <>
+struct Prec<double> {
+  static constexpr int idx = 1;
+};
+
+struct Setup {
+  int dim, nc;
+  Geom g;
+  AxisPlan px, py, pz;
+  double lam0, mu0;
+  double eps_bar[6];
+  int green, scheme;
+  const uint8_t* d_phase;
+  cudaStream_t s;
+  bool profile, graphs;
+};
+
+template <typename T>
+fftls_status upload_tables(fftls_ctx* c, const Setup& S, const fftls_problem* p, const T** coef, const void** tw,
+                           const void** kt) {
+  const int d = S.dim;
+  // 256 phase entries: ids >= n_phases read NaN coefficients (never out of bounds)
+  std::vector<T> cf(256 * kCoef, (T)NAN);
+  const double k0 = S.lam0 + 2.0 / d * S.mu0;
+  for (int a = 0; a < p->n_phases; ++a) {
+    const double l = p->lambda[a], m = p->mu[a];
+    const double k = l + 2.0 / d * m;
+    const double ak = k0 / (k + k0), am = S.mu0 / (m + S.mu0);
+    T* e = &cf[(size_t)a * kCoef];
+    e[0] = (T)l;
+    e[1] = (T)(2.0 * m);
+    e[2] = (T)(l - S.lam0);
+    e[3] = (T)(2.0 * (m - S.mu0));
+    e[4] = (T)(2.0 * am);
+    e[5] = (T)(2.0 * (ak - am) / d);
+    e[6] = e[7] = (T)0;
+  }
+  DevBuf& cb = Prec<T>::idx ? c->coef64 : c->coef32;
+  CUDA_TRY(c, cb.ensure(cf.size() * sizeof(T)));
+  CUDA_TRY(c, cudaMemcpyAsync(cb.p, cf.data(), cf.size() * sizeof(T), cudaMemcpyHostToDevice, S.s));
+  *coef = (const T*)cb.p;
+  // twiddles and wave-vector tables, three axes back to back
+  std::vector<T> twall, ktall;
+  size_t off_tw[3], off_kt[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    std::vector<double> twd, ktd;
+    axis_tables(ax == 0 ? S.g.n1 : (ax == 1 ? S.g.n2 : S.g.n3), twd, ktd);
+    off_tw[ax] = twall.size();
+    off_kt[ax] = ktall.size();
+    for (double v : twd) twall.push_back((T)v);
+    for (double v : ktd) ktall.push_back((T)v);
+    while (twall.size() % 4) twall.push_back((T)0);
+  }
+  DevBuf& tb = Prec<T>::idx ? c->tw64 : c->tw32;
+  DevBuf& kb = Prec<T>::idx ? c->kt64 : c->kt32;
+  CUDA_TRY(c, tb.ensure(twall.size() * sizeof(T)));
+  CUDA_TRY(c, kb.ensure(ktall.size() * sizeof(T)));
+  CUDA_TRY(c, cudaMemcpyAsync(tb.p, twall.data(), twall.size() * sizeof(T), cudaMemcpyHostToDevice, S.s));
+  CUDA_TRY(c, cudaMemcpyAsync(kb.p, ktall.data(), ktall.size() * sizeof(T), cudaMemcpyHostToDevice, S.s));
+  // the vectors are freed on return: make the copies complete first
+  CUDA_TRY(c, cudaStreamSynchronize(S.s));
+  for (int ax = 0; ax < 3; ++ax) {
+    tw[ax] = (const T*)tb.p + off_tw[ax];
+    kt[ax] = (const T*)kb.p + off_kt[ax];
+  }
+  return FFTLS_OK;
+}
+
+// Launch shapes for precision T.  Every stage of the in-place shared-memory
+// FFT needs its butterflies held by the block at once (kPer per thread), and
+// each kernel's block size is capped by its register use.  Returns false if a
+// size does not fit.
+template <typename T>
+bool plan_launch(fftls_ctx* c, const Setup& S, IterArgs<T>& a) {
+  typedef typename Cplx<T>::type T2;
+  const size_t cb = sizeof(T2);
+  const size_t lim = c->smem_optin;
+  const int nc = S.nc;
+  const Geom& g = S.g;
+  const long long nlines = (long long)g.n2 * g.n3;
+  auto cap_of = [&](int which) {
+    int m = kernel_max_threads<T>(S.dim, which);
+    m = (m / 32) * 32;
+    return std::max(32, std::min(m, 1024));
+  };
+  const int cap1 = cap_of(0), capy = cap_of(1), capz = cap_of(2), cap5 = cap_of(3);
+  auto threads = [&](long long butterflies, long long elems, int cap) {
+    long long t = (butterflies + kPer - 1) / kPer;
+    t = std::max(t, std::min<long long>(elems, 256));
+    t = ((t + 31) / 32) * 32;
+    return (int)std::min<long long>(std::max<long long>(t, 64), cap);
+  };
+  // x kernels: target ~48 KB per block
+  const int np1 = nc;  // dual pairs (worst case)
+  const int np5 = (nc + 1) / 2;
+  auto pick_lines = [&](int np, int cap) {
+    const size_t per = (size_t)np * g.n1 * cb;
+    if (per > lim) return 0;
+    int G = (int)std::max<size_t>(1, (48 * 1024) / per);
+    G = (int)std::min<long long>(G, nlines);
+    while (G > 1 && bfly(S.px, (long long)G * np) > (long long)cap * kPer) --G;
+    if (bfly(S.px, np) > (long long)cap * kPer) return 0;
+    return G;
+  };
+  const int G1 = pick_lines(np1, cap1), G5 = pick_lines(np5, cap5);
+  if (!G1 || !G5) return false;
+  a.x_lines = std::min(G1, G5);
+  const int G = a.x_lines;
+  a.x1_smem = (size_t)G * np1 * g.n1 * cb;
+  a.x5_smem = (size_t)G * np5 * g.n1 * cb;
+  a.x1_threads = threads(bfly(S.px, (long long)G * np1), (long long)G * g.n1, cap1);
+  a.x5_threads = threads(bfly(S.px, (long long)G * np5), (long long)G * g.n1, cap5);
+  const long long nbatches = (nlines + G - 1) / G;
+  a.x1_blocks = (int)std::min<long long>(nbatches, (long long)c->num_sms * 8);
+  a.x5_blocks = a.x1_blocks;
+  // y kernel: column tiles of up to 16, <= 64 KB
+  int wy = 16;
+  while (wy > 1 && ((size_t)g.n2 * wy * cb > std::min<size_t>(lim, 64 * 1024) ||
+                    bfly(S.py, wy) > (long long)capy * kPer))
+    wy /= 2;
+  if ((size_t)g.n2 * wy * cb > lim || bfly(S.py, wy) > (long long)capy * kPer) return false;
+  while (wy > 1 && wy / 2 >= g.H) wy /= 2;
+  a.y_w = wy;
+  a.y_smem = (size_t)g.n2 * wy * cb;
+  a.y_threads = threads(bfly(S.py, wy), (long long)g.n2 * wy, capy);
+  // z kernel: n_c components x n3 x w, <= ~100 KB (two blocks per SM)
+  int wz = g.n3 == 1 ? 32 : 16;
+  while (wz > 1 && ((size_t)nc * g.n3 * wz * cb > std::min<size_t>(lim, 100 * 1024) ||
+                    bfly(S.pz, (long long)nc * wz) > (long long)capz * kPer))
+    wz /= 2;
+  if ((size_t)nc * g.n3 * wz * cb > lim || bfly(S.pz, (long long)nc * wz) > (long long)capz * kPer) return false;
+  while (wz > 1 && wz / 2 >= g.H) wz /= 2;
+  a.z_w = wz;
+  a.z_smem = (size_t)nc * g.n3 * wz * cb;
+  a.z_threads = threads(bfly(S.pz, (long long)nc * wz), (long long)g.n3 * wz, capz);
+  return true;
+}
+
+template <typename T>
+struct Runner {
+  fftls_ctx* c;
+  const Setup& S;
+  IterArgs<T> a;
+  bool capturing = false;
+  int graph_kernels = 0;
+  Runner(fftls_ctx* c_, const Setup& S_) : c(c_), S(S_) { memset(&a, 0, sizeof(a)); }
+
+  int kernels_per_iter() const {
+    return 4 + (S.g.n2 > 1 ? 2 : 0) + (a.want_delta ? 1 : 0);
+  }
+
+  fftls_status launch(int kind, cudaError_t (*fn)(Runner*, cudaStream_t), bool prof) {
+    const int pi = Prec<T>::idx;
+    if (!capturing) c->launches += (kind == 1 || kind == 4) ? (S.g.n2 > 1) : 1;
+    if (prof) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, S.s);
+      cudaError_t e = fn(this, S.s);
+      cudaEventRecord(e1, S.s);
+      if (e != cudaSuccess) return set_err(c, FFTLS_E_CUDA, "kernel %s: %s", kKindNames[pi][kind], cudaGetErrorString(e));
+      c->ev.push_back({e0, e1, pi * kNumKinds + kind});
+      return FFTLS_OK;
+    }
+    cudaError_t e = fn(this, S.s);
+    if (e != cudaSuccess) return set_err(c, FFTLS_E_CUDA, "kernel %s: %s", kKindNames[pi][kind], cudaGetErrorString(e));
+    return FFTLS_OK;
+  }
+
+  fftls_status iteration(bool dual, int update, bool prof) {
+    a.dual = dual ? 1 : 0;
+    a.update = update;
+    fftls_status st;
+    if ((st = launch(0, [](Runner* r, cudaStream_t s) { return launch_fwd_x<T>(r->a, s); }, prof))) return st;
+    if ((st = launch(1, [](Runner* r, cudaStream_t s) {
+           return launch_mid_y<T>(r->a, r->a.dual ? 2 * ncomp(r->a.dim) : ncomp(r->a.dim), false, s);
+         }, prof)))
+      return st;
+    if ((st = launch(2, [](Runner* r, cudaStream_t s) { return launch_fourier_z<T>(r->a, s); }, prof))) return st;
+    if ((st = launch(3, [](Runner* r, cudaStream_t s) { return launch_reduce_eta<T>(r->a, s); }, prof))) return st;
+    if ((st = launch(4, [](Runner* r, cudaStream_t s) { return launch_mid_y<T>(r->a, ncomp(r->a.dim), true, s); },
+                     prof)))
+      return st;
+    if ((st = launch(5, [](Runner* r, cudaStream_t s) { return launch_inv_x<T>(r->a, s); }, prof))) return st;
+    if (a.want_delta)
+      if ((st = launch(6, [](Runner* r, cudaStream_t s) { return launch_reduce_delta<T>(r->a, s); }, prof)))
+        return st;
+    return FFTLS_OK;
+  }
+
+  fftls_status collect_profile() {
+    if (c->ev.empty()) return FFTLS_OK;
+    CUDA_TRY(c, cudaStreamSynchronize(S.s));
+    for (auto& e : c->ev) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e.a, e.b);
+      c->prof_ms[e.kind / kNumKinds][e.kind % kNumKinds] += ms;
+      c->prof_n[e.kind / kNumKinds][e.kind % kNumKinds] += 1;
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    c->ev.clear();
+    return FFTLS_OK;
+  }
+
+  // Run iterations until the device state leaves kRunning.
+  fftls_status run(Ctrl init, bool first_dual, bool dual, int update, int* final_state) {
+    CUDA_TRY(c, cudaMemcpyAsync(a.ctrl, &init, sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
+    fftls_status st;
+    if (first_dual && !dual) {
+      if ((st = iteration(true, kUpdDirectTau, S.profile))) return st;
+      if ((st = collect_profile())) return st;
+      CUDA_TRY(c, cudaMemcpyAsync(c->h_ctrl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
+      CUDA_TRY(c, cudaStreamSynchronize(S.s));
+      if (c->h_ctrl->state != kRunning) {
+        *final_state = c->h_ctrl->state;
+        return FFTLS_OK;
+      }
+    }
+    const long long N = S.g.N;
+    int chunk = (int)std::max<long long>(1, std::min<long long>(32, 40000000LL / std::max<long long>(N, 1)));
+    cudaGraphExec_t exec = nullptr;
+    if (S.graphs && !S.profile) {
+      a.dual = dual ? 1 : 0;
+      a.update = update;
+      GraphCache& gc = c->graphs[Prec<T>::idx];
+      std::vector<unsigned char> key(sizeof(a) + sizeof(int));
+      memcpy(key.data(), &a, sizeof(a));
+      memcpy(key.data() + sizeof(a), &chunk, sizeof(int));
+      if (gc.exec && gc.key == key) {
+        exec = gc.exec;
+      } else {
+        gc.release();
+        cudaGraph_t graph;
+        CUDA_TRY(c, cudaStreamBeginCapture(S.s, cudaStreamCaptureModeThreadLocal));
+        fftls_status cs = FFTLS_OK;
+        capturing = true;
+        for (int i = 0; i < chunk && cs == FFTLS_OK; ++i) cs = iteration(dual, update, false);
+        capturing = false;
+        cudaError_t ce = cudaStreamEndCapture(S.s, &graph);
+        if (cs) return cs;
+        CUDA_TRY(c, ce);
+        ce = cudaGraphInstantiate(&gc.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CUDA_TRY(c, ce);
+        gc.key = key;
+        exec = gc.exec;
+      }
+    }
+    for (;;) {
+      if (exec) {
+        CUDA_TRY(c, cudaGraphLaunch(exec, S.s));
+        c->graph_launches += 1;
+        c->launches += (long long)chunk * kernels_per_iter();
+      } else {
+        for (int i = 0; i < chunk; ++i)
+          if ((st = iteration(dual, update, S.profile))) return st;
+        if ((st = collect_profile())) return st;
+      }
+      CUDA_TRY(c, cudaMemcpyAsync(c->h_ctrl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
+      CUDA_TRY(c, cudaStreamSynchronize(S.s));
+      if (c->h_ctrl->state != kRunning) break;
+    }
+    *final_state = c->h_ctrl->state;
+    return FFTLS_OK;
+  }
+};
+
+template <typename T>
+fftls_status prepare(fftls_ctx* c, const Setup& S, const fftls_problem* p, const fftls_options* o, Runner<T>& R,
+                     T* eps) {
+  IterArgs<T>& a = R.a;
+  a.g = S.g;
+  a.dim = S.dim;
+  a.green = S.green;
+  a.px = S.px;
+  a.py = S.py;
+  a.pz = S.pz;
+  a.lam0 = S.lam0;
+  a.mu0 = S.mu0;
+  for (int i = 0; i < 6; ++i) a.eps_bar[i] = S.eps_bar[i];
+  if (!plan_launch<T>(c, S, a))
+    return set_err(c, FFTLS_E_UNSUPPORTED_SIZE, "grid %dx%dx%d does not fit the shared-memory tiles", S.g.n1, S.g.n2,
+                   S.g.n3);
+  const T* coef;
+  const void* tw[3];
+  const void* kt[3];
+  fftls_status st = upload_tables<T>(c, S, p, &coef, tw, kt);
+  if (st) return st;
+  a.coef = coef;
+  a.twx = (const typename Cplx<T>::type*)tw[0];
+  a.twy = (const typename Cplx<T>::type*)tw[1];
+  a.twz = (const typename Cplx<T>::type*)tw[2];
+  a.kx = (const KTab<T>*)kt[0];
+  a.ky = (const KTab<T>*)kt[1];
+  a.kz = (const KTab<T>*)kt[2];
+  a.eps = eps;
+  a.phase = S.d_phase;
+  a.spec = (typename Cplx<T>::type*)c->spec.p;
+  a.ctrl = (Ctrl*)c->ctrl.p;
+  a.part_mean = (double*)c->part_mean.p;
+  a.part_eta = (double*)c->part_eta.p;
+  a.part_delta = (double*)c->part_delta.p;
+  a.eta_hist = (double*)c->eta_hist.p;
+  a.ms_hist = (double*)c->ms_hist.p;
+  a.want_delta = o->stop == FFTLS_STOP_MAXDELTA ? 1 : 0;
+  // buffers sized by this phase's launch shapes
+  const int ntz = (S.g.H + a.z_w - 1) / a.z_w;
+  CUDA_TRY(c, c->part_mean.ensure((size_t)a.x1_blocks * 2 * S.nc * sizeof(double)));
+  CUDA_TRY(c, c->part_eta.ensure((size_t)ntz * S.g.n2 * 2 * sizeof(double)));
+  CUDA_TRY(c, c->part_delta.ensure((size_t)a.x5_blocks * 2 * sizeof(double)));
+  a.part_mean = (double*)c->part_mean.p;
+  a.part_eta = (double*)c->part_eta.p;
+  a.part_delta = (double*)c->part_delta.p;
+  CUDA_TRY(c, set_kernel_attributes<T>(a));
+  return FFTLS_OK;
+}
+
+void mandel_unit(int dim, int J, double* e) {
+  for (int i = 0; i < 6; ++i) e[i] = 0.0;
+  e[J] = J < dim ? 1.0 : 1.0 / sqrt(2.0);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void fftls_default_options(fftls_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->tol = 1e-8;
+  o->stop = FFTLS_STOP_ETA;
+  o->max_iter = 1000;
+  o->precision = FFTLS_FP64;
+  o->refine_switch = 0.0;
+  o->use_graphs = 1;
+}
+
+fftls_status fftls_create(fftls_ctx** out, int device) {
+  if (!out) return FFTLS_E_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FFTLS_E_CUDA;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return FFTLS_E_CUDA;
+  fftls_ctx* c = new fftls_ctx();
+  c->device = device;
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, device);
+  c->smem_optin = prop.sharedMemPerBlockOptin;
+  c->num_sms = prop.multiProcessorCount;
+  bool ok = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMallocHost((void**)&c->h_ctrl, sizeof(Ctrl)) == cudaSuccess &&
+            cudaMallocHost((void**)&c->h_sums, 64 * sizeof(double)) == cudaSuccess &&
+            c->ctrl.ensure(sizeof(Ctrl)) == cudaSuccess && c->sums.ensure(64 * sizeof(double)) == cudaSuccess;
+  memset(c->prof_ms, 0, sizeof(c->prof_ms));
+  memset(c->prof_n, 0, sizeof(c->prof_n));
+  cudaSetDevice(prev);
+  if (!ok) {
+    fftls_destroy(c);
+    return FFTLS_E_CUDA;
+  }
+  *out = c;
+  return FFTLS_OK;
+}
+
+void fftls_destroy(fftls_ctx* c) {
+  if (!c) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  for (auto& g : c->graphs) g.release();
+  DevBuf* bufs[] = {&c->phase, &c->eps32, &c->eps64, &c->spec, &c->coef32, &c->coef64, &c->tw32, &c->tw64,
+                    &c->kt32, &c->kt64, &c->part_mean, &c->part_eta, &c->part_delta, &c->sums, &c->ctrl,
+                    &c->eta_hist, &c->ms_hist, &c->scratch};
+  for (DevBuf* b : bufs) b->release();
+  for (auto& e : c->ev) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->h_sums) cudaFreeHost(c->h_sums);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  cudaSetDevice(prev);
+  delete c;
+}
+
+const char* fftls_last_error(const fftls_ctx* c) { return c ? c->err.c_str() : ""; }
+
+fftls_status fftls_counters(const fftls_ctx* c, long long* kernel_launches, long long* graph_launches) {
+  if (!c) return FFTLS_E_INVALID_ARG;
+  if (kernel_launches) *kernel_launches = c->launches;
+  if (graph_launches) *graph_launches = c->graph_launches;
+  return FFTLS_OK;
+}
+
+const char* fftls_status_string(fftls_status s) {
+  switch (s) {
+    case FFTLS_OK: return "FFTLS_OK";
+    case FFTLS_E_INVALID_ARG: return "FFTLS_E_INVALID_ARG";
+    case FFTLS_E_UNSUPPORTED_SIZE: return "FFTLS_E_UNSUPPORTED_SIZE";
+    case FFTLS_E_OOM: return "FFTLS_E_OOM";
+    case FFTLS_E_CUDA: return "FFTLS_E_CUDA";
+    case FFTLS_E_NOT_CONVERGED: return "FFTLS_E_NOT_CONVERGED";
+    case FFTLS_E_DIVERGED: return "FFTLS_E_DIVERGED";
+  }
+  return "unknown";
+}
+
+fftls_status fftls_supported_length(int L) {
+  AxisPlan p;
+  return factor_plan(L, &p) ? FFTLS_OK : FFTLS_E_UNSUPPORTED_SIZE;
+}
+
+fftls_status fftls_reference_medium(const fftls_problem* p, double* l0, double* m0) {
+  if (!p || !l0 || !m0 || (p->dim != 2 && p->dim != 3) || p->n_phases < 1 || !p->lambda || !p->mu)
+    return FFTLS_E_INVALID_ARG;
+  return default_medium(p, l0, m0) ? FFTLS_OK : FFTLS_E_INVALID_ARG;
+}
+
+fftls_status fftls_profile(const fftls_ctx* c, const char** names, double* total_ms, int* launches, int* count) {
+  if (!c || !count) return FFTLS_E_INVALID_ARG;
+  int n = 0;
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < kNumKinds; ++k) {
+      if (!c->prof_n[p][k]) continue;
+      if (n < *count) {
+        if (names) names[n] = kKindNames[p][k];
+        if (total_ms) total_ms[n] = c->prof_ms[p][k];
+        if (launches) launches[n] = c->prof_n[p][k];
+      }
+      ++n;
+    }
+  *count = n;
+  return FFTLS_OK;
+}
+
+static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls_options* o, fftls_result* r) {
+  fftls_status st = validate(c, p, o);
+  if (st) return st;
+  if (!r) return set_err(c, FFTLS_E_INVALID_ARG, "null result");
+  const int d = p->dim, nc = ncomp(d);
+  Setup S;
+  memset(&S, 0, sizeof(S));
+  S.dim = d;
+  S.nc = nc;
+  S.green = p->green;
+  S.scheme = p->scheme;
+  S.g.n1 = p->n[0];
+  S.g.n2 = p->n[1];
+  S.g.n3 = p->n[2];
+  S.g.H = p->n[0] / 2 + 1;
+  S.g.P = ((S.g.H + 15) / 16) * 16;
+  S.g.N = (long long)p->n[0] * p->n[1] * p->n[2];
+  S.g.CS = (long long)S.g.n3 * S.g.n2 * S.g.P;
+  factor_plan(S.g.n1, &S.px);
+  factor_plan(S.g.n2, &S.py);
+  factor_plan(S.g.n3, &S.pz);
+  if (isnan(p->lambda0)) default_medium(p, &S.lam0, &S.mu0);
+  else { S.lam0 = p->lambda0; S.mu0 = p->mu0; }
+  for (int i = 0; i < 6; ++i) S.eps_bar[i] = i < nc ? p->eps_bar[i] : 0.0;
+  S.s = o->stream ? (cudaStream_t)o->stream : c->stream;
+  S.profile = o->profile != 0;
+  S.graphs = o->use_graphs != 0;
+  const long long N = S.g.N;
+  if (S.profile) {
+    memset(c->prof_ms, 0, sizeof(c->prof_ms));
+    memset(c->prof_n, 0, sizeof(c->prof_n));
+  }
+  // phase image on the device, ids checked there (< n_phases)
+  if (p->phase_on_device) {
+    S.d_phase = p->phase;
+  } else {
+    CUDA_TRY(c, c->phase.ensure((size_t)N));
+    CUDA_TRY(c, cudaMemcpyAsync(c->phase.p, p->phase, (size_t)N, cudaMemcpyHostToDevice, S.s));
+    S.d_phase = (const uint8_t*)c->phase.p;
+  }
+  {
+    const int pb = (int)std::min<long long>((N + 255) / 256, (long long)c->num_sms * 8);
+    CUDA_TRY(c, launch_phase_max(S.d_phase, N, (unsigned int*)c->sums.p, pb, S.s));
+    c->launches += 1;
+    unsigned int pmax = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_sums, c->sums.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, S.s));
+    CUDA_TRY(c, cudaStreamSynchronize(S.s));
+    memcpy(&pmax, c->h_sums, sizeof(unsigned int));
+    if ((int)pmax >= p->n_phases)
+      return set_err(c, FFTLS_E_INVALID_ARG, "phase image holds id %u >= n_phases = %d", pmax, p->n_phases);
+  }
+  const bool use32 = o->precision != FFTLS_FP64;
+  const bool use64 = o->precision != FFTLS_FP32;
+  const int nout_max = 2 * nc;
+  const size_t spec_bytes = (size_t)nout_max * S.g.CS * (use64 ? 16 : 8);
+  CUDA_TRY(c, c->spec.ensure(spec_bytes));
+  if (use32) CUDA_TRY(c, c->eps32.ensure((size_t)nc * N * sizeof(float)));
+  if (use64 || o->eps_init) CUDA_TRY(c, c->eps64.ensure((size_t)nc * N * sizeof(double)));
+  CUDA_TRY(c, c->eta_hist.ensure((size_t)o->max_iter * sizeof(double)));
+  CUDA_TRY(c, c->ms_hist.ensure((size_t)o->max_iter * nc * sizeof(double)));
+  // initial field
+  const bool warm = o->eps_init != nullptr;
+  if (warm) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->eps64.p, o->eps_init, (size_t)nc * N * sizeof(double),
+                                o->eps_init_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S.s));
+    if (use32 && o->precision != FFTLS_FP64)
+      CUDA_TRY(c, launch_convert<float, double>((float*)c->eps32.p, (const double*)c->eps64.p, (long long)nc * N, S.s));
+  } else {
+    if (o->precision == FFTLS_FP64) CUDA_TRY(c, launch_fill_eps<double>((double*)c->eps64.p, nc, N, S.eps_bar, S.s));
+    else CUDA_TRY(c, launch_fill_eps<float>((float*)c->eps32.p, nc, N, S.eps_bar, S.s));
+    c->launches += 1;
+  }
+  const bool direct = p->scheme == FFTLS_DIRECT;
+  const int upd_steady = direct ? kUpdDirectSig : kUpdAccel;
+  const bool dual_steady = !direct;
+  Ctrl ctl;
+  memset(&ctl, 0, sizeof(ctl));
+  ctl.state = kRunning;
+  ctl.max_it = o->max_iter;
+  ctl.mean_guard = direct ? 0 : 1;
+  ctl.best = INFINITY;
+  int state = kRunning;
+  int it32 = 0;
+  bool final64 = o->precision == FFTLS_FP64;
+  if (use32) {
+    Runner<float> R32(c, S);
+    if ((st = prepare<float>(c, S, p, o, R32, (float*)c->eps32.p))) return st;
+    Ctrl c32 = ctl;
+    if (o->precision == FFTLS_FP32_REFINE64) {
+      c32.stop_rule = 0;
+      c32.tol = o->refine_switch > 0.0 ? o->refine_switch : o->tol;
+      c32.switch_mode = 1;
+      c32.stall_window = 32;
+      R32.a.want_delta = 0;
+    } else {
+      c32.stop_rule = o->stop;
+      c32.tol = o->tol;
+    }
+    if ((st = R32.run(c32, warm && direct, dual_steady, upd_steady, &state))) return st;
+    it32 = c->h_ctrl->it;
+    ctl = *c->h_ctrl;
+    if (o->precision == FFTLS_FP32_REFINE64 && state == kSwitch && ctl.it >= o->max_iter) {
+      state = kStopped;  // no budget left for the FP64 phase
+    } else if (o->precision == FFTLS_FP32_REFINE64 && state == kSwitch) {
+      CUDA_TRY(c, launch_convert<double, float>((double*)c->eps64.p, (const float*)c->eps32.p, (long long)nc * N, S.s));
+      final64 = true;
+    }
+  }
+  if (final64) {
+    Runner<double> R64(c, S);
+    if ((st = prepare<double>(c, S, p, o, R64, (double*)c->eps64.p))) return st;
+    Ctrl c64 = ctl;
+    c64.state = kRunning;
+    c64.stop_rule = o->stop;
+    c64.tol = o->tol;
+    c64.switch_mode = 0;
+    c64.stall_window = 0;
+    c64.stall = 0;
+    const bool from32 = o->precision == FFTLS_FP32_REFINE64;
+    if ((st = R64.run(c64, direct && (warm || from32), dual_steady, upd_steady, &state))) return st;
+  }
+  const Ctrl fin = *c->h_ctrl;
+  // outputs from the final field
+  const bool out64 = final64;
+  const void* epsf = out64 ? c->eps64.p : c->eps32.p;
+  const int sblocks = (int)std::min<long long>((N + 255) / 256, (long long)c->num_sms * 8);
+  CUDA_TRY(c, c->part_mean.ensure((size_t)sblocks * 2 * nc * sizeof(double)));
+  double* stress_dev = nullptr;
+  if (r->stress) {
+    if (o->fields_on_device) stress_dev = r->stress;
+    else {
+      CUDA_TRY(c, c->scratch.ensure((size_t)nc * N * sizeof(double)));
+      stress_dev = (double*)c->scratch.p;
+    }
+  }
+  // coefficient table of the final precision (already uploaded by prepare)
+  if (out64)
+    CUDA_TRY(c, launch_stress<double>((const double*)epsf, S.d_phase, (const double*)c->coef64.p, d, N, stress_dev,
+                                      (double*)c->part_mean.p, sblocks, S.s));
+  else
+    CUDA_TRY(c, launch_stress<float>((const float*)epsf, S.d_phase, (const float*)c->coef32.p, d, N, stress_dev,
+                                     (double*)c->part_mean.p, sblocks, S.s));
+  CUDA_TRY(c, launch_sum_parts((const double*)c->part_mean.p, sblocks, 2 * nc, (double*)c->sums.p, S.s));
+  c->launches += 2;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_sums, c->sums.p, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, S.s));
+  if (r->stress && !o->fields_on_device)
+    CUDA_TRY(c, cudaMemcpyAsync(r->stress, stress_dev, (size_t)nc * N * sizeof(double), cudaMemcpyDeviceToHost, S.s));
+  if (r->strain) {
+    const cudaMemcpyKind kind = o->fields_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (out64) {
+      CUDA_TRY(c, cudaMemcpyAsync(r->strain, epsf, (size_t)nc * N * sizeof(double), kind, S.s));
+    } else if (o->fields_on_device) {
+      CUDA_TRY(c, launch_convert<double, float>(r->strain, (const float*)epsf, (long long)nc * N, S.s));
+    } else {
+      CUDA_TRY(c, c->scratch.ensure((size_t)nc * N * sizeof(double)));
+      CUDA_TRY(c, launch_convert<double, float>((double*)c->scratch.p, (const float*)epsf, (long long)nc * N, S.s));
+      CUDA_TRY(c, cudaMemcpyAsync(r->strain, c->scratch.p, (size_t)nc * N * sizeof(double), kind, S.s));
+    }
+  }
+  const int hl = std::min(fin.it, r->history_capacity);
+  if (r->eta_history && hl > 0)
+    CUDA_TRY(c, cudaMemcpyAsync(r->eta_history, c->eta_hist.p, (size_t)hl * sizeof(double), cudaMemcpyDeviceToHost, S.s));
+  if (r->mean_stress_history && hl > 0)
+    CUDA_TRY(c, cudaMemcpyAsync(r->mean_stress_history, c->ms_hist.p, (size_t)hl * nc * sizeof(double),
+                                cudaMemcpyDeviceToHost, S.s));
+  CUDA_TRY(c, cudaStreamSynchronize(S.s));
+  for (int i = 0; i < 6; ++i) {
+    r->mean_stress[i] = i < nc ? c->h_sums[i] / (double)N : 0.0;
+    r->mean_strain[i] = i < nc ? c->h_sums[nc + i] / (double)N : 0.0;
+  }
+  r->iterations = fin.it;
+  r->iterations_fp32 = it32;
+  r->final_eta = fin.last_eta;
+  r->final_delta = fin.last_delta;
+  r->history_len = hl;
+  if (state == kConverged) return FFTLS_OK;
+  if (state == kDiverged) return set_err(c, FFTLS_E_DIVERGED, "diverged: eta = %g after %d iterations", fin.last_eta, fin.it);
+  return set_err(c, FFTLS_E_NOT_CONVERGED, "not converged after %d iterations (eta = %g)", fin.it, fin.last_eta);
+}
+
+fftls_status fftls_solve(fftls_ctx* c, const fftls_problem* p, const fftls_options* o, fftls_result* r) {
+  if (!c) return FFTLS_E_INVALID_ARG;
+  c->err.clear();
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, FFTLS_E_CUDA, "cannot select device %d", c->device);
+  fftls_status s = solve_impl(c, p, o, r);
+  cudaSetDevice(prev);
+  return s;
+}
+
+fftls_status fftls_effective_stiffness(fftls_ctx* c, const fftls_problem* p, const fftls_options* o, double* C_eff,
+                                       int* iterations) {
+  if (!c || !p || !o || !C_eff) return set_err(c, FFTLS_E_INVALID_ARG, "null argument");
+  if (p->dim != 2 && p->dim != 3) return set_err(c, FFTLS_E_INVALID_ARG, "dim must be 2 or 3");
+  const int nc = ncomp(p->dim);
+  fftls_problem q = *p;
+  fftls_status worst = FFTLS_OK;
+  for (int J = 0; J < nc; ++J) {
+    mandel_unit(p->dim, J, q.eps_bar);
+    fftls_result r;
+    memset(&r, 0, sizeof(r));
+    fftls_status s = fftls_solve(c, &q, o, &r);
+    if (s != FFTLS_OK && s != FFTLS_E_NOT_CONVERGED && s != FFTLS_E_DIVERGED) return s;
+    if (s != FFTLS_OK && worst == FFTLS_OK) worst = s;
+    for (int I = 0; I < nc; ++I) C_eff[I * nc + J] = r.mean_stress[I] * (I < p->dim ? 1.0 : sqrt(2.0));
+    if (iterations) iterations[J] = r.iterations;
+  }
+  return worst;
+}
+
+}  // extern "C"

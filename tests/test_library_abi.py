@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads and exports every function of include/fftls.h.
+
+Runs without a GPU: only host-side entry points are called.
+"""
+import math
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fftls.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fftls_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1412_8398_gb300 import build, fftls
+    build.build()
+    return fftls.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["fftls_create", "fftls_destroy", "fftls_solve", "fftls_effective_stiffness",
+                     "fftls_reference_medium", "fftls_last_error"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_signatures_cover_header(lib):
+    from paper_1412_8398_gb300 import fftls
+    assert set(_declared_functions()) == set(fftls._SIGNATURES)
+
+
+def test_host_only_calls(lib):
+    from paper_1412_8398_gb300 import fftls
+    assert fftls.supported_length(512) and fftls.supported_length(96) and fftls.supported_length(1)
+    assert fftls.supported_length(48) and fftls.supported_length(5) and fftls.supported_length(1000)
+    assert not fftls.supported_length(7) and not fftls.supported_length(2048) and not fftls.supported_length(0)
+    l0, m0 = fftls.reference_medium([0.6, 600.0], [0.6, 600.0], 3, "AS")
+    assert abs(m0 - math.sqrt(0.6 * 600.0)) < 1e-12 and abs(l0 + 2 * m0 / 3 - math.sqrt(1000.0)) < 1e-12
+    l0, m0 = fftls.reference_medium([0.4, 4.0], [0.6, 6.0], 2, "DS")
+    assert abs(m0 - 3.3) < 1e-14 and abs(l0 + m0 - 5.5) < 1e-14
+    with pytest.raises(fftls.FftlsError):
+        fftls.reference_medium([0.6, 0.0], [0.6, 0.0], 3, "AS")   # porous: default degenerates
+    assert lib.fftls_status_string(5) == b"FFTLS_E_NOT_CONVERGED"
