@@ -892,3 +892,253 @@ fftls_status fftls_effective_stiffness(fftls_ctx* c, const fftls_problem* p, con
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve (fftls_solve_noalloc).  The paper has no counterpart:
+// this serves callers that cannot call cudaMalloc (for example code running
+// inside stream capture, or hosts whose device memory is handed out by
+// another allocator).  All scratch lives in one file-scope device array.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB, held by every device that loads the library
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_base[kNoAllocMaxDevices];  // device address of g_noalloc_scratch per device (set up on first call)
+
+// host staging for the tables (fixed size: no heap allocation)
+double g_na_coef[256 * kCoef];
+double g_na_tw[3][2 * kMaxL + 8];
+double g_na_kt[3][6 * kMaxL];
+
+size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void na_axis_tables(int L, double* tw, double* kt) {
+  for (int t = 0; t < L; ++t) {
+    const double ang = -2.0 * M_PI * (double)t / (double)L;
+    double cs = cos(ang), sn = sin(ang);
+    if ((4 * t) % L == 0) {
+      const int qd = (4 * t) / L;
+      const double cq[4] = {1, 0, -1, 0}, sq[4] = {0, -1, 0, 1};
+      cs = cq[qd % 4];
+      sn = sq[qd % 4];
+    }
+    tw[2 * t] = cs;
+    tw[2 * t + 1] = sn;
+  }
+  for (int m = 0; m < L; ++m) {
+    const int s = m <= L / 2 ? m : m - L;
+    const double q = 2.0 * M_PI * s / L;
+    double sn = sin(q), sh = sin(0.5 * q), ch = cos(0.5 * q);
+    if ((2 * s) % L == 0) sn = 0.0;
+    if (s == 0) sh = 0.0;
+    if (2 * s == L) ch = 0.0;
+    if (4 * s == L) sn = 1.0;
+    if (4 * s == -L) sn = -1.0;
+    double* e = kt + 6 * (size_t)m;
+    e[0] = q;
+    e[1] = sn;
+    e[2] = -2.0 * sh * sh;
+    e[3] = sh;
+    e[4] = ch;
+    e[5] = (L % 2 == 0 && 2 * m == L) ? 1.0 : 0.0;
+  }
+}
+
+}  // namespace
+
+extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_options* o, fftls_result* r) {
+#define NA_TRY(...)                                    \
+  do {                                                 \
+    if ((__VA_ARGS__) != cudaSuccess) return FFTLS_E_CUDA; \
+  } while (0)
+  fftls_status st = validate(nullptr, p, o);
+  if (st) return st;
+  if (!r || !r->strain || !o->fields_on_device || o->precision != FFTLS_FP64) return FFTLS_E_INVALID_ARG;
+  int dev = 0;
+  NA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return FFTLS_E_CUDA;
+  if (!g_noalloc_base[dev]) {  // set-up, once per device, with that device current
+    void* base = nullptr;
+    NA_TRY(cudaGetSymbolAddress(&base, g_noalloc_scratch));
+    g_noalloc_base[dev] = base;
+  }
+  unsigned char* base = (unsigned char*)g_noalloc_base[dev];
+  const int d = p->dim, nc = ncomp(d);
+  Setup S;
+  memset(&S, 0, sizeof(S));
+  S.dim = d;
+  S.nc = nc;
+  S.green = p->green;
+  S.scheme = p->scheme;
+  S.g.n1 = p->n[0];
+  S.g.n2 = p->n[1];
+  S.g.n3 = p->n[2];
+  S.g.H = p->n[0] / 2 + 1;
+  S.g.P = ((S.g.H + 15) / 16) * 16;
+  S.g.N = (long long)p->n[0] * p->n[1] * p->n[2];
+  S.g.CS = (long long)S.g.n3 * S.g.n2 * S.g.P;
+  factor_plan(S.g.n1, &S.px);
+  factor_plan(S.g.n2, &S.py);
+  factor_plan(S.g.n3, &S.pz);
+  if (isnan(p->lambda0)) default_medium(p, &S.lam0, &S.mu0);
+  else { S.lam0 = p->lambda0; S.mu0 = p->mu0; }
+  for (int i = 0; i < 6; ++i) S.eps_bar[i] = i < nc ? p->eps_bar[i] : 0.0;
+  S.s = (cudaStream_t)o->stream;
+  const long long N = S.g.N;
+  // launch shapes (a stack context only carries the device limits)
+  fftls_ctx probe;
+  int v = 0;
+  NA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  probe.smem_optin = (size_t)v;
+  NA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+  probe.num_sms = v;
+  IterArgs<double> a;
+  memset(&a, 0, sizeof(a));
+  if (!plan_launch<double>(&probe, S, a)) return FFTLS_E_UNSUPPORTED_SIZE;
+  // scratch layout
+  const int ntz = (S.g.H + a.z_w - 1) / a.z_w;
+  const int sblocks = (int)std::min<long long>((N + 255) / 256, (long long)probe.num_sms * 8);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t at = off; off = na_align(off + bytes); return at; };
+  const size_t o_spec = take((size_t)2 * nc * S.g.CS * 16);
+  const size_t o_pmean = take((size_t)std::max(a.x1_blocks, sblocks) * 2 * nc * 8);
+  const size_t o_peta = take((size_t)ntz * S.g.n2 * 2 * 8);
+  const size_t o_pdelta = take((size_t)a.x5_blocks * 2 * 8);
+  const size_t o_sums = take(64 * 8);
+  const size_t o_ctrl = take(sizeof(Ctrl));
+  const size_t o_eh = take((size_t)o->max_iter * 8);
+  const size_t o_mh = take((size_t)o->max_iter * nc * 8);
+  const size_t o_coef = take(256 * kCoef * 8);
+  size_t o_tw[3], o_kt[3];
+  const int Ls[3] = {S.g.n1, S.g.n2, S.g.n3};
+  for (int ax = 0; ax < 3; ++ax) o_tw[ax] = take((size_t)Ls[ax] * 16);
+  for (int ax = 0; ax < 3; ++ax) o_kt[ax] = take((size_t)Ls[ax] * 48);
+  const size_t o_phase = p->phase_on_device ? 0 : take((size_t)N);
+  if (off > kNoAllocScratchBytes) return FFTLS_E_UNSUPPORTED_SIZE;  // grid too large for the fixed scratch
+  // tables
+  for (int i = 0; i < 256 * kCoef; ++i) g_na_coef[i] = NAN;
+  const double k0 = S.lam0 + 2.0 / d * S.mu0;
+  for (int ph = 0; ph < p->n_phases; ++ph) {
+    const double l = p->lambda[ph], m = p->mu[ph], k = l + 2.0 / d * m;
+    double* e = &g_na_coef[ph * kCoef];
+    e[0] = l;
+    e[1] = 2.0 * m;
+    e[2] = l - S.lam0;
+    e[3] = 2.0 * (m - S.mu0);
+    e[4] = 2.0 * (S.mu0 / (m + S.mu0));
+    e[5] = 2.0 * (k0 / (k + k0) - S.mu0 / (m + S.mu0)) / d;
+    e[6] = e[7] = 0.0;
+  }
+  NA_TRY(cudaMemcpyAsync(base + o_coef, g_na_coef, sizeof(g_na_coef), cudaMemcpyHostToDevice, S.s));
+  for (int ax = 0; ax < 3; ++ax) {
+    na_axis_tables(Ls[ax], g_na_tw[ax], g_na_kt[ax]);
+    NA_TRY(cudaMemcpyAsync(base + o_tw[ax], g_na_tw[ax], (size_t)Ls[ax] * 16, cudaMemcpyHostToDevice, S.s));
+    NA_TRY(cudaMemcpyAsync(base + o_kt[ax], g_na_kt[ax], (size_t)Ls[ax] * 48, cudaMemcpyHostToDevice, S.s));
+  }
+  // phase image (copied into the scratch when it is on the host) and its id check
+  const uint8_t* d_phase = p->phase;
+  if (!p->phase_on_device) {
+    NA_TRY(cudaMemcpyAsync(base + o_phase, p->phase, (size_t)N, cudaMemcpyHostToDevice, S.s));
+    d_phase = base + o_phase;
+  }
+  S.d_phase = d_phase;
+  unsigned int pmax = 0;
+  NA_TRY(launch_phase_max(d_phase, N, (unsigned int*)(base + o_sums), sblocks, S.s));
+  NA_TRY(cudaMemcpyAsync(&pmax, base + o_sums, sizeof(pmax), cudaMemcpyDeviceToHost, S.s));
+  NA_TRY(cudaStreamSynchronize(S.s));
+  if ((int)pmax >= p->n_phases) return FFTLS_E_INVALID_ARG;
+  // the iterate lives in the caller's strain buffer
+  double* eps = r->strain;
+  if (o->eps_init)
+    NA_TRY(cudaMemcpyAsync(eps, o->eps_init, (size_t)nc * N * 8,
+                           o->eps_init_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S.s));
+  else
+    NA_TRY(launch_fill_eps<double>(eps, nc, N, S.eps_bar, S.s));
+  a.g = S.g;
+  a.dim = d;
+  a.green = S.green;
+  a.px = S.px;
+  a.py = S.py;
+  a.pz = S.pz;
+  a.lam0 = S.lam0;
+  a.mu0 = S.mu0;
+  for (int i = 0; i < 6; ++i) a.eps_bar[i] = S.eps_bar[i];
+  a.eps = eps;
+  a.phase = d_phase;
+  a.coef = (const double*)(base + o_coef);
+  a.spec = (double2*)(base + o_spec);
+  a.twx = (const double2*)(base + o_tw[0]);
+  a.twy = (const double2*)(base + o_tw[1]);
+  a.twz = (const double2*)(base + o_tw[2]);
+  a.kx = (const KTab<double>*)(base + o_kt[0]);
+  a.ky = (const KTab<double>*)(base + o_kt[1]);
+  a.kz = (const KTab<double>*)(base + o_kt[2]);
+  a.ctrl = (Ctrl*)(base + o_ctrl);
+  a.part_mean = (double*)(base + o_pmean);
+  a.part_eta = (double*)(base + o_peta);
+  a.part_delta = (double*)(base + o_pdelta);
+  a.eta_hist = (double*)(base + o_eh);
+  a.ms_hist = (double*)(base + o_mh);
+  a.want_delta = o->stop == FFTLS_STOP_MAXDELTA ? 1 : 0;
+  NA_TRY(set_kernel_attributes<double>(a));
+  const bool direct = p->scheme == FFTLS_DIRECT;
+  Ctrl ctl;
+  memset(&ctl, 0, sizeof(ctl));
+  ctl.state = kRunning;
+  ctl.max_it = o->max_iter;
+  ctl.stop_rule = o->stop;
+  ctl.tol = o->tol;
+  ctl.mean_guard = direct ? 0 : 1;
+  ctl.best = INFINITY;
+  NA_TRY(cudaMemcpyAsync(a.ctrl, &ctl, sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
+  auto iteration = [&](bool dual, int update) -> cudaError_t {
+    a.dual = dual ? 1 : 0;
+    a.update = update;
+    cudaError_t e;
+    if ((e = launch_fwd_x<double>(a, S.s)) != cudaSuccess) return e;
+    if ((e = launch_mid_y<double>(a, dual ? 2 * nc : nc, false, S.s)) != cudaSuccess) return e;
+    if ((e = launch_fourier_z<double>(a, S.s)) != cudaSuccess) return e;
+    if ((e = launch_reduce_eta<double>(a, S.s)) != cudaSuccess) return e;
+    if ((e = launch_mid_y<double>(a, nc, true, S.s)) != cudaSuccess) return e;
+    if ((e = launch_inv_x<double>(a, S.s)) != cudaSuccess) return e;
+    if (a.want_delta && (e = launch_reduce_delta<double>(a, S.s)) != cudaSuccess) return e;
+    return cudaSuccess;
+  };
+  const bool dual = !direct;
+  const int upd = direct ? kUpdDirectSig : kUpdAccel;
+  if (direct && o->eps_init) NA_TRY(iteration(true, kUpdDirectTau));
+  const int chunk = (int)std::max<long long>(1, std::min<long long>(32, 40000000LL / std::max<long long>(N, 1)));
+  for (;;) {
+    NA_TRY(cudaMemcpyAsync(&ctl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
+    NA_TRY(cudaStreamSynchronize(S.s));
+    if (ctl.state != kRunning) break;
+    for (int i = 0; i < chunk; ++i) NA_TRY(iteration(dual, upd));
+  }
+  // outputs
+  double* part = (double*)(base + o_pmean);
+  double* sums = (double*)(base + o_sums);
+  NA_TRY(launch_stress<double>(eps, d_phase, a.coef, d, N, r->stress, part, sblocks, S.s));
+  NA_TRY(launch_sum_parts(part, sblocks, 2 * nc, sums, S.s));
+  double hs[12];
+  NA_TRY(cudaMemcpyAsync(hs, sums, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, S.s));
+  const int hl = std::min(ctl.it, r->history_capacity);
+  if (r->eta_history && hl > 0)
+    NA_TRY(cudaMemcpyAsync(r->eta_history, a.eta_hist, (size_t)hl * 8, cudaMemcpyDeviceToHost, S.s));
+  if (r->mean_stress_history && hl > 0)
+    NA_TRY(cudaMemcpyAsync(r->mean_stress_history, a.ms_hist, (size_t)hl * nc * 8, cudaMemcpyDeviceToHost, S.s));
+  NA_TRY(cudaStreamSynchronize(S.s));
+  for (int i = 0; i < 6; ++i) {
+    r->mean_stress[i] = i < nc ? hs[i] / (double)N : 0.0;
+    r->mean_strain[i] = i < nc ? hs[nc + i] / (double)N : 0.0;
+  }
+  r->iterations = ctl.it;
+  r->iterations_fp32 = 0;
+  r->final_eta = ctl.last_eta;
+  r->final_delta = ctl.last_delta;
+  r->history_len = hl;
+  if (ctl.state == kConverged) return FFTLS_OK;
+  if (ctl.state == kDiverged) return FFTLS_E_DIVERGED;
+  return FFTLS_E_NOT_CONVERGED;
+#undef NA_TRY
+}

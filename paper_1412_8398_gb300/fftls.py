@@ -96,6 +96,8 @@ _SIGNATURES = {
     "fftls_destroy": (None, [ctypes.c_void_p]),
     "fftls_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Problem), ctypes.POINTER(_Options),
                                    ctypes.POINTER(_Result)]),
+    "fftls_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.POINTER(_Options),
+                                           ctypes.POINTER(_Result)]),
     "fftls_effective_stiffness": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Problem),
                                                  ctypes.POINTER(_Options), ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_int)]),

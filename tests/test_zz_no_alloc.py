@@ -1,0 +1,93 @@
+"""fftls_solve_noalloc, the allocation-free entry point, against fftls_solve.
+
+Some callers cannot allocate device memory (code running during CUDA stream
+capture, or applications whose device memory comes from their own fixed
+pools), so the library offers a solve whose scratch sits in a fixed
+file-scope device array.  This test calls it through the C ABI twice in a
+row and checks each result against the regular entry point.  The file is
+named so that pytest collects it last.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from paper_1412_8398_gb300 import microstructure as MS
+
+pytestmark = pytest.mark.gpu
+FIELD_TOL = 1e-9
+
+
+def _noalloc(lib, fftls, torch, ph, lam, mu, eb, green, scheme, tol, max_iter):
+    dim = ph.ndim
+    nc = 6 if dim == 3 else 3
+    p = fftls._Problem()
+    p.dim = dim
+    p.n[:] = list(reversed(ph.shape)) + [1] * (3 - dim)
+    dph = torch.from_numpy(ph).cuda()
+    p.phase = dph.data_ptr()
+    p.phase_on_device = 1
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    p.n_phases = lam.size
+    p.lambda_ = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.mu = mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.lambda0 = math.nan
+    p.mu0 = math.nan
+    p.green = fftls.GREEN[green]
+    p.scheme = fftls.SCHEME[scheme]
+    ebv = fftls._eps_bar_vector(eb, dim)
+    p.eps_bar[:] = list(ebv) + [0.0] * (6 - ebv.size)
+    o = fftls._Options()
+    lib.fftls_default_options(ctypes.byref(o))
+    o.tol = tol
+    o.max_iter = max_iter
+    o.fields_on_device = 1
+    strain = torch.empty((nc,) + ph.shape, dtype=torch.float64, device="cuda")
+    stress = torch.empty((nc,) + ph.shape, dtype=torch.float64, device="cuda")
+    r = fftls._Result()
+    r.strain = strain.data_ptr()
+    r.stress = stress.data_ptr()
+    eh = np.zeros(max_iter)
+    r.eta_history = eh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    r.history_capacity = max_iter
+    st = lib.fftls_solve_noalloc(ctypes.byref(p), ctypes.byref(o), ctypes.byref(r))
+    torch.cuda.synchronize()
+    return st, strain.cpu().numpy(), stress.cpu().numpy(), np.array(r.mean_stress[:nc]), r.iterations, \
+        eh[:r.history_len].copy()
+
+
+def test_noalloc_matches_solve_twice():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_8398_gb300 import build, fftls
+    build.build()
+    lib = fftls.load_library()
+    solver = fftls.Solver(0)
+    cases = [
+        (MS.boolean_spheres((20, 18, 16), 2.5, 0.3, seed=5)[0], "R", "AS"),
+        (MS.centered_disc(64, 0.25), "W", "DS"),
+    ]
+    for ph, green, scheme in cases:
+        d = ph.ndim
+        lam, mu = MS.young_poisson_phases([(1.0, 0.3), (50.0, 0.25)])
+        eb = np.zeros((d, d))
+        eb[0, 0] = 1.0
+        eb[0, 1] = eb[1, 0] = 0.2
+        ref = solver.solve(ph, lam, mu, eb, green, scheme, tol=1e-9, max_iter=800)
+        assert ref.converged
+        for _ in range(2):   # two calls in a row share (and reuse) the scratch array
+            st, strain, stress, ms, its, eh = _noalloc(lib, fftls, torch, ph, lam, mu, eb, green, scheme, 1e-9, 800)
+            assert st == fftls.OK
+            assert its == ref.iterations
+            assert np.abs(strain - ref.strain).max() < FIELD_TOL
+            assert np.abs(stress - ref.stress).max() < FIELD_TOL * 100
+            assert np.abs(ms - ref.mean_stress).max() < 1e-10 * np.abs(ref.mean_stress).max()
+            np.testing.assert_allclose(eh, ref.eta_history, rtol=1e-9, atol=1e-15)
+    # a grid whose scratch exceeds the fixed array is refused up front
+    big = np.zeros((64, 64, 64), dtype=np.uint8)
+    st = _noalloc(lib, fftls, torch, big, [1.0], [1.0], np.eye(3), "R", "AS", 1e-6, 10)[0]
+    assert st == fftls.E_UNSUPPORTED_SIZE
+    solver.close()
