@@ -1,18 +1,20 @@
-// Shared-memory mixed-radix Stockham FFT building blocks (sm_103a).
+// Shared-memory mixed-radix FFT building blocks (sm_103a).
 //
 // Transforms follow the paper's DFT convention (Sec. 3, eq. ft2 / ft):
 // forward X[m] = sum_n x[n] e^{-2 pi i m n / L} (unnormalised), inverse with
 // the opposite sign and no scaling here (the 1/N of eq. ft is folded into the
 // Fourier-space kernel).
 //
-// A batch of lines lives in shared memory.  Line l starts at
-//   base(l) = (l / W) * SA + (l % W) * SB
-// and its element e sits at base(l) + e * ES.  One Stockham stage of radix R
-// with Ns = product of the radices already applied reads element j + r L/R,
-// multiplies by the twiddle W_{Ns R}^{(j mod Ns) r}, runs an R-point DFT in
-// registers and writes element (j / Ns) Ns R + (j mod Ns) + r Ns.  Every
-// thread first loads all its butterflies, the block synchronises, then all
-// threads store: the transform runs in place.
+// Tiles live in shared memory as [block][row e][column c]: element (b, e, c)
+// sits at b * BS + e * C + c; the transform runs along e (length L) for every
+// column c < ncols of every block.  The forward transform is an in-place
+// decimation in frequency: natural order in, digit-reversed order out (position
+// p holds frequency perm(p), see AxisPlan).  The inverse is the matching
+// decimation in time: digit-reversed in, natural order out.  Each butterfly
+// reads and writes the same R locations, so a stage needs no buffering across
+// threads and a block may loop over any number of butterflies; one
+// __syncthreads() separates stages.  The spectrum is never reordered: the
+// Fourier-space kernel maps positions to frequencies through per-axis tables.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -21,12 +23,15 @@ namespace fftls {
 
 constexpr int kMaxStages = 12;
 constexpr int kMaxRadix = 8;
-constexpr int kPer = 2;  // butterflies per thread per stage (host sizes blocks for this)
 
+// Stage s (s = 0 first in the forward transform) has radix radix[s] and acts on
+// sub-sequences of length msize[s] = L / (radix[0] ... radix[s-1]).  Position
+// p = s_0 L/R_0 + s_1 L/(R_0 R_1) + ... holds frequency s_0 + R_0 (s_1 + R_1 (...)).
 struct AxisPlan {
-  int L;                    // transform length
-  int nst;                  // number of stages
-  int radix[kMaxStages];    // radix of each stage, applied in order
+  int L;
+  int nst;
+  int radix[kMaxStages];
+  int msize[kMaxStages];
 };
 
 template <typename T> struct Cplx;
@@ -37,12 +42,15 @@ template <typename T2> __device__ __forceinline__ T2 cmk(decltype(T2::x) a, decl
 template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return cmk<T2>(a.x + b.x, a.y + b.y); }
 template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return cmk<T2>(a.x - b.x, a.y - b.y); }
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) { return cmk<T2>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// a * conj(b)
+template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b) { return cmk<T2>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }
 template <typename T2> __device__ __forceinline__ T2 cconj(T2 a) { return cmk<T2>(a.x, -a.y); }
 template <typename T2> __device__ __forceinline__ T2 cscale(T2 a, decltype(T2::x) s) { return cmk<T2>(a.x * s, a.y * s); }
 // multiply by -i (forward) or +i (inverse)
 template <typename T2> __device__ __forceinline__ T2 cmul_mi(T2 a, bool inv) { return inv ? cmk<T2>(-a.y, a.x) : cmk<T2>(a.y, -a.x); }
 
-// R-point DFTs in registers. Sign of the exponent: -1 forward, +1 inverse.
+// R-point DFTs in registers, output in natural order.  Exponent sign -1
+// forward, +1 inverse.
 template <typename T2>
 __device__ __forceinline__ void dft2(T2* v) {
   T2 a = v[0], b = v[1];
@@ -68,7 +76,7 @@ __device__ __forceinline__ void dft8(T2* v, bool inv) {
   T2 o[4] = {v[1], v[3], v[5], v[7]};
   dft4(e, inv);
   dft4(o, inv);
-  // twiddles w8^s, s = 0..3: 1, (1 -+ i)/sqrt2, -+i, (-1 -+ i)/sqrt2
+  // o[s] * w8^s, w8 = e^{-+ i pi / 4}
   T2 t1 = inv ? cmk<T2>(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
               : cmk<T2>(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
   T2 t2 = cmul_mi(o[2], inv);
@@ -92,7 +100,7 @@ __device__ __forceinline__ void dft3(T2* v, bool inv) {
   T2 b = csub(v[1], v[2]);
   T2 y0 = cadd(v[0], a);
   T2 t = cmk<T2>(v[0].x - (T)0.5 * a.x, v[0].y - (T)0.5 * a.y);
-  T2 u = cmul_mi(cscale(b, s3), inv);  // -i s3 b (forward)
+  T2 u = cmul_mi(cscale(b, s3), inv);
   v[0] = y0;
   v[1] = cadd(t, u);
   v[2] = csub(t, u);
@@ -131,60 +139,51 @@ __device__ __forceinline__ void dft_r(T2* v, int R, bool inv) {
   }
 }
 
-// In-place batched FFT of `nlines` lines of length p.L held in shared memory.
-// tw[t] = e^{-2 pi i t / L}, t = 0 .. L-1 (global memory, read through L1).
-// Requires nlines * L / min_radix <= kPer * blockDim.x (checked on the host).
+// In-place transform of a tile (see the file comment).  tw[t] = e^{-2 pi i t / L}
+// (shared memory).  Ends with __syncthreads().
 template <typename T2>
-__device__ void smem_fft(T2* buf, const AxisPlan& p, int nlines, int W, int SA, int SB, int ES,
-                         const T2* __restrict__ tw, bool inv) {
+__device__ void tile_fft(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv) {
   const int L = p.L;
-  const int nthr = blockDim.x;
-  const int tid = threadIdx.x;
-  int Ns = 1;
-  for (int s = 0; s < p.nst; ++s) {
+  for (int si = 0; si < p.nst; ++si) {
+    const int s = inv ? p.nst - 1 - si : si;
     const int R = p.radix[s];
+    const int M = p.msize[s];
+    const int MR = M / R;
+    const int tstr = L / M;
     const int nb = L / R;
-    const int total = nlines * nb;
-    const int twstride = L / (Ns * R);
-    T2 v[kPer][kMaxRadix];
-    int dst[kPer];
+    const int total = nblk * nb * ncols;
+    const int rs = MR * C;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int c = idx % ncols;
+      const int rest = idx / ncols;
+      const int bf = rest % nb;
+      const int blk = rest / nb;
+      const int b = bf / MR, j = bf - b * MR;
+      T2* base = buf + blk * BS + (b * M + j) * C + c;
+      T2 v[kMaxRadix];
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int idx = tid + q * nthr;
-      dst[q] = -1;
-      if (idx < total) {
-        const int line = idx / nb;
-        const int j = idx - line * nb;
-        const int base = (line / W) * SA + (line % W) * SB;
-        const int k = j % Ns;
+      for (int r = 0; r < kMaxRadix; ++r)
+        if (r < R) v[r] = base[r * rs];
+      if (!inv) {
+        dft_r(v, R, false);
+        if (j) {
 #pragma unroll
-        for (int r = 0; r < kMaxRadix; ++r)
-          if (r < R) v[q][r] = buf[base + (j + r * nb) * ES];
-        if (Ns > 1) {
-#pragma unroll
-          for (int r = 1; r < kMaxRadix; ++r) {
-            if (r < R) {
-              T2 w = __ldg(&tw[k * r * twstride]);
-              if (inv) w.y = -w.y;
-              v[q][r] = cmul(v[q][r], w);
-            }
-          }
+          for (int r = 1; r < kMaxRadix; ++r)
+            if (r < R) v[r] = cmul(v[r], tw[j * r * tstr]);
         }
-        dft_r(v[q], R, inv);
-        dst[q] = base + ((j / Ns) * Ns * R + k) * ES;
+      } else {
+        if (j) {
+#pragma unroll
+          for (int r = 1; r < kMaxRadix; ++r)
+            if (r < R) v[r] = cmulc(v[r], tw[j * r * tstr]);
+        }
+        dft_r(v, R, true);
       }
+#pragma unroll
+      for (int r = 0; r < kMaxRadix; ++r)
+        if (r < R) base[r * rs] = v[r];
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      if (dst[q] >= 0) {
-#pragma unroll
-        for (int r = 0; r < kMaxRadix; ++r)
-          if (r < R) buf[dst[q] + r * Ns * ES] = v[q][r];
-      }
-    }
-    __syncthreads();
-    Ns *= R;
   }
 }
 

@@ -2,18 +2,21 @@
 //
 // One iteration is five passes over the fields in HBM:
 //   K1 fwd_x     : sigma = C(x):eps (and tau = sigma - C0:eps) per voxel,
-//                  fused with the x1 real-to-complex transform; FP64 sums of
-//                  <sigma>, <eps>                            (eq. ls, a1)
-//   K2 mid_y     : complex transform along x2 (forward)
+//                  fused with the x1 real-to-half-complex transform; FP64 sums
+//                  of <sigma>, <eps>                          (eq. ls, a1)
+//   K2 mid_y     : transform along x2 (forward)
 //   K3 fourier_z : transform along x3, then per mode the equilibrium norm
 //                  |k* . sigma_hat|^2 and e_hat = -G'(k):x_hat, the mean mode,
 //                  the 1/N of eq. ft, then the inverse transform along x3
-//                                                            (eq. discFour2, criterion)
+//                                                             (eq. discFour2, criterion)
 //   R  reduce_eta: eta, <sigma> history and the stop decision (one block)
 //   K2 mid_y     : inverse transform along x2
-//   K5 inv_x     : complex-to-real along x1 fused with the scheme update
+//   K5 inv_x     : half-complex-to-real along x1 fused with the scheme update
 //                  (eq. ds or eq. as), optional max |delta| for the max-delta stop
-// The half spectrum is stored [comp][x3][x2][P] with x1 fastest, P >= n1/2 + 1.
+// The half spectrum is array-of-structures [x3 pos][x2 pos][x1][component]: a
+// strided pass reads rows of W modes x n_c components (192 contiguous bytes in
+// FP32 with W = 4, n_c = 6).  Along x2 and x3 the spectrum is kept in the
+// digit-reversed order of the in-place transforms (see fftls_fft.cuh).
 #include <math.h>
 
 #include "fftls_kernels.cuh"
@@ -90,20 +93,36 @@ __device__ void block_max(double (&v)[W]) {
   __syncthreads();
 }
 
+// Dynamic shared memory: twiddles of the transformed axis, then the tile.
+template <typename T2>
+__device__ __forceinline__ T2* load_twiddles(const T2* __restrict__ tw, int L, T2** tile) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* tws = reinterpret_cast<T2*>(smem_raw);
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = tw[t];
+  *tile = tws + ((L + 1) & ~1);
+  __syncthreads();
+  return tws;
+}
+
+__host__ __device__ constexpr int odd_stride(int n) { return (n & 1) ? n : n + 1; }
+
 // ---------------------------------------------------------------------------
 // K1: constitutive law + forward x1 transform (real -> half complex)
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void k_fwd_x(IterArgs<T> a) {
+__global__ void __launch_bounds__(512) k_fwd_x(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
   if (a.ctrl->state != kRunning) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* buf = reinterpret_cast<T2*>(smem_raw);
   const Geom g = a.g;
   const int L1 = g.n1, H = g.H;
+  T2* tile;
+  const T2* tws = load_twiddles(a.tw[0], L1, &tile);
   const int nout = a.dual ? 2 * NC : NC;
   const int NP = (nout + 1) / 2;
+  const int CP = odd_stride(NP);
+  const int BS = L1 * CP;
+  const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
   const int G = a.x_lines;
   double acc[2 * NC];
@@ -139,34 +158,36 @@ __global__ void k_fwd_x(IterArgs<T> a) {
           out[c] = s;
         }
       }
-      T2* line = buf + (size_t)gl * NP * L1;
+      T2* row = tile + gl * BS + x * CP;
 #pragma unroll
       for (int p = 0; p < NC; ++p) {
         if (p < NP) {
           T2 v;
           v.x = out[2 * p];
           v.y = (2 * p + 1 < nout) ? out[2 * p + 1] : (T)0;
-          line[p * L1 + x] = v;
+          row[p] = v;
         }
       }
     }
 #pragma unroll
     for (int c = 0; c < 2 * NC; ++c) acc[c] += (double)accf[c];
     __syncthreads();
-    smem_fft(buf, a.px, nl * NP, 1, L1, 0, 1, a.twx, false);
-    for (int idx = threadIdx.x; idx < nl * NP * H; idx += blockDim.x) {
-      const int line = idx / H, k = idx - line * H;
-      const int gl = line / NP, p = line - gl * NP;
-      const T2 Z = buf[line * L1 + k];
-      const T2 Zm = buf[line * L1 + (k == 0 ? 0 : L1 - k)];
+    tile_fft(tile, nl, BS, CP, NP, a.pl[0], tws, false);
+    for (int idx = threadIdx.x; idx < nl * H * NP; idx += blockDim.x) {
+      const int p = idx % NP;
+      const int rest = idx / NP;
+      const int k = rest % H, gl = rest / H;
+      const T2 Z = tile[gl * BS + __ldg(&pos[k]) * CP + p];
+      const T2 Zm = tile[gl * BS + __ldg(&pos[k == 0 ? 0 : L1 - k]) * CP + p];
       T2 A, B;
       A.x = (T)0.5 * (Z.x + Zm.x);
       A.y = (T)0.5 * (Z.y - Zm.y);
       B.x = (T)0.5 * (Z.y + Zm.y);
       B.y = (T)-0.5 * (Z.x - Zm.x);
-      const long long off = (l0 + gl) * (long long)g.P + k;
-      a.spec[(long long)(2 * p) * g.CS + off] = A;
-      if (2 * p + 1 < nout) a.spec[(long long)(2 * p + 1) * g.CS + off] = B;
+      const long long m = (l0 + gl) * (long long)H + k;
+      const int o0 = 2 * p, o1 = 2 * p + 1;
+      (o0 < NC ? a.specA : a.specB)[m * NC + (o0 % NC)] = A;
+      if (o1 < nout) (o1 < NC ? a.specA : a.specB)[m * NC + (o1 % NC)] = B;
     }
     __syncthreads();
   }
@@ -177,33 +198,33 @@ __global__ void k_fwd_x(IterArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
-// K2: complex transform along x2, in place, tiles of y_w columns
+// K2: transform along x2, in place; tiles of y_w modes x n2 rows x n_c
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_mid_y(IterArgs<T> a, int comp0, int inv) {
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_mid_y(IterArgs<T> a, int inv) {
   typedef typename Cplx<T>::type T2;
   const int st = a.ctrl->state;
   if (inv ? (st != kRunning && st != kLast) : (st != kRunning)) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* buf = reinterpret_cast<T2*>(smem_raw);
   const Geom g = a.g;
-  const int w = a.y_w;
-  const int x0 = blockIdx.x * w;
-  const int nx = min(w, g.H - x0);
   const int n2 = g.n2;
-  const long long base = (long long)(comp0 + blockIdx.z) * g.CS + (long long)blockIdx.y * n2 * g.P + x0;
-  for (int idx = threadIdx.x; idx < n2 * w; idx += blockDim.x) {
-    const int y = idx / w, xc = idx - y * w;
-    T2 v;
-    if (xc < nx) v = a.spec[base + (long long)y * g.P + xc];
-    else { v.x = (T)0; v.y = (T)0; }
-    buf[idx] = v;
+  T2* tile;
+  const T2* tws = load_twiddles(a.tw[1], n2, &tile);
+  const int W = a.y_w;
+  const int x0 = blockIdx.x * W;
+  const int nx = min(W, g.H - x0);
+  const int C = W * NC, cols = nx * NC;
+  T2* spec = blockIdx.z ? a.specB : a.specA;
+  const long long base = ((long long)blockIdx.y * n2 * g.H + x0) * NC;
+  const long long rstride = (long long)g.H * NC;
+  for (int idx = threadIdx.x; idx < n2 * cols; idx += blockDim.x) {
+    const int y = idx / cols, cc = idx - y * cols;
+    tile[y * C + cc] = spec[base + y * rstride + cc];
   }
   __syncthreads();
-  smem_fft(buf, a.py, w, w, 0, 1, w, a.twy, inv != 0);
-  for (int idx = threadIdx.x; idx < n2 * w; idx += blockDim.x) {
-    const int y = idx / w, xc = idx - y * w;
-    if (xc < nx) a.spec[base + (long long)y * g.P + xc] = buf[idx];
+  tile_fft(tile, 1, 0, C, cols, a.pl[1], tws, inv != 0);
+  for (int idx = threadIdx.x; idx < n2 * cols; idx += blockDim.x) {
+    const int y = idx / cols, cc = idx - y * cols;
+    spec[base + y * rstride + cc] = tile[y * C + cc];
   }
 }
 
@@ -212,27 +233,28 @@ __global__ void k_mid_y(IterArgs<T> a, int comp0, int inv) {
 // ---------------------------------------------------------------------------
 // Per mode with x_hat the tensor held by this block:
 //   * eta: w_q |k* . x_hat|^2 (x_hat = sigma_hat), w_q = 2 for x1 modes with a
-//     conjugate partner outside the half spectrum, else 1 (eq. criterion, A3);
+//     conjugate partner outside the half spectrum, else 1 (eq. criterion);
 //   * e_hat = -G'(k) : x_hat / N at q != 0, with
 //       MS/C/R (k = phase * i * kr, kr real): the continuum operator eq. green0b at
 //       direction kr (the phase cancels),
 //       W: the displacement form with a 2x2 solve in span{k, conj(k)},
 //       MS with some q_i = pi (even L): G = C0^{-1} (eq. hfreq),
 //       k = 0 at q != 0 (C, R): 0 (eq. mulfix, mysymgr, 3D rule);
-//   * q = 0: e_hat = eps_bar (tau form: N eps_bar / N) or 0 (sigma form).
+//   * q = 0: e_hat = eps_bar (tau form: N eps_bar / N) or 0 (sigma form, corrections).
+// The divergence is accumulated in a phase-free form: V = x_hat . kr for MS/C/R
+// and b = conj(k) . x_hat for W; d64 holds that vector for the FP64 iterate.
 template <typename T, int DIM>
-__device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y, int z,
+__device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y, int z, long long mstore,
                                              typename Cplx<T>::type* X, bool do_green, bool do_eta,
                                              T& eta_acc) {
   typedef typename Cplx<T>::type T2;
   typedef Comp<DIM> CM;
   constexpr int NC = CM::NC;
-  const KTab<T> kt[3] = {a.kx[x], a.ky[y], a.kz[z]};
+  const KTab<T> kt[3] = {a.kt[0][x], a.kt[1][y], a.kt[2][z]};
   const bool q0 = (x == 0 && y == 0 && z == 0);
   const T wq = (x == 0 || 2 * x == a.g.n1) ? (T)1 : (T)2;
   const T invN = (T)(1.0 / (double)a.g.N);
   const T mu0 = (T)a.mu0, lam0 = (T)a.lam0;
-  // full symmetric tensor view
   T2 M[DIM][DIM];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -266,34 +288,55 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
       K2 += kr[j] * kr[j];
     }
     if (do_eta) {
-      T s = (T)0;
+      if (a.write_d64) {
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) s += V[j].x * V[j].x + V[j].y * V[j].y;
-      // operator G uses q_i = +pi at an even-L Nyquist index on both sides of the
-      // spectrum, so the conjugate partner (-q) of a half-spectrum mode has k with
-      // the Nyquist components of x2, x3 not negated: add its term explicitly.
-      bool flip = false;
-      if (a.green == kMS && wq == (T)2) {
-#pragma unroll
-        for (int i = 1; i < DIM; ++i) flip = flip || (kt[i].nyq != (T)0);
+        for (int j = 0; j < 3; ++j) {
+          float2 f;
+          f.x = j < DIM ? (float)V[j].x : 0.f;
+          f.y = j < DIM ? (float)V[j].y : 0.f;
+          a.d64[mstore * 3 + j] = f;
+        }
       }
-      if (flip) {
-        T sp = (T)0;
+      T s = (T)0;
+      if (a.corr) {
+        // estimate for a correction phase: the stored FP64 divergence plus this one
+        // (the conjugate-partner term of operator G below is left out here)
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
-          T2 u;
-          u.x = (T)0; u.y = (T)0;
-#pragma unroll
-          for (int i = 0; i < DIM; ++i) {
-            const T kk = (i > 0 && kt[i].nyq != (T)0) ? -kr[i] : kr[i];
-            u.x += M[i][j].x * kk;
-            u.y += M[i][j].y * kk;
-          }
-          sp += u.x * u.x + u.y * u.y;
+          const float2 f = a.d64[mstore * 3 + j];
+          const T vx = V[j].x + (T)f.x, vy = V[j].y + (T)f.y;
+          s += vx * vx + vy * vy;
         }
-        eta_acc += s + sp;
-      } else {
         eta_acc += wq * s;
+      } else {
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) s += V[j].x * V[j].x + V[j].y * V[j].y;
+        // operator G uses q_i = +pi at an even-L Nyquist index on both sides of the
+        // spectrum, so the conjugate partner (-q) of a half-spectrum mode has k with
+        // the Nyquist components of x2, x3 not negated: add its term explicitly.
+        bool flip = false;
+        if (a.green == kMS && wq == (T)2) {
+#pragma unroll
+          for (int i = 1; i < DIM; ++i) flip = flip || (kt[i].nyq != (T)0);
+        }
+        if (flip) {
+          T sp = (T)0;
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) {
+            T2 u;
+            u.x = (T)0; u.y = (T)0;
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+              const T kk = (i > 0 && kt[i].nyq != (T)0) ? -kr[i] : kr[i];
+              u.x += M[i][j].x * kk;
+              u.y += M[i][j].y * kk;
+            }
+            sp += u.x * u.x + u.y * u.y;
+          }
+          eta_acc += s + sp;
+        } else {
+          eta_acc += wq * s;
+        }
       }
     }
     if (!do_green) return;
@@ -304,7 +347,7 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
     }
     if (q0) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) { E[c].x = a.dual ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
+      for (int c = 0; c < NC; ++c) { E[c].x = (a.dual && !a.corr) ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
     } else if (nyq) {
       // -C0^{-1}:x / N,  C0^{-1} = I/(2 mu0) - lam0 / (2 mu0 (d lam0 + 2 mu0)) dd
       T2 tr;
@@ -342,8 +385,7 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
     T2 k[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) { k[i].x = kt[i].cm1; k[i].y = kt[i].sn; }
-    // b_j = sum_i conj(k_i) x_ij
-    T2 b[DIM];
+    T2 b[DIM];  // b_j = sum_i conj(k_i) x_ij
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
       T2 s;
@@ -353,15 +395,32 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
       b[j] = s;
     }
     if (do_eta) {
+      if (a.write_d64) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          float2 f;
+          f.x = j < DIM ? (float)b[j].x : 0.f;
+          f.y = j < DIM ? (float)b[j].y : 0.f;
+          a.d64[mstore * 3 + j] = f;
+        }
+      }
       T s = (T)0;
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) s += b[j].x * b[j].x + b[j].y * b[j].y;
+      for (int j = 0; j < DIM; ++j) {
+        T bx = b[j].x, by = b[j].y;
+        if (a.corr) {
+          const float2 f = a.d64[mstore * 3 + j];
+          bx += (T)f.x;
+          by += (T)f.y;
+        }
+        s += bx * bx + by * by;
+      }
       eta_acc += wq * s;
     }
     if (!do_green) return;
     if (q0) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) { E[c].x = a.dual ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
+      for (int c = 0; c < NC; ++c) { E[c].x = (a.dual && !a.corr) ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
     } else {
       T K = (T)0;
       T2 gk, p, r;
@@ -401,54 +460,52 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
 }
 
 template <typename T, int DIM>
-__global__ void k_fourier_z(IterArgs<T> a) {
+__global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
   if (a.ctrl->state != kRunning) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* buf = reinterpret_cast<T2*>(smem_raw);
   const Geom g = a.g;
-  const int w = a.z_w;
-  const int x0 = blockIdx.x * w;
-  const int y = blockIdx.y;
+  const int n3 = g.n3;
+  T2* tile;
+  const T2* tws = load_twiddles(a.tw[2], n3, &tile);
+  const int W = a.z_w;
+  const int x0 = blockIdx.x * W;
+  const int py = blockIdx.y;
   const int kind = blockIdx.z;
-  const int c0 = kind == 0 ? 0 : NC;
   const bool do_green = kind == 0;
   const bool do_eta = a.dual ? (kind == 1) : true;
-  const int n3 = g.n3;
-  const int nx = min(w, g.H - x0);
-  const int cs = n3 * w;
-  const long long rowz = (long long)g.n2 * g.P;
-  const long long base = (long long)y * g.P + x0;
-  for (int idx = threadIdx.x; idx < NC * cs; idx += blockDim.x) {
-    const int c = idx / cs, rem = idx - c * cs;
-    const int z = rem / w, xc = rem - z * w;
-    T2 v;
-    if (xc < nx) v = a.spec[(long long)(c0 + c) * g.CS + z * rowz + base + xc];
-    else { v.x = (T)0; v.y = (T)0; }
-    buf[idx] = v;
+  const int nx = min(W, g.H - x0);
+  const int C = W * NC, cols = nx * NC;
+  T2* spec = kind ? a.specB : a.specA;
+  const long long base = ((long long)py * g.H + x0) * NC;
+  const long long zstride = (long long)g.n2 * g.H * NC;
+  for (int idx = threadIdx.x; idx < n3 * cols; idx += blockDim.x) {
+    const int z = idx / cols, cc = idx - z * cols;
+    tile[z * C + cc] = spec[base + z * zstride + cc];
   }
   __syncthreads();
-  smem_fft(buf, a.pz, NC * w, w, cs, 1, w, a.twz, false);
+  tile_fft(tile, 1, 0, C, cols, a.pl[2], tws, false);
+  const int ym = __ldg(&a.perm[1][py]);
   T eta_acc = (T)0;
-  for (int idx = threadIdx.x; idx < cs; idx += blockDim.x) {
-    const int z = idx / w, xc = idx - z * w;
-    if (xc >= nx) continue;
+  for (int idx = threadIdx.x; idx < n3 * nx; idx += blockDim.x) {
+    const int pz = idx / nx, xc = idx - pz * nx;
+    const int zm = __ldg(&a.perm[2][pz]);
+    T2* mp = tile + pz * C + xc * NC;
     T2 X[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) X[c] = buf[c * cs + idx];
-    fourier_mode<T, DIM>(a, x0 + xc, y, z, X, do_green, do_eta, eta_acc);
+    for (int c = 0; c < NC; ++c) X[c] = mp[c];
+    const long long mstore = ((long long)pz * g.n2 + py) * g.H + x0 + xc;
+    fourier_mode<T, DIM>(a, x0 + xc, ym, zm, mstore, X, do_green, do_eta, eta_acc);
     if (do_green)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) buf[c * cs + idx] = X[c];
+      for (int c = 0; c < NC; ++c) mp[c] = X[c];
   }
   __syncthreads();
   if (do_green) {
-    smem_fft(buf, a.pz, NC * w, w, cs, 1, w, a.twz, true);
-    for (int idx = threadIdx.x; idx < NC * cs; idx += blockDim.x) {
-      const int c = idx / cs, rem = idx - c * cs;
-      const int z = rem / w, xc = rem - z * w;
-      if (xc < nx) a.spec[(long long)c * g.CS + z * rowz + base + xc] = buf[idx];
+    tile_fft(tile, 1, 0, C, cols, a.pl[2], tws, true);
+    for (int idx = threadIdx.x; idx < n3 * cols; idx += blockDim.x) {
+      const int z = idx / cols, cc = idx - z * cols;
+      spec[base + z * zstride + cc] = tile[z * C + cc];
     }
   }
   double e1[1] = {(double)eta_acc};
@@ -472,7 +529,7 @@ __global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts) {
   double s[2 * NC + 1];
 #pragma unroll
   for (int c = 0; c < 2 * NC + 1; ++c) s[c] = 0.0;
-  for (int b = threadIdx.x; b < a.x1_blocks; b += blockDim.x)
+  for (int b = threadIdx.x; b < a.x_blocks; b += blockDim.x)
 #pragma unroll
     for (int c = 0; c < 2 * NC; ++c) s[c] += a.part_mean[(size_t)b * 2 * NC + c];
   for (int b = threadIdx.x; b < n_eta_parts; b += blockDim.x) s[2 * NC] += a.part_eta[b];
@@ -483,12 +540,14 @@ __global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts) {
   const int it = ctl->it;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const double ms = s[c] / N, me = s[NC + c] / N;
+    const double ms = ctl->off_sig[c] + s[c] / N, me = ctl->off_eps[c] + s[NC + c] / N;
     const double wgt = c < DIM ? 1.0 : 2.0;
     fro2 += wgt * ms * ms;
     eb2 += wgt * a.eps_bar[c] * a.eps_bar[c];
     d2 += wgt * (me - a.eps_bar[c]) * (me - a.eps_bar[c]);
     a.ms_hist[(size_t)it * NC + c] = ms;
+    ctl->last_ms[c] = ms;
+    ctl->last_me[c] = me;
   }
   const double num = sqrt(fmax(s[2 * NC], 0.0));
   const double den = N * sqrt(fro2);
@@ -499,6 +558,7 @@ __global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts) {
   const double merr = eb2 > 0.0 ? sqrt(d2 / eb2) : sqrt(d2);
   a.eta_hist[it] = eta;
   ctl->it = it + 1;
+  ctl->phase_it += 1;
   ctl->last_eta = eta;
   ctl->last_mean_err = merr;
   if (it == 0) { ctl->eta0 = eta; ctl->best = eta; }
@@ -510,8 +570,9 @@ __global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts) {
   } else {
     if (ctl->stall_window > 0) {
       if (eta < 0.9 * ctl->best) { ctl->best = eta; ctl->stall = 0; }
-      else if (++ctl->stall >= ctl->stall_window) ns = kSwitch;
+      else if (++ctl->stall >= (ctl->best < 1e-3 ? ctl->stall_window : 8 * ctl->stall_window)) ns = kSwitch;
     }
+    if (ns == kRunning && ctl->phase_max > 0 && ctl->phase_it >= ctl->phase_max) ns = kSwitch;
     if (ns == kRunning && it + 1 >= ctl->max_it) ns = kLast;
   }
   ctl->state = ns;
@@ -521,73 +582,93 @@ __global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts) {
 // K5: inverse x1 transform (half complex -> real) + scheme update
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void k_inv_x(IterArgs<T> a) {
+__global__ void __launch_bounds__(512) k_inv_x(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
   constexpr int NPI = (NC + 1) / 2;
+  constexpr int CP = odd_stride(NPI);
   const int st = a.ctrl->state;
   if (st != kRunning && st != kLast) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* buf = reinterpret_cast<T2*>(smem_raw);
   const Geom g = a.g;
   const int L1 = g.n1, H = g.H;
+  T2* tile;
+  const T2* tws = load_twiddles(a.tw[0], L1, &tile);
+  const int BS = L1 * CP;
+  const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
   const int G = a.x_lines;
   double dmax[2] = {0.0, 0.0};
   for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
     const int nl = (int)min((long long)G, nlines - l0);
-    for (int idx = threadIdx.x; idx < nl * NPI * H; idx += blockDim.x) {
-      const int line = idx / H, k = idx - line * H;
-      const int gl = line / NPI, p = line - gl * NPI;
-      const long long off = (l0 + gl) * (long long)g.P + k;
-      T2 A = a.spec[(long long)(2 * p) * g.CS + off];
+    for (int idx = threadIdx.x; idx < nl * H * NPI; idx += blockDim.x) {
+      const int p = idx % NPI;
+      const int rest = idx / NPI;
+      const int k = rest % H, gl = rest / H;
+      const long long m = (l0 + gl) * (long long)H + k;
+      T2 A = a.specA[m * NC + 2 * p];
       T2 B;
-      if (2 * p + 1 < NC) B = a.spec[(long long)(2 * p + 1) * g.CS + off];
+      if (2 * p + 1 < NC) B = a.specA[m * NC + 2 * p + 1];
       else { B.x = (T)0; B.y = (T)0; }
       if (k == 0 || 2 * k == L1) { A.y = (T)0; B.y = (T)0; }
       T2 z;
       z.x = A.x - B.y;
       z.y = A.y + B.x;
-      buf[line * L1 + k] = z;
+      tile[gl * BS + __ldg(&pos[k]) * CP + p] = z;
       if (k > 0 && L1 - k >= H) {
         T2 zm;
         zm.x = A.x + B.y;
         zm.y = B.x - A.y;
-        buf[line * L1 + L1 - k] = zm;
+        tile[gl * BS + __ldg(&pos[L1 - k]) * CP + p] = zm;
       }
     }
     __syncthreads();
-    smem_fft(buf, a.px, nl * NPI, 1, L1, 0, 1, a.twx, true);
+    tile_fft(tile, nl, BS, CP, NPI, a.pl[0], tws, true);
     for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
       const int gl = idx / L1, x = idx - gl * L1;
       const long long vox = (l0 + gl) * (long long)L1 + x;
       T e[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const T2 v = buf[(gl * NPI + c / 2) * L1 + x];
+        const T2 v = tile[gl * BS + x * CP + c / 2];
         e[c] = (c & 1) ? v.y : v.x;
       }
       T o[NC], n[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) o[c] = a.eps[(long long)c * g.N + vox];
       const T* cf = a.coef + (int)a.phase[vox] * kCoef;
-      if (a.update == kUpdDirectTau) {
+      const int upd = a.update;
+      if (upd == kUpdDirectTau) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) n[c] = e[c];
-      } else if (a.update == kUpdDirectSig) {
+      } else if (upd == kUpdDirectSig) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) n[c] = o[c] + e[c];
+      } else if (upd == kUpdResidual) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          a.rfield[(long long)c * g.N + vox] = (float)(e[c] - o[c]);
+          n[c] = o[c];
+        }
+      } else if (upd == kUpdCorrDirect) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) n[c] = (T)a.rfield[(long long)c * g.N + vox] + e[c];
       } else {
         T d[NC];
         T trd = (T)0;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) { d[c] = e[c] - o[c]; if (c < DIM) trd += d[c]; }
+        for (int c = 0; c < NC; ++c) {
+          d[c] = e[c] - o[c];
+          if (upd == kUpdCorrAccel) d[c] += (T)a.rfield[(long long)c * g.N + vox];
+          if (c < DIM) trd += d[c];
+        }
         const T am = cf[4], av = cf[5];
 #pragma unroll
         for (int c = 0; c < NC; ++c) n[c] = o[c] + am * d[c] + (c < DIM ? av * trd : (T)0);
       }
+      if (upd != kUpdResidual) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) a.eps[(long long)c * g.N + vox] = n[c];
+        for (int c = 0; c < NC; ++c) a.eps[(long long)c * g.N + vox] = n[c];
+      }
       if (a.want_delta) {
         T dn[NC];
         T trn = (T)0;
@@ -618,7 +699,7 @@ __global__ void k_reduce_delta(IterArgs<T> a) {
   const int st = ctl->state;
   if (st != kRunning && st != kLast) return;
   double m[2] = {0.0, 0.0};
-  for (int b = threadIdx.x; b < a.x5_blocks; b += blockDim.x) {
+  for (int b = threadIdx.x; b < a.x_blocks; b += blockDim.x) {
     m[0] = fmax(m[0], a.part_delta[(size_t)b * 2]);
     m[1] = fmax(m[1], a.part_delta[(size_t)b * 2 + 1]);
   }
@@ -645,6 +726,11 @@ template <typename TO, typename TI>
 __global__ void k_convert(TO* out, const TI* in, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = (TO)in[i];
+}
+
+__global__ void k_add_correction(double* out, const float* in, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] += (double)in[i];
 }
 
 template <typename T, int DIM>
@@ -696,16 +782,17 @@ __global__ void k_sum_parts(const double* part, int blocks, int width, double* o
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) {
-  if (a.dim == 3) k_fwd_x<T, 3><<<a.x1_blocks, a.x1_threads, a.x1_smem, s>>>(a);
-  else k_fwd_x<T, 2><<<a.x1_blocks, a.x1_threads, a.x1_smem, s>>>(a);
+  if (a.dim == 3) k_fwd_x<T, 3><<<a.x_blocks, a.x_threads, a.x1_smem, s>>>(a);
+  else k_fwd_x<T, 2><<<a.x_blocks, a.x_threads, a.x1_smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_mid_y(const IterArgs<T>& a, int ncomp, bool inv, cudaStream_t s) {
+cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s) {
   if (a.g.n2 == 1) return cudaSuccess;
-  dim3 grid((a.g.H + a.y_w - 1) / a.y_w, a.g.n3, ncomp);
-  k_mid_y<T><<<grid, a.y_threads, a.y_smem, s>>>(a, 0, inv ? 1 : 0);
+  dim3 grid((a.g.H + a.y_w - 1) / a.y_w, a.g.n3, (!inv && a.dual) ? 2 : 1);
+  if (a.dim == 3) k_mid_y<T, 6><<<grid, a.y_threads, a.y_smem, s>>>(a, inv ? 1 : 0);
+  else k_mid_y<T, 3><<<grid, a.y_threads, a.y_smem, s>>>(a, inv ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -727,8 +814,8 @@ cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_inv_x(const IterArgs<T>& a, cudaStream_t s) {
-  if (a.dim == 3) k_inv_x<T, 3><<<a.x5_blocks, a.x5_threads, a.x5_smem, s>>>(a);
-  else k_inv_x<T, 2><<<a.x5_blocks, a.x5_threads, a.x5_smem, s>>>(a);
+  if (a.dim == 3) k_inv_x<T, 3><<<a.x_blocks, a.x_threads, a.x5_smem, s>>>(a);
+  else k_inv_x<T, 2><<<a.x_blocks, a.x_threads, a.x5_smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -736,24 +823,6 @@ template <typename T>
 cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s) {
   k_reduce_delta<T><<<1, 512, 0, s>>>(a);
   return cudaGetLastError();
-}
-
-template <typename T>
-int kernel_max_threads(int dim, int which) {
-  cudaFuncAttributes at;
-  cudaError_t e = cudaErrorInvalidValue;
-  if (dim == 3) {
-    if (which == 0) e = cudaFuncGetAttributes(&at, (const void*)k_fwd_x<T, 3>);
-    if (which == 1) e = cudaFuncGetAttributes(&at, (const void*)k_mid_y<T>);
-    if (which == 2) e = cudaFuncGetAttributes(&at, (const void*)k_fourier_z<T, 3>);
-    if (which == 3) e = cudaFuncGetAttributes(&at, (const void*)k_inv_x<T, 3>);
-  } else {
-    if (which == 0) e = cudaFuncGetAttributes(&at, (const void*)k_fwd_x<T, 2>);
-    if (which == 1) e = cudaFuncGetAttributes(&at, (const void*)k_mid_y<T>);
-    if (which == 2) e = cudaFuncGetAttributes(&at, (const void*)k_fourier_z<T, 2>);
-    if (which == 3) e = cudaFuncGetAttributes(&at, (const void*)k_inv_x<T, 2>);
-  }
-  return e == cudaSuccess ? at.maxThreadsPerBlock : 0;
 }
 
 template <typename T>
@@ -765,12 +834,13 @@ cudaError_t set_kernel_attributes(const IterArgs<T>& a) {
     FFTLS_ATTR((k_fwd_x<T, 3>), a.x1_smem);
     FFTLS_ATTR((k_inv_x<T, 3>), a.x5_smem);
     FFTLS_ATTR((k_fourier_z<T, 3>), a.z_smem);
+    FFTLS_ATTR((k_mid_y<T, 6>), a.y_smem);
   } else {
     FFTLS_ATTR((k_fwd_x<T, 2>), a.x1_smem);
     FFTLS_ATTR((k_inv_x<T, 2>), a.x5_smem);
     FFTLS_ATTR((k_fourier_z<T, 2>), a.z_smem);
+    FFTLS_ATTR((k_mid_y<T, 3>), a.y_smem);
   }
-  FFTLS_ATTR((k_mid_y<T>), a.y_smem);
 #undef FFTLS_ATTR
   return e;
 }
@@ -786,6 +856,12 @@ template <typename TO, typename TI>
 cudaError_t launch_convert(TO* out, const TI* in, long long n, cudaStream_t s) {
   const int blocks = (int)min((n + 255) / 256, (long long)152 * 16);
   k_convert<TO, TI><<<blocks, 256, 0, s>>>(out, in, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_correction(double* out, const float* in, long long n, cudaStream_t s) {
+  const int blocks = (int)min((n + 255) / 256, (long long)152 * 16);
+  k_add_correction<<<blocks, 256, 0, s>>>(out, in, n);
   return cudaGetLastError();
 }
 
@@ -811,13 +887,12 @@ cudaError_t launch_sum_parts(const double* part, int blocks, int width, double* 
 
 #define FFTLS_INST(T)                                                                                   \
   template cudaError_t launch_fwd_x<T>(const IterArgs<T>&, cudaStream_t);                              \
-  template cudaError_t launch_mid_y<T>(const IterArgs<T>&, int, bool, cudaStream_t);                   \
+  template cudaError_t launch_mid_y<T>(const IterArgs<T>&, bool, cudaStream_t);                        \
   template cudaError_t launch_fourier_z<T>(const IterArgs<T>&, cudaStream_t);                          \
   template cudaError_t launch_reduce_eta<T>(const IterArgs<T>&, cudaStream_t);                         \
   template cudaError_t launch_inv_x<T>(const IterArgs<T>&, cudaStream_t);                              \
   template cudaError_t launch_reduce_delta<T>(const IterArgs<T>&, cudaStream_t);                       \
   template cudaError_t set_kernel_attributes<T>(const IterArgs<T>&);                                    \
-  template int kernel_max_threads<T>(int, int);                                                         \
   template cudaError_t launch_fill_eps<T>(T*, int, long long, const double*, cudaStream_t);            \
   template cudaError_t launch_stress<T>(const T*, const uint8_t*, const T*, int, long long, double*,   \
                                         double*, int, cudaStream_t);

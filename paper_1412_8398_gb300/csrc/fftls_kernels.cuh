@@ -16,11 +16,19 @@ enum State : int {
   kLast = 2,        // max_iter reached: run this iteration's update, then stop
   kStopped = 3,     // set one iteration after kLast
   kDiverged = 4,    // non-finite eta or eta > 1e4 eta_0
-  kSwitch = 5,      // precision hand-over (FP32 -> FP64): no update
+  kSwitch = 5,      // hand-over to the next precision phase: no update
 };
 
 enum Green : int { kMS = 0, kCentered = 1, kWillot = 2, kRotated = 3 };
-enum Update : int { kUpdDirectTau = 0, kUpdDirectSig = 1, kUpdAccel = 2 };
+// scheme update of the inverse x1 pass
+enum Update : int {
+  kUpdDirectTau = 0,  // eps <- e                        (eq. ds, tau form)
+  kUpdDirectSig = 1,  // eps <- eps + e                  (eq. ds, sigma form)
+  kUpdAccel = 2,      // eps <- eps + 2 M (e - eps)      (eq. as)
+  kUpdResidual = 3,   // r <- e - eps (eps unchanged)    (defect of the current iterate)
+  kUpdCorrDirect = 4, // delta <- r + e                  (correction, direct scheme)
+  kUpdCorrAccel = 5,  // delta <- delta + 2 M (r + e - delta) (correction, accelerated)
+};
 
 // Mutable solver control block (device memory, written by the host between
 // phases, advanced by the reduction kernels).
@@ -29,30 +37,36 @@ struct Ctrl {
   int it;            // eta evaluations so far (all phases)
   int max_it;        // cap on `it`
   int stop_rule;     // 0 = eta, 1 = max delta
-  int switch_mode;   // 1: eta <= tol means hand over to FP64 (kSwitch) instead of kConverged
+  int switch_mode;   // 1: eta <= tol means hand over (kSwitch) instead of kConverged
   int stall;         // iterations since the last 10 % improvement of eta
   int stall_window;  // 0 disables stall detection
   int mean_guard;    // 1: eta test also needs |<eps> - eps_bar| <= tol |eps_bar|
+  int phase_it;      // iterations in the current phase
+  int phase_max;     // cap on phase_it (0: none); reaching it hands over (kSwitch)
   double tol;
   double eta0;
   double best;
   double last_eta;
   double last_delta;
   double last_mean_err;
+  double off_sig[6];   // added to <sigma> and <eps> (correction phases: the FP64 iterate's means)
+  double off_eps[6];
+  double last_ms[6];   // <sigma>, <eps> of the last eta evaluation (with offsets)
+  double last_me[6];
 };
 
-// Geometry of the grid and of the half spectrum [comp][n3][n2][P].
+// Geometry: grid n1 x n2 x n3, half spectrum of H = n1/2 + 1 modes along x1,
+// stored array-of-structures [x3 pos][x2 pos][x1][component].
 struct Geom {
   int n1, n2, n3;
-  int H;          // n1 / 2 + 1 (half spectrum length along x1)
-  int P;          // padded row stride of the half spectrum (complex elements)
-  long long N;    // voxels
-  long long CS;   // complex elements per spectrum component = n3 * n2 * P
+  int H;
+  long long N;      // voxels
+  long long modes;  // n3 * n2 * H
 };
 
-// Per-axis wave-vector table entry for index m (signed s, q = 2 pi s / L):
-// {q, sin q, cos q - 1, sin(q/2), cos(q/2), nyquist flag}; exact zeros at the
-// special modes so that k(q) = 0 is detected exactly.
+// Per-axis wave-vector table entry for frequency index m (signed s,
+// q = 2 pi s / L): {q, sin q, cos q - 1, sin(q/2), cos(q/2), nyquist flag};
+// exact zeros at the special modes so that k(q) = 0 is detected exactly.
 template <typename T>
 struct KTab {
   T q, sn, cm1, sh, ch, nyq;
@@ -66,53 +80,55 @@ constexpr int kCoef = 8;
 
 template <typename T>
 struct IterArgs {
+  typedef typename Cplx<T>::type T2;
   Geom g;
   int dim;
   int green;
-  int dual;          // 1: forward transform carries tau (comps 0..nc-1) and sigma (nc..2nc-1)
+  int dual;          // 1: forward transform carries tau (buffer A) and sigma (buffer B)
   int update;        // Update
-  int want_delta;    // K5 computes max |d eps|, |d sigma|
-  T* eps;            // nc x N
+  int corr;          // 1: correction phase (zero mean mode, eta adds d64)
+  int want_delta;    // inverse x1 pass computes max |d eps|, |d sigma|
+  int write_d64;     // eta blocks store k*.sigma_hat (FP32) for a later correction phase
+  T* eps;            // n_c x N (the iterate, or the correction delta)
   const uint8_t* phase;
-  const T* coef;     // n_phases x kCoef
-  typename Cplx<T>::type* spec;
-  const typename Cplx<T>::type* twx;
-  const typename Cplx<T>::type* twy;
-  const typename Cplx<T>::type* twz;
-  const KTab<T>* kx;
-  const KTab<T>* ky;
-  const KTab<T>* kz;
-  AxisPlan px, py, pz;
+  const T* coef;     // 256 x kCoef
+  T2* specA;         // AoS [modes][n_c]: tau_hat (dual) or sigma_hat
+  T2* specB;         // AoS [modes][n_c]: sigma_hat (dual)
+  const T2* tw[3];   // per axis: e^{-2 pi i t / L}
+  const KTab<T>* kt[3];
+  const int* perm[3];  // per axis: storage position -> frequency index
+  const int* pos[3];   // per axis: frequency index -> storage position
+  AxisPlan pl[3];
   double lam0, mu0;
   double eps_bar[6];
   Ctrl* ctrl;
-  double* part_mean;   // [grid_x1][2 nc]: sums of sigma and eps per block
-  double* part_eta;    // [grid_fz]: sums of |k*.sigma_hat|^2 per block
-  double* part_delta;  // [grid_x5][2]: max |d eps|, max |d sigma| per block
+  double* part_mean;   // [x_blocks][2 nc]: sums of sigma and eps per block
+  double* part_eta;    // [z blocks]: sums of |k*.sigma_hat|^2 per block
+  double* part_delta;  // [x_blocks][2]: max |d eps|, max |d sigma| per block
   double* eta_hist;    // [max_it]
   double* ms_hist;     // [max_it][nc]
+  float* rfield;       // n_c x N defect r (written by kUpdResidual, read by corrections)
+  float2* d64;         // [modes][3]: k*.sigma_hat of the FP64 iterate (phase-free form)
   // launch shapes (host-computed)
-  int x_lines;         // lines per batch in the x kernels
-  int x1_blocks, x5_blocks;
-  int y_w, z_w;        // column tile widths of the y and z kernels
-  int y_threads, z_threads, x1_threads, x5_threads;
+  int x_lines, x_blocks, x_threads;
+  int y_w, y_threads, z_w, z_threads;
   size_t x1_smem, x5_smem, y_smem, z_smem;
 };
 
 // Launchers (fftls_kernels.cu).  All return cudaGetLastError().
 template <typename T> cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_mid_y(const IterArgs<T>& a, int ncomp, bool inv, cudaStream_t s);
+template <typename T> cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s);
 template <typename T> cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_inv_x(const IterArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t set_kernel_attributes(const IterArgs<T>& a);
-// Largest block size the register use of kernel `which` allows (0 fwd_x, 1 mid_y, 2 fourier_z, 3 inv_x).
-template <typename T> int kernel_max_threads(int dim, int which);
 
 // Elementwise helpers.
 template <typename T> cudaError_t launch_fill_eps(T* eps, int nc, long long N, const double* eps_bar6, cudaStream_t s);
 template <typename TO, typename TI> cudaError_t launch_convert(TO* out, const TI* in, long long n, cudaStream_t s);
+// out += in (FP64 += FP32), n values
+cudaError_t launch_add_correction(double* out, const float* in, long long n, cudaStream_t s);
 // stress = C(x):eps as FP64 (optional), plus FP64 sums of sigma and eps into part[blocks][2 nc]
 template <typename T> cudaError_t launch_stress(const T* eps, const uint8_t* phase, const T* coef, int dim,
                                                  long long N, double* stress_out, double* part, int blocks,

@@ -23,6 +23,7 @@ const char* const kKindNames[2][kNumKinds] = {
      "reduce_delta_f32"},
     {"fwd_x_f64", "mid_y_fwd_f64", "fourier_z_f64", "reduce_eta_f64", "mid_y_inv_f64", "inv_x_f64",
      "reduce_delta_f64"}};
+constexpr int kMaxOuter = 8;  // FP64 residual evaluations of the refinement ladder
 
 struct DevBuf {
   void* p = nullptr;
@@ -71,18 +72,63 @@ bool factor_plan(int L, AxisPlan* p) {
   if ((int)r.size() > kMaxStages) return false;
   p->L = L;
   p->nst = (int)r.size();
-  for (int i = 0; i < kMaxStages; ++i) p->radix[i] = i < p->nst ? r[i] : 1;
+  int M = L;
+  for (int i = 0; i < kMaxStages; ++i) {
+    p->radix[i] = i < p->nst ? r[i] : 1;
+    p->msize[i] = i < p->nst ? M : 1;
+    if (i < p->nst) M /= r[i];
+  }
   return true;
 }
 
-int min_radix(const AxisPlan& p) {
-  int m = 1 << 30;
-  for (int i = 0; i < p.nst; ++i) m = std::min(m, p.radix[i]);
-  return p.nst ? m : 1 << 30;
+// storage position -> frequency index of the in-place forward transform (fftls_fft.cuh)
+void plan_permutation(const AxisPlan& p, int* perm, int* pos) {
+  for (int q = 0; q < p.L; ++q) {
+    int rem = q, k = 0, mult = 1, span = p.L;
+    for (int s = 0; s < p.nst; ++s) {
+      span /= p.radix[s];
+      const int d = rem / span;
+      rem %= span;
+      k += d * mult;
+      mult *= p.radix[s];
+    }
+    perm[q] = k;
+    pos[k] = q;
+  }
 }
 
-long long bfly(const AxisPlan& p, long long lines) {
-  return p.nst ? lines * p.L / min_radix(p) : 0;
+// Twiddles e^{-2 pi i t / L} (exact at multiples of pi/2) and the wave-vector
+// table {q, sin q, cos q - 1, sin q/2, cos q/2, nyquist} by frequency index.
+void axis_tables(int L, double* tw, double* kt) {
+  for (int t = 0; t < L; ++t) {
+    const double ang = -2.0 * M_PI * (double)t / (double)L;
+    double cs = cos(ang), sn = sin(ang);
+    if ((4 * t) % L == 0) {
+      const int qd = (4 * t) / L;
+      const double cq[4] = {1, 0, -1, 0}, sq[4] = {0, -1, 0, 1};
+      cs = cq[qd % 4];
+      sn = sq[qd % 4];
+    }
+    tw[2 * t] = cs;
+    tw[2 * t + 1] = sn;
+  }
+  for (int m = 0; m < L; ++m) {
+    const int s = m <= L / 2 ? m : m - L;
+    const double q = 2.0 * M_PI * s / L;
+    double sn = sin(q), sh = sin(0.5 * q), ch = cos(0.5 * q);
+    if ((2 * s) % L == 0) sn = 0.0;  // q = 0, pi
+    if (s == 0) sh = 0.0;
+    if (2 * s == L) ch = 0.0;  // q = pi
+    if (4 * s == L) sn = 1.0;
+    if (4 * s == -L) sn = -1.0;
+    double* e = kt + 6 * (size_t)m;
+    e[0] = q;
+    e[1] = sn;
+    e[2] = -2.0 * sh * sh;  // cos q - 1 without cancellation
+    e[3] = sh;
+    e[4] = ch;
+    e[5] = (L % 2 == 0 && 2 * m == L) ? 1.0 : 0.0;
+  }
 }
 
 }  // namespace
@@ -93,16 +139,15 @@ struct fftls_ctx {
   std::string err;
   size_t smem_optin = 0;
   int num_sms = 0;
-  DevBuf phase, eps32, eps64, spec, coef32, coef64, tw32, tw64, kt32, kt64;
-  DevBuf part_mean, part_eta, part_delta, sums, ctrl, eta_hist, ms_hist, scratch;
+  DevBuf phase, eps32, eps64, specA, specB, coef32, coef64, tab32, tab64, perms;
+  DevBuf part_mean, part_eta, part_delta, sums, ctrl, eta_hist, ms_hist, scratch, rfield, d64;
   GraphCache graphs[2];
   Ctrl* h_ctrl = nullptr;  // pinned
   double* h_sums = nullptr;
-  // profiling
+  long long launches = 0;  // kernels launched (graph nodes counted one by one)
+  long long graph_launches = 0;
   double prof_ms[2][kNumKinds];
   int prof_n[2][kNumKinds];
-  long long launches = 0;        // kernels launched (graph nodes counted one by one)
-  long long graph_launches = 0;
   struct ProfEv { cudaEvent_t a, b; int kind; };
   std::vector<ProfEv> ev;
 };
@@ -128,6 +173,8 @@ fftls_status set_err(fftls_ctx* c, fftls_status s, const char* fmt, ...) {
   } while (0)
 
 int ncomp(int dim) { return dim == 3 ? 6 : 3; }
+int even_up(int n) { return (n + 1) & ~1; }
+int odd_up(int n) { return (n & 1) ? n : n + 1; }
 
 bool default_medium(const fftls_problem* p, double* l0, double* m0) {
   const int d = p->dim;
@@ -193,186 +240,124 @@ fftls_status validate(fftls_ctx* c, const fftls_problem* p, const fftls_options*
     return set_err(c, FFTLS_E_INVALID_ARG, "unknown stop rule %d", o->stop);
   if (o->max_iter < 1) return set_err(c, FFTLS_E_INVALID_ARG, "max_iter must be >= 1");
   if (o->precision < 0 || o->precision > 2) return set_err(c, FFTLS_E_INVALID_ARG, "unknown precision %d", o->precision);
+  if (o->precision == FFTLS_FP32_REFINE64 && o->stop != FFTLS_STOP_ETA)
+    return set_err(c, FFTLS_E_INVALID_ARG, "FP32_REFINE64 refines on eta: use FFTLS_STOP_ETA");
   return FFTLS_OK;
 }
 
-// Per-axis tables in FP64, then converted.
-void axis_tables(int L, std::vector<double>& tw, std::vector<double>& kt) {
-  tw.resize(2 * (size_t)L);
-  for (int t = 0; t < L; ++t) {
-    const double ang = -2.0 * M_PI * (double)t / (double)L;
-    double cs = cos(ang), sn = sin(ang);
-    if ((4 * t) % L == 0) {  // exact values at multiples of pi/2
-      const int qd = (4 * t) / L;
-      const double cq[4] = {1, 0, -1, 0}, sq[4] = {0, -1, 0, 1};
-      cs = cq[qd % 4];
-      sn = sq[qd % 4];
-    }
-    tw[2 * t] = cs;
-    tw[2 * t + 1] = sn;
-  }
-  kt.resize(6 * (size_t)L);
-  for (int m = 0; m < L; ++m) {
-    const int s = m <= L / 2 ? m : m - L;
-    const double q = 2.0 * M_PI * s / L;
-    double sn = sin(q), sh = sin(0.5 * q), ch = cos(0.5 * q);
-    if ((2 * s) % L == 0) sn = 0.0;        // q = 0, pi
-    if (s == 0) sh = 0.0;
-    if (2 * s == L) ch = 0.0;               // q = pi
-    if (4 * s == L) sn = 1.0;
-    if (4 * s == -L) sn = -1.0;
-    const double cm1 = -2.0 * sh * sh;     // cos q - 1 without cancellation
-    double* e = &kt[6 * (size_t)m];
-    e[0] = q;
-    e[1] = sn;
-    e[2] = cm1;
-    e[3] = sh;
-    e[4] = ch;
-    e[5] = (L % 2 == 0 && 2 * m == L) ? 1.0 : 0.0;
-  }
-}
-
-template <typename T>
-struct Prec;
-template <>
-struct Prec<float> {
-  static constexpr int idx = 0;
-};
-template <>
-struct Prec<double> {
-  static constexpr int idx = 1;
-};
+template <typename T> struct Prec;
+template <> struct Prec<float> { static constexpr int idx = 0; };
+template <> struct Prec<double> { static constexpr int idx = 1; };
 
 struct Setup {
   int dim, nc;
   Geom g;
-  AxisPlan px, py, pz;
+  AxisPlan pl[3];
   double lam0, mu0;
   double eps_bar[6];
   int green, scheme;
   const uint8_t* d_phase;
   cudaStream_t s;
   bool profile, graphs;
+  int smem_optin, num_sms;
 };
 
-template <typename T>
-fftls_status upload_tables(fftls_ctx* c, const Setup& S, const fftls_problem* p, const T** coef, const void** tw,
-                           const void** kt) {
+void setup_geometry(Setup& S, const fftls_problem* p) {
+  const int d = p->dim, nc = ncomp(d);
+  S.dim = d;
+  S.nc = nc;
+  S.green = p->green;
+  S.scheme = p->scheme;
+  S.g.n1 = p->n[0];
+  S.g.n2 = p->n[1];
+  S.g.n3 = p->n[2];
+  S.g.H = p->n[0] / 2 + 1;
+  S.g.N = (long long)p->n[0] * p->n[1] * p->n[2];
+  S.g.modes = (long long)S.g.n3 * S.g.n2 * S.g.H;
+  for (int ax = 0; ax < 3; ++ax) factor_plan(p->n[ax], &S.pl[ax]);
+  if (isnan(p->lambda0)) default_medium(p, &S.lam0, &S.mu0);
+  else { S.lam0 = p->lambda0; S.mu0 = p->mu0; }
+  for (int i = 0; i < 6; ++i) S.eps_bar[i] = i < nc ? p->eps_bar[i] : 0.0;
+}
+
+// Phase coefficient table (256 entries: ids >= n_phases read NaN, never out of bounds).
+void coef_table(const Setup& S, const fftls_problem* p, double* cf) {
   const int d = S.dim;
-  // 256 phase entries: ids >= n_phases read NaN coefficients (never out of bounds)
-  std::vector<T> cf(256 * kCoef, (T)NAN);
+  for (int i = 0; i < 256 * kCoef; ++i) cf[i] = NAN;
   const double k0 = S.lam0 + 2.0 / d * S.mu0;
   for (int a = 0; a < p->n_phases; ++a) {
     const double l = p->lambda[a], m = p->mu[a];
     const double k = l + 2.0 / d * m;
     const double ak = k0 / (k + k0), am = S.mu0 / (m + S.mu0);
-    T* e = &cf[(size_t)a * kCoef];
-    e[0] = (T)l;
-    e[1] = (T)(2.0 * m);
-    e[2] = (T)(l - S.lam0);
-    e[3] = (T)(2.0 * (m - S.mu0));
-    e[4] = (T)(2.0 * am);
-    e[5] = (T)(2.0 * (ak - am) / d);
-    e[6] = e[7] = (T)0;
+    double* e = cf + (size_t)a * kCoef;
+    e[0] = l;
+    e[1] = 2.0 * m;
+    e[2] = l - S.lam0;
+    e[3] = 2.0 * (m - S.mu0);
+    e[4] = 2.0 * am;
+    e[5] = 2.0 * (ak - am) / d;
+    e[6] = e[7] = 0.0;
   }
-  DevBuf& cb = Prec<T>::idx ? c->coef64 : c->coef32;
-  CUDA_TRY(c, cb.ensure(cf.size() * sizeof(T)));
-  CUDA_TRY(c, cudaMemcpyAsync(cb.p, cf.data(), cf.size() * sizeof(T), cudaMemcpyHostToDevice, S.s));
-  *coef = (const T*)cb.p;
-  // twiddles and wave-vector tables, three axes back to back
-  std::vector<T> twall, ktall;
-  size_t off_tw[3], off_kt[3];
-  for (int ax = 0; ax < 3; ++ax) {
-    std::vector<double> twd, ktd;
-    axis_tables(ax == 0 ? S.g.n1 : (ax == 1 ? S.g.n2 : S.g.n3), twd, ktd);
-    off_tw[ax] = twall.size();
-    off_kt[ax] = ktall.size();
-    for (double v : twd) twall.push_back((T)v);
-    for (double v : ktd) ktall.push_back((T)v);
-    while (twall.size() % 4) twall.push_back((T)0);
-  }
-  DevBuf& tb = Prec<T>::idx ? c->tw64 : c->tw32;
-  DevBuf& kb = Prec<T>::idx ? c->kt64 : c->kt32;
-  CUDA_TRY(c, tb.ensure(twall.size() * sizeof(T)));
-  CUDA_TRY(c, kb.ensure(ktall.size() * sizeof(T)));
-  CUDA_TRY(c, cudaMemcpyAsync(tb.p, twall.data(), twall.size() * sizeof(T), cudaMemcpyHostToDevice, S.s));
-  CUDA_TRY(c, cudaMemcpyAsync(kb.p, ktall.data(), ktall.size() * sizeof(T), cudaMemcpyHostToDevice, S.s));
-  // the vectors are freed on return: make the copies complete first
-  CUDA_TRY(c, cudaStreamSynchronize(S.s));
-  for (int ax = 0; ax < 3; ++ax) {
-    tw[ax] = (const T*)tb.p + off_tw[ax];
-    kt[ax] = (const T*)kb.p + off_kt[ax];
-  }
-  return FFTLS_OK;
 }
 
-// Launch shapes for precision T.  Every stage of the in-place shared-memory
-// FFT needs its butterflies held by the block at once (kPer per thread), and
-// each kernel's block size is capped by its register use.  Returns false if a
-// size does not fit.
+// Table block per precision: per axis twiddles (L complex) then k tables (L x 6).
+size_t table_offset_tw(const Setup& S, int ax) {
+  size_t off = 0;
+  for (int a = 0; a < ax; ++a) off += 2 * (size_t)even_up(S.pl[a].L) + 6 * (size_t)S.pl[a].L;
+  return off;
+}
+size_t table_offset_kt(const Setup& S, int ax) { return table_offset_tw(S, ax) + 2 * (size_t)even_up(S.pl[ax].L); }
+size_t table_count(const Setup& S) { return table_offset_tw(S, 3); }
+
+void build_tables(const Setup& S, std::vector<double>& tab, std::vector<int>& perms) {
+  tab.assign(table_count(S), 0.0);
+  perms.assign(2 * (size_t)(S.pl[0].L + S.pl[1].L + S.pl[2].L), 0);
+  size_t po = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    axis_tables(S.pl[ax].L, &tab[table_offset_tw(S, ax)], &tab[table_offset_kt(S, ax)]);
+    plan_permutation(S.pl[ax], &perms[po], &perms[po + S.pl[ax].L]);
+    po += 2 * (size_t)S.pl[ax].L;
+  }
+}
+
+// Launch shapes for precision T; false if a size does not fit in shared memory.
 template <typename T>
-bool plan_launch(fftls_ctx* c, const Setup& S, IterArgs<T>& a) {
+bool plan_launch(const Setup& S, IterArgs<T>& a) {
   typedef typename Cplx<T>::type T2;
   const size_t cb = sizeof(T2);
-  const size_t lim = c->smem_optin;
+  const size_t lim = (size_t)S.smem_optin - 4096;  // static reduction arrays
   const int nc = S.nc;
   const Geom& g = S.g;
   const long long nlines = (long long)g.n2 * g.n3;
-  auto cap_of = [&](int which) {
-    int m = kernel_max_threads<T>(S.dim, which);
-    m = (m / 32) * 32;
-    return std::max(32, std::min(m, 1024));
-  };
-  const int cap1 = cap_of(0), capy = cap_of(1), capz = cap_of(2), cap5 = cap_of(3);
-  auto threads = [&](long long butterflies, long long elems, int cap) {
-    long long t = (butterflies + kPer - 1) / kPer;
-    t = std::max(t, std::min<long long>(elems, 256));
-    t = ((t + 31) / 32) * 32;
-    return (int)std::min<long long>(std::max<long long>(t, 64), cap);
-  };
-  // x kernels: target ~48 KB per block
-  const int np1 = nc;  // dual pairs (worst case)
-  const int np5 = (nc + 1) / 2;
-  auto pick_lines = [&](int np, int cap) {
-    const size_t per = (size_t)np * g.n1 * cb;
-    if (per > lim) return 0;
-    int G = (int)std::max<size_t>(1, (48 * 1024) / per);
-    G = (int)std::min<long long>(G, nlines);
-    while (G > 1 && bfly(S.px, (long long)G * np) > (long long)cap * kPer) --G;
-    if (bfly(S.px, np) > (long long)cap * kPer) return 0;
-    return G;
-  };
-  const int G1 = pick_lines(np1, cap1), G5 = pick_lines(np5, cap5);
-  if (!G1 || !G5) return false;
-  a.x_lines = std::min(G1, G5);
-  const int G = a.x_lines;
-  a.x1_smem = (size_t)G * np1 * g.n1 * cb;
-  a.x5_smem = (size_t)G * np5 * g.n1 * cb;
-  a.x1_threads = threads(bfly(S.px, (long long)G * np1), (long long)G * g.n1, cap1);
-  a.x5_threads = threads(bfly(S.px, (long long)G * np5), (long long)G * g.n1, cap5);
+  // x kernels: lines per block so that a tile is ~64 KB (at least one line)
+  const size_t twx = (size_t)even_up(g.n1) * cb;
+  const size_t line1 = (size_t)g.n1 * odd_up(nc) * cb;             // forward, tau and sigma pairs
+  const size_t line5 = (size_t)g.n1 * odd_up((nc + 1) / 2) * cb;  // inverse
+  if (twx + line1 > lim) return false;
+  int G = (int)std::max<size_t>(1, (64 * 1024) / line1);
+  G = (int)std::min<long long>(G, nlines);
+  while (G > 1 && twx + G * line1 > lim) --G;
+  a.x_lines = G;
+  a.x1_smem = twx + G * line1;
+  a.x5_smem = twx + G * line5;
+  a.x_threads = 256;
   const long long nbatches = (nlines + G - 1) / G;
-  a.x1_blocks = (int)std::min<long long>(nbatches, (long long)c->num_sms * 8);
-  a.x5_blocks = a.x1_blocks;
-  // y kernel: column tiles of up to 16, <= 64 KB
-  int wy = 16;
-  while (wy > 1 && ((size_t)g.n2 * wy * cb > std::min<size_t>(lim, 64 * 1024) ||
-                    bfly(S.py, wy) > (long long)capy * kPer))
-    wy /= 2;
-  if ((size_t)g.n2 * wy * cb > lim || bfly(S.py, wy) > (long long)capy * kPer) return false;
-  while (wy > 1 && wy / 2 >= g.H) wy /= 2;
-  a.y_w = wy;
-  a.y_smem = (size_t)g.n2 * wy * cb;
-  a.y_threads = threads(bfly(S.py, wy), (long long)g.n2 * wy, capy);
-  // z kernel: n_c components x n3 x w, <= ~100 KB (two blocks per SM)
-  int wz = g.n3 == 1 ? 32 : 16;
-  while (wz > 1 && ((size_t)nc * g.n3 * wz * cb > std::min<size_t>(lim, 100 * 1024) ||
-                    bfly(S.pz, (long long)nc * wz) > (long long)capz * kPer))
-    wz /= 2;
-  if ((size_t)nc * g.n3 * wz * cb > lim || bfly(S.pz, (long long)nc * wz) > (long long)capz * kPer) return false;
-  while (wz > 1 && wz / 2 >= g.H) wz /= 2;
-  a.z_w = wz;
-  a.z_smem = (size_t)nc * g.n3 * wz * cb;
-  a.z_threads = threads(bfly(S.pz, (long long)nc * wz), (long long)g.n3 * wz, capz);
+  a.x_blocks = (int)std::min<long long>(nbatches, (long long)S.num_sms * 4);
+  // strided kernels: W modes x L rows x n_c, <= ~100 KB so two blocks fit an SM
+  auto pick_w = [&](int L, int* W, size_t* smem) {
+    const size_t tw = (size_t)even_up(L) * cb;
+    int w = 16;
+    while (w > 1 && tw + (size_t)L * w * nc * cb > std::min<size_t>(lim, 100 * 1024)) w /= 2;
+    while (w > 1 && w / 2 >= g.H) w /= 2;
+    if (tw + (size_t)L * w * nc * cb > lim) return false;
+    *W = w;
+    *smem = tw + (size_t)L * w * nc * cb;
+    return true;
+  };
+  if (!pick_w(g.n2, &a.y_w, &a.y_smem)) return false;
+  if (!pick_w(g.n3, &a.z_w, &a.z_smem)) return false;
+  a.y_threads = (long long)g.n2 * a.y_w * nc >= 4096 ? 512 : 256;
+  a.z_threads = (long long)g.n3 * a.z_w * nc >= 4096 ? 512 : 256;
   return true;
 }
 
@@ -382,12 +367,9 @@ struct Runner {
   const Setup& S;
   IterArgs<T> a;
   bool capturing = false;
-  int graph_kernels = 0;
   Runner(fftls_ctx* c_, const Setup& S_) : c(c_), S(S_) { memset(&a, 0, sizeof(a)); }
 
-  int kernels_per_iter() const {
-    return 4 + (S.g.n2 > 1 ? 2 : 0) + (a.want_delta ? 1 : 0);
-  }
+  int kernels_per_iter() const { return 4 + (S.g.n2 > 1 ? 2 : 0) + (a.want_delta ? 1 : 0); }
 
   fftls_status launch(int kind, cudaError_t (*fn)(Runner*, cudaStream_t), bool prof) {
     const int pi = Prec<T>::idx;
@@ -413,15 +395,10 @@ struct Runner {
     a.update = update;
     fftls_status st;
     if ((st = launch(0, [](Runner* r, cudaStream_t s) { return launch_fwd_x<T>(r->a, s); }, prof))) return st;
-    if ((st = launch(1, [](Runner* r, cudaStream_t s) {
-           return launch_mid_y<T>(r->a, r->a.dual ? 2 * ncomp(r->a.dim) : ncomp(r->a.dim), false, s);
-         }, prof)))
-      return st;
+    if ((st = launch(1, [](Runner* r, cudaStream_t s) { return launch_mid_y<T>(r->a, false, s); }, prof))) return st;
     if ((st = launch(2, [](Runner* r, cudaStream_t s) { return launch_fourier_z<T>(r->a, s); }, prof))) return st;
     if ((st = launch(3, [](Runner* r, cudaStream_t s) { return launch_reduce_eta<T>(r->a, s); }, prof))) return st;
-    if ((st = launch(4, [](Runner* r, cudaStream_t s) { return launch_mid_y<T>(r->a, ncomp(r->a.dim), true, s); },
-                     prof)))
-      return st;
+    if ((st = launch(4, [](Runner* r, cudaStream_t s) { return launch_mid_y<T>(r->a, true, s); }, prof))) return st;
     if ((st = launch(5, [](Runner* r, cudaStream_t s) { return launch_inv_x<T>(r->a, s); }, prof))) return st;
     if (a.want_delta)
       if ((st = launch(6, [](Runner* r, cudaStream_t s) { return launch_reduce_delta<T>(r->a, s); }, prof)))
@@ -444,6 +421,23 @@ struct Runner {
     return FFTLS_OK;
   }
 
+  fftls_status read_ctrl() {
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_ctrl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
+    CUDA_TRY(c, cudaStreamSynchronize(S.s));
+    return FFTLS_OK;
+  }
+
+  // One iteration launched directly (no graph); returns the state after it.
+  fftls_status single(Ctrl init, bool dual, int update, int* final_state) {
+    CUDA_TRY(c, cudaMemcpyAsync(a.ctrl, &init, sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
+    fftls_status st;
+    if ((st = iteration(dual, update, S.profile))) return st;
+    if ((st = collect_profile())) return st;
+    if ((st = read_ctrl())) return st;
+    *final_state = c->h_ctrl->state;
+    return FFTLS_OK;
+  }
+
   // Run iterations until the device state leaves kRunning.
   fftls_status run(Ctrl init, bool first_dual, bool dual, int update, int* final_state) {
     CUDA_TRY(c, cudaMemcpyAsync(a.ctrl, &init, sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
@@ -451,15 +445,14 @@ struct Runner {
     if (first_dual && !dual) {
       if ((st = iteration(true, kUpdDirectTau, S.profile))) return st;
       if ((st = collect_profile())) return st;
-      CUDA_TRY(c, cudaMemcpyAsync(c->h_ctrl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
-      CUDA_TRY(c, cudaStreamSynchronize(S.s));
+      if ((st = read_ctrl())) return st;
       if (c->h_ctrl->state != kRunning) {
         *final_state = c->h_ctrl->state;
         return FFTLS_OK;
       }
     }
     const long long N = S.g.N;
-    int chunk = (int)std::max<long long>(1, std::min<long long>(32, 40000000LL / std::max<long long>(N, 1)));
+    const int chunk = (int)std::max<long long>(1, std::min<long long>(32, 40000000LL / std::max<long long>(N, 1)));
     cudaGraphExec_t exec = nullptr;
     if (S.graphs && !S.profile) {
       a.dual = dual ? 1 : 0;
@@ -498,8 +491,7 @@ struct Runner {
           if ((st = iteration(dual, update, S.profile))) return st;
         if ((st = collect_profile())) return st;
       }
-      CUDA_TRY(c, cudaMemcpyAsync(c->h_ctrl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
-      CUDA_TRY(c, cudaStreamSynchronize(S.s));
+      if ((st = read_ctrl())) return st;
       if (c->h_ctrl->state != kRunning) break;
     }
     *final_state = c->h_ctrl->state;
@@ -509,50 +501,56 @@ struct Runner {
 
 template <typename T>
 fftls_status prepare(fftls_ctx* c, const Setup& S, const fftls_problem* p, const fftls_options* o, Runner<T>& R,
-                     T* eps) {
+                     T* eps, const std::vector<double>& tab, const int* d_perms) {
+  typedef typename Cplx<T>::type T2;
   IterArgs<T>& a = R.a;
   a.g = S.g;
   a.dim = S.dim;
   a.green = S.green;
-  a.px = S.px;
-  a.py = S.py;
-  a.pz = S.pz;
+  for (int ax = 0; ax < 3; ++ax) a.pl[ax] = S.pl[ax];
   a.lam0 = S.lam0;
   a.mu0 = S.mu0;
   for (int i = 0; i < 6; ++i) a.eps_bar[i] = S.eps_bar[i];
-  if (!plan_launch<T>(c, S, a))
+  if (!plan_launch<T>(S, a))
     return set_err(c, FFTLS_E_UNSUPPORTED_SIZE, "grid %dx%dx%d does not fit the shared-memory tiles", S.g.n1, S.g.n2,
                    S.g.n3);
-  const T* coef;
-  const void* tw[3];
-  const void* kt[3];
-  fftls_status st = upload_tables<T>(c, S, p, &coef, tw, kt);
-  if (st) return st;
-  a.coef = coef;
-  a.twx = (const typename Cplx<T>::type*)tw[0];
-  a.twy = (const typename Cplx<T>::type*)tw[1];
-  a.twz = (const typename Cplx<T>::type*)tw[2];
-  a.kx = (const KTab<T>*)kt[0];
-  a.ky = (const KTab<T>*)kt[1];
-  a.kz = (const KTab<T>*)kt[2];
+  // coefficients and tables in precision T
+  std::vector<double> cf(256 * kCoef);
+  coef_table(S, p, cf.data());
+  std::vector<T> cfT(cf.begin(), cf.end()), tabT(tab.begin(), tab.end());
+  DevBuf& cb = Prec<T>::idx ? c->coef64 : c->coef32;
+  DevBuf& tb = Prec<T>::idx ? c->tab64 : c->tab32;
+  CUDA_TRY(c, cb.ensure(cfT.size() * sizeof(T)));
+  CUDA_TRY(c, tb.ensure(tabT.size() * sizeof(T)));
+  CUDA_TRY(c, cudaMemcpyAsync(cb.p, cfT.data(), cfT.size() * sizeof(T), cudaMemcpyHostToDevice, S.s));
+  CUDA_TRY(c, cudaMemcpyAsync(tb.p, tabT.data(), tabT.size() * sizeof(T), cudaMemcpyHostToDevice, S.s));
+  CUDA_TRY(c, cudaStreamSynchronize(S.s));  // the host vectors go out of scope
+  a.coef = (const T*)cb.p;
+  size_t po = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    a.tw[ax] = (const T2*)((const T*)tb.p + table_offset_tw(S, ax));
+    a.kt[ax] = (const KTab<T>*)((const T*)tb.p + table_offset_kt(S, ax));
+    a.perm[ax] = d_perms + po;
+    a.pos[ax] = d_perms + po + S.pl[ax].L;
+    po += 2 * (size_t)S.pl[ax].L;
+  }
   a.eps = eps;
   a.phase = S.d_phase;
-  a.spec = (typename Cplx<T>::type*)c->spec.p;
+  a.specA = (T2*)c->specA.p;
+  a.specB = (T2*)c->specB.p;
   a.ctrl = (Ctrl*)c->ctrl.p;
-  a.part_mean = (double*)c->part_mean.p;
-  a.part_eta = (double*)c->part_eta.p;
-  a.part_delta = (double*)c->part_delta.p;
   a.eta_hist = (double*)c->eta_hist.p;
   a.ms_hist = (double*)c->ms_hist.p;
   a.want_delta = o->stop == FFTLS_STOP_MAXDELTA ? 1 : 0;
-  // buffers sized by this phase's launch shapes
   const int ntz = (S.g.H + a.z_w - 1) / a.z_w;
-  CUDA_TRY(c, c->part_mean.ensure((size_t)a.x1_blocks * 2 * S.nc * sizeof(double)));
+  CUDA_TRY(c, c->part_mean.ensure((size_t)a.x_blocks * 2 * S.nc * sizeof(double)));
   CUDA_TRY(c, c->part_eta.ensure((size_t)ntz * S.g.n2 * 2 * sizeof(double)));
-  CUDA_TRY(c, c->part_delta.ensure((size_t)a.x5_blocks * 2 * sizeof(double)));
+  CUDA_TRY(c, c->part_delta.ensure((size_t)a.x_blocks * 2 * sizeof(double)));
   a.part_mean = (double*)c->part_mean.p;
   a.part_eta = (double*)c->part_eta.p;
   a.part_delta = (double*)c->part_delta.p;
+  a.rfield = (float*)c->rfield.p;
+  a.d64 = (float2*)c->d64.p;
   CUDA_TRY(c, set_kernel_attributes<T>(a));
   return FFTLS_OK;
 }
@@ -615,9 +613,9 @@ void fftls_destroy(fftls_ctx* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   for (auto& g : c->graphs) g.release();
-  DevBuf* bufs[] = {&c->phase, &c->eps32, &c->eps64, &c->spec, &c->coef32, &c->coef64, &c->tw32, &c->tw64,
-                    &c->kt32, &c->kt64, &c->part_mean, &c->part_eta, &c->part_delta, &c->sums, &c->ctrl,
-                    &c->eta_hist, &c->ms_hist, &c->scratch};
+  DevBuf* bufs[] = {&c->phase, &c->eps32, &c->eps64, &c->specA, &c->specB, &c->coef32, &c->coef64, &c->tab32,
+                    &c->tab64, &c->perms, &c->part_mean, &c->part_eta, &c->part_delta, &c->sums, &c->ctrl,
+                    &c->eta_hist, &c->ms_hist, &c->scratch, &c->rfield, &c->d64};
   for (DevBuf* b : bufs) b->release();
   for (auto& e : c->ev) {
     cudaEventDestroy(e.a);
@@ -684,29 +682,15 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
   fftls_status st = validate(c, p, o);
   if (st) return st;
   if (!r) return set_err(c, FFTLS_E_INVALID_ARG, "null result");
-  const int d = p->dim, nc = ncomp(d);
   Setup S;
   memset(&S, 0, sizeof(S));
-  S.dim = d;
-  S.nc = nc;
-  S.green = p->green;
-  S.scheme = p->scheme;
-  S.g.n1 = p->n[0];
-  S.g.n2 = p->n[1];
-  S.g.n3 = p->n[2];
-  S.g.H = p->n[0] / 2 + 1;
-  S.g.P = ((S.g.H + 15) / 16) * 16;
-  S.g.N = (long long)p->n[0] * p->n[1] * p->n[2];
-  S.g.CS = (long long)S.g.n3 * S.g.n2 * S.g.P;
-  factor_plan(S.g.n1, &S.px);
-  factor_plan(S.g.n2, &S.py);
-  factor_plan(S.g.n3, &S.pz);
-  if (isnan(p->lambda0)) default_medium(p, &S.lam0, &S.mu0);
-  else { S.lam0 = p->lambda0; S.mu0 = p->mu0; }
-  for (int i = 0; i < 6; ++i) S.eps_bar[i] = i < nc ? p->eps_bar[i] : 0.0;
+  setup_geometry(S, p);
+  const int d = S.dim, nc = S.nc;
   S.s = o->stream ? (cudaStream_t)o->stream : c->stream;
   S.profile = o->profile != 0;
   S.graphs = o->use_graphs != 0;
+  S.smem_optin = (int)c->smem_optin;
+  S.num_sms = c->num_sms;
   const long long N = S.g.N;
   if (S.profile) {
     memset(c->prof_ms, 0, sizeof(c->prof_ms));
@@ -733,20 +717,34 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
   }
   const bool use32 = o->precision != FFTLS_FP64;
   const bool use64 = o->precision != FFTLS_FP32;
-  const int nout_max = 2 * nc;
-  const size_t spec_bytes = (size_t)nout_max * S.g.CS * (use64 ? 16 : 8);
-  CUDA_TRY(c, c->spec.ensure(spec_bytes));
+  const bool ladder = o->precision == FFTLS_FP32_REFINE64;
+  const size_t spec_bytes = (size_t)S.g.modes * nc * (use64 ? 16 : 8);
+  CUDA_TRY(c, c->specA.ensure(spec_bytes));
+  CUDA_TRY(c, c->specB.ensure(spec_bytes));
   if (use32) CUDA_TRY(c, c->eps32.ensure((size_t)nc * N * sizeof(float)));
   if (use64 || o->eps_init) CUDA_TRY(c, c->eps64.ensure((size_t)nc * N * sizeof(double)));
+  if (ladder) {
+    CUDA_TRY(c, c->rfield.ensure((size_t)nc * N * sizeof(float)));
+    CUDA_TRY(c, c->d64.ensure((size_t)S.g.modes * 3 * sizeof(float2)));
+  }
   CUDA_TRY(c, c->eta_hist.ensure((size_t)o->max_iter * sizeof(double)));
   CUDA_TRY(c, c->ms_hist.ensure((size_t)o->max_iter * nc * sizeof(double)));
+  // tables shared by both precisions
+  std::vector<double> tab;
+  std::vector<int> perms;
+  build_tables(S, tab, perms);
+  CUDA_TRY(c, c->perms.ensure(perms.size() * sizeof(int)));
+  CUDA_TRY(c, cudaMemcpyAsync(c->perms.p, perms.data(), perms.size() * sizeof(int), cudaMemcpyHostToDevice, S.s));
+  const int* d_perms = (const int*)c->perms.p;
   // initial field
   const bool warm = o->eps_init != nullptr;
   if (warm) {
     CUDA_TRY(c, cudaMemcpyAsync(c->eps64.p, o->eps_init, (size_t)nc * N * sizeof(double),
                                 o->eps_init_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S.s));
-    if (use32 && o->precision != FFTLS_FP64)
+    if (use32) {
       CUDA_TRY(c, launch_convert<float, double>((float*)c->eps32.p, (const double*)c->eps64.p, (long long)nc * N, S.s));
+      c->launches += 1;
+    }
   } else {
     if (o->precision == FFTLS_FP64) CUDA_TRY(c, launch_fill_eps<double>((double*)c->eps64.p, nc, N, S.eps_bar, S.s));
     else CUDA_TRY(c, launch_fill_eps<float>((float*)c->eps32.p, nc, N, S.eps_bar, S.s));
@@ -761,45 +759,87 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
   ctl.max_it = o->max_iter;
   ctl.mean_guard = direct ? 0 : 1;
   ctl.best = INFINITY;
+  ctl.stop_rule = o->stop;
+  ctl.tol = o->tol;
   int state = kRunning;
   int it32 = 0;
   bool final64 = o->precision == FFTLS_FP64;
-  if (use32) {
+  if (o->precision == FFTLS_FP64) {
+    Runner<double> R64(c, S);
+    if ((st = prepare<double>(c, S, p, o, R64, (double*)c->eps64.p, tab, d_perms))) return st;
+    if ((st = R64.run(ctl, direct && warm, dual_steady, upd_steady, &state))) return st;
+  } else if (o->precision == FFTLS_FP32) {
     Runner<float> R32(c, S);
-    if ((st = prepare<float>(c, S, p, o, R32, (float*)c->eps32.p))) return st;
-    Ctrl c32 = ctl;
-    if (o->precision == FFTLS_FP32_REFINE64) {
-      c32.stop_rule = 0;
-      c32.tol = o->refine_switch > 0.0 ? o->refine_switch : o->tol;
-      c32.switch_mode = 1;
-      c32.stall_window = 32;
-      R32.a.want_delta = 0;
-    } else {
-      c32.stop_rule = o->stop;
-      c32.tol = o->tol;
-    }
-    if ((st = R32.run(c32, warm && direct, dual_steady, upd_steady, &state))) return st;
+    if ((st = prepare<float>(c, S, p, o, R32, (float*)c->eps32.p, tab, d_perms))) return st;
+    if ((st = R32.run(ctl, direct && warm, dual_steady, upd_steady, &state))) return st;
+    it32 = c->h_ctrl->it;
+  } else {
+    // Ladder.  A: plain FP32 iterations until eta <= refine_switch (or a stall).
+    Runner<float> R32(c, S);
+    if ((st = prepare<float>(c, S, p, o, R32, (float*)c->eps32.p, tab, d_perms))) return st;
+    Runner<double> R64(c, S);
+    if ((st = prepare<double>(c, S, p, o, R64, (double*)c->eps64.p, tab, d_perms))) return st;
+    Ctrl ca = ctl;
+    ca.stop_rule = 0;
+    ca.tol = o->refine_switch > 0.0 ? o->refine_switch : std::max(o->tol, 3e-5);
+    ca.switch_mode = 1;
+    ca.stall_window = 32;
+    R32.a.want_delta = 0;
+    if ((st = R32.run(ca, direct && warm, dual_steady, upd_steady, &state))) return st;
     it32 = c->h_ctrl->it;
     ctl = *c->h_ctrl;
-    if (o->precision == FFTLS_FP32_REFINE64 && state == kSwitch && ctl.it >= o->max_iter) {
-      state = kStopped;  // no budget left for the FP64 phase
-    } else if (o->precision == FFTLS_FP32_REFINE64 && state == kSwitch) {
+    if (state == kSwitch) {
       CUDA_TRY(c, launch_convert<double, float>((double*)c->eps64.p, (const float*)c->eps32.p, (long long)nc * N, S.s));
+      c->launches += 1;
       final64 = true;
+      // B / C: FP64 defect of the iterate (and its exact eta), then an FP32
+      // correction solve for delta, eps64 += delta; until the FP64 eta passes.
+      R64.a.write_d64 = 1;
+      R32.a.corr = 1;
+      state = kRunning;
+      for (int outer = 0; outer < kMaxOuter; ++outer) {
+        if (ctl.it >= o->max_iter) { state = kStopped; break; }
+        Ctrl cb = ctl;
+        cb.state = kRunning;
+        cb.stop_rule = 0;
+        cb.tol = o->tol;
+        cb.switch_mode = 0;
+        cb.stall_window = 0;
+        cb.phase_max = 0;
+        cb.max_it = ctl.it + 1;  // exactly one evaluation; kLast runs the residual update
+        for (int i = 0; i < 6; ++i) cb.off_sig[i] = cb.off_eps[i] = 0.0;
+        if ((st = R64.single(cb, true, kUpdResidual, &state))) return st;
+        ctl = *c->h_ctrl;
+        ctl.max_it = o->max_iter;
+        if (state == kConverged || state == kDiverged) break;
+        if (ctl.it >= o->max_iter) { state = kStopped; break; }
+        // C: correction delta from 0 with the defect r as source
+        CUDA_TRY(c, cudaMemsetAsync(c->eps32.p, 0, (size_t)nc * N * sizeof(float), S.s));
+        Ctrl cc = ctl;
+        cc.state = kRunning;
+        cc.stop_rule = 0;
+        cc.tol = 0.25 * o->tol;
+        cc.switch_mode = 1;
+        cc.stall_window = 32;
+        cc.stall = 0;
+        cc.best = INFINITY;
+        cc.phase_it = 0;
+        cc.phase_max = 0;
+        for (int i = 0; i < 6; ++i) {
+          cc.off_sig[i] = ctl.last_ms[i];
+          cc.off_eps[i] = ctl.last_me[i];
+        }
+        if ((st = R32.run(cc, false, true, direct ? kUpdCorrDirect : kUpdCorrAccel, &state))) return st;
+        it32 += c->h_ctrl->it - ctl.it;
+        ctl = *c->h_ctrl;
+        CUDA_TRY(c, launch_add_correction((double*)c->eps64.p, (const float*)c->eps32.p, (long long)nc * N, S.s));
+        c->launches += 1;
+        if (state == kDiverged) break;
+        if (state != kSwitch) { state = kStopped; break; }  // max_iter reached inside the correction
+        state = kRunning;
+      }
+      if (state == kRunning) state = kStopped;
     }
-  }
-  if (final64) {
-    Runner<double> R64(c, S);
-    if ((st = prepare<double>(c, S, p, o, R64, (double*)c->eps64.p))) return st;
-    Ctrl c64 = ctl;
-    c64.state = kRunning;
-    c64.stop_rule = o->stop;
-    c64.tol = o->tol;
-    c64.switch_mode = 0;
-    c64.stall_window = 0;
-    c64.stall = 0;
-    const bool from32 = o->precision == FFTLS_FP32_REFINE64;
-    if ((st = R64.run(c64, direct && (warm || from32), dual_steady, upd_steady, &state))) return st;
   }
   const Ctrl fin = *c->h_ctrl;
   // outputs from the final field
@@ -815,7 +855,6 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
       stress_dev = (double*)c->scratch.p;
     }
   }
-  // coefficient table of the final precision (already uploaded by prepare)
   if (out64)
     CUDA_TRY(c, launch_stress<double>((const double*)epsf, S.d_phase, (const double*)c->coef64.p, d, N, stress_dev,
                                       (double*)c->part_mean.p, sblocks, S.s));
@@ -908,48 +947,16 @@ void* g_noalloc_base[kNoAllocMaxDevices];  // device address of g_noalloc_scratc
 
 // host staging for the tables (fixed size: no heap allocation)
 double g_na_coef[256 * kCoef];
-double g_na_tw[3][2 * kMaxL + 8];
-double g_na_kt[3][6 * kMaxL];
+double g_na_tab[3 * (2 * (kMaxL + 2) + 6 * kMaxL)];
+int g_na_perm[6 * kMaxL];
 
 size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
-
-void na_axis_tables(int L, double* tw, double* kt) {
-  for (int t = 0; t < L; ++t) {
-    const double ang = -2.0 * M_PI * (double)t / (double)L;
-    double cs = cos(ang), sn = sin(ang);
-    if ((4 * t) % L == 0) {
-      const int qd = (4 * t) / L;
-      const double cq[4] = {1, 0, -1, 0}, sq[4] = {0, -1, 0, 1};
-      cs = cq[qd % 4];
-      sn = sq[qd % 4];
-    }
-    tw[2 * t] = cs;
-    tw[2 * t + 1] = sn;
-  }
-  for (int m = 0; m < L; ++m) {
-    const int s = m <= L / 2 ? m : m - L;
-    const double q = 2.0 * M_PI * s / L;
-    double sn = sin(q), sh = sin(0.5 * q), ch = cos(0.5 * q);
-    if ((2 * s) % L == 0) sn = 0.0;
-    if (s == 0) sh = 0.0;
-    if (2 * s == L) ch = 0.0;
-    if (4 * s == L) sn = 1.0;
-    if (4 * s == -L) sn = -1.0;
-    double* e = kt + 6 * (size_t)m;
-    e[0] = q;
-    e[1] = sn;
-    e[2] = -2.0 * sh * sh;
-    e[3] = sh;
-    e[4] = ch;
-    e[5] = (L % 2 == 0 && 2 * m == L) ? 1.0 : 0.0;
-  }
-}
 
 }  // namespace
 
 extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_options* o, fftls_result* r) {
-#define NA_TRY(...)                                    \
-  do {                                                 \
+#define NA_TRY(...)                                        \
+  do {                                                     \
     if ((__VA_ARGS__) != cudaSuccess) return FFTLS_E_CUDA; \
   } while (0)
   fftls_status st = validate(nullptr, p, o);
@@ -964,78 +971,52 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
     g_noalloc_base[dev] = base;
   }
   unsigned char* base = (unsigned char*)g_noalloc_base[dev];
-  const int d = p->dim, nc = ncomp(d);
   Setup S;
   memset(&S, 0, sizeof(S));
-  S.dim = d;
-  S.nc = nc;
-  S.green = p->green;
-  S.scheme = p->scheme;
-  S.g.n1 = p->n[0];
-  S.g.n2 = p->n[1];
-  S.g.n3 = p->n[2];
-  S.g.H = p->n[0] / 2 + 1;
-  S.g.P = ((S.g.H + 15) / 16) * 16;
-  S.g.N = (long long)p->n[0] * p->n[1] * p->n[2];
-  S.g.CS = (long long)S.g.n3 * S.g.n2 * S.g.P;
-  factor_plan(S.g.n1, &S.px);
-  factor_plan(S.g.n2, &S.py);
-  factor_plan(S.g.n3, &S.pz);
-  if (isnan(p->lambda0)) default_medium(p, &S.lam0, &S.mu0);
-  else { S.lam0 = p->lambda0; S.mu0 = p->mu0; }
-  for (int i = 0; i < 6; ++i) S.eps_bar[i] = i < nc ? p->eps_bar[i] : 0.0;
+  setup_geometry(S, p);
+  const int d = S.dim, nc = S.nc;
   S.s = (cudaStream_t)o->stream;
   const long long N = S.g.N;
-  // launch shapes (a stack context only carries the device limits)
-  fftls_ctx probe;
   int v = 0;
   NA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  probe.smem_optin = (size_t)v;
+  S.smem_optin = v;
   NA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
-  probe.num_sms = v;
+  S.num_sms = v;
   IterArgs<double> a;
   memset(&a, 0, sizeof(a));
-  if (!plan_launch<double>(&probe, S, a)) return FFTLS_E_UNSUPPORTED_SIZE;
+  if (!plan_launch<double>(S, a)) return FFTLS_E_UNSUPPORTED_SIZE;
   // scratch layout
   const int ntz = (S.g.H + a.z_w - 1) / a.z_w;
-  const int sblocks = (int)std::min<long long>((N + 255) / 256, (long long)probe.num_sms * 8);
+  const int sblocks = (int)std::min<long long>((N + 255) / 256, (long long)S.num_sms * 8);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t at = off; off = na_align(off + bytes); return at; };
-  const size_t o_spec = take((size_t)2 * nc * S.g.CS * 16);
-  const size_t o_pmean = take((size_t)std::max(a.x1_blocks, sblocks) * 2 * nc * 8);
+  const size_t o_specA = take((size_t)S.g.modes * nc * 16);
+  const size_t o_specB = take((size_t)S.g.modes * nc * 16);
+  const size_t o_pmean = take((size_t)std::max(a.x_blocks, sblocks) * 2 * nc * 8);
   const size_t o_peta = take((size_t)ntz * S.g.n2 * 2 * 8);
-  const size_t o_pdelta = take((size_t)a.x5_blocks * 2 * 8);
+  const size_t o_pdelta = take((size_t)a.x_blocks * 2 * 8);
   const size_t o_sums = take(64 * 8);
   const size_t o_ctrl = take(sizeof(Ctrl));
   const size_t o_eh = take((size_t)o->max_iter * 8);
   const size_t o_mh = take((size_t)o->max_iter * nc * 8);
   const size_t o_coef = take(256 * kCoef * 8);
-  size_t o_tw[3], o_kt[3];
-  const int Ls[3] = {S.g.n1, S.g.n2, S.g.n3};
-  for (int ax = 0; ax < 3; ++ax) o_tw[ax] = take((size_t)Ls[ax] * 16);
-  for (int ax = 0; ax < 3; ++ax) o_kt[ax] = take((size_t)Ls[ax] * 48);
+  const size_t ntab = table_count(S);
+  const size_t o_tab = take(ntab * 8);
+  const size_t nperm = 2 * (size_t)(S.g.n1 + S.g.n2 + S.g.n3);
+  const size_t o_perm = take(nperm * sizeof(int));
   const size_t o_phase = p->phase_on_device ? 0 : take((size_t)N);
   if (off > kNoAllocScratchBytes) return FFTLS_E_UNSUPPORTED_SIZE;  // grid too large for the fixed scratch
-  // tables
-  for (int i = 0; i < 256 * kCoef; ++i) g_na_coef[i] = NAN;
-  const double k0 = S.lam0 + 2.0 / d * S.mu0;
-  for (int ph = 0; ph < p->n_phases; ++ph) {
-    const double l = p->lambda[ph], m = p->mu[ph], k = l + 2.0 / d * m;
-    double* e = &g_na_coef[ph * kCoef];
-    e[0] = l;
-    e[1] = 2.0 * m;
-    e[2] = l - S.lam0;
-    e[3] = 2.0 * (m - S.mu0);
-    e[4] = 2.0 * (S.mu0 / (m + S.mu0));
-    e[5] = 2.0 * (k0 / (k + k0) - S.mu0 / (m + S.mu0)) / d;
-    e[6] = e[7] = 0.0;
-  }
+  // tables (host staging arrays, no heap)
+  coef_table(S, p, g_na_coef);
   NA_TRY(cudaMemcpyAsync(base + o_coef, g_na_coef, sizeof(g_na_coef), cudaMemcpyHostToDevice, S.s));
+  size_t po = 0;
   for (int ax = 0; ax < 3; ++ax) {
-    na_axis_tables(Ls[ax], g_na_tw[ax], g_na_kt[ax]);
-    NA_TRY(cudaMemcpyAsync(base + o_tw[ax], g_na_tw[ax], (size_t)Ls[ax] * 16, cudaMemcpyHostToDevice, S.s));
-    NA_TRY(cudaMemcpyAsync(base + o_kt[ax], g_na_kt[ax], (size_t)Ls[ax] * 48, cudaMemcpyHostToDevice, S.s));
+    axis_tables(S.pl[ax].L, &g_na_tab[table_offset_tw(S, ax)], &g_na_tab[table_offset_kt(S, ax)]);
+    plan_permutation(S.pl[ax], &g_na_perm[po], &g_na_perm[po + S.pl[ax].L]);
+    po += 2 * (size_t)S.pl[ax].L;
   }
+  NA_TRY(cudaMemcpyAsync(base + o_tab, g_na_tab, ntab * 8, cudaMemcpyHostToDevice, S.s));
+  NA_TRY(cudaMemcpyAsync(base + o_perm, g_na_perm, nperm * sizeof(int), cudaMemcpyHostToDevice, S.s));
   // phase image (copied into the scratch when it is on the host) and its id check
   const uint8_t* d_phase = p->phase;
   if (!p->phase_on_device) {
@@ -1058,22 +1039,23 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   a.g = S.g;
   a.dim = d;
   a.green = S.green;
-  a.px = S.px;
-  a.py = S.py;
-  a.pz = S.pz;
+  for (int ax = 0; ax < 3; ++ax) a.pl[ax] = S.pl[ax];
   a.lam0 = S.lam0;
   a.mu0 = S.mu0;
   for (int i = 0; i < 6; ++i) a.eps_bar[i] = S.eps_bar[i];
   a.eps = eps;
   a.phase = d_phase;
   a.coef = (const double*)(base + o_coef);
-  a.spec = (double2*)(base + o_spec);
-  a.twx = (const double2*)(base + o_tw[0]);
-  a.twy = (const double2*)(base + o_tw[1]);
-  a.twz = (const double2*)(base + o_tw[2]);
-  a.kx = (const KTab<double>*)(base + o_kt[0]);
-  a.ky = (const KTab<double>*)(base + o_kt[1]);
-  a.kz = (const KTab<double>*)(base + o_kt[2]);
+  a.specA = (double2*)(base + o_specA);
+  a.specB = (double2*)(base + o_specB);
+  po = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    a.tw[ax] = (const double2*)((const double*)(base + o_tab) + table_offset_tw(S, ax));
+    a.kt[ax] = (const KTab<double>*)((const double*)(base + o_tab) + table_offset_kt(S, ax));
+    a.perm[ax] = (const int*)(base + o_perm) + po;
+    a.pos[ax] = (const int*)(base + o_perm) + po + S.pl[ax].L;
+    po += 2 * (size_t)S.pl[ax].L;
+  }
   a.ctrl = (Ctrl*)(base + o_ctrl);
   a.part_mean = (double*)(base + o_pmean);
   a.part_eta = (double*)(base + o_peta);
@@ -1097,10 +1079,10 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
     a.update = update;
     cudaError_t e;
     if ((e = launch_fwd_x<double>(a, S.s)) != cudaSuccess) return e;
-    if ((e = launch_mid_y<double>(a, dual ? 2 * nc : nc, false, S.s)) != cudaSuccess) return e;
+    if ((e = launch_mid_y<double>(a, false, S.s)) != cudaSuccess) return e;
     if ((e = launch_fourier_z<double>(a, S.s)) != cudaSuccess) return e;
     if ((e = launch_reduce_eta<double>(a, S.s)) != cudaSuccess) return e;
-    if ((e = launch_mid_y<double>(a, nc, true, S.s)) != cudaSuccess) return e;
+    if ((e = launch_mid_y<double>(a, true, S.s)) != cudaSuccess) return e;
     if ((e = launch_inv_x<double>(a, S.s)) != cudaSuccess) return e;
     if (a.want_delta && (e = launch_reduce_delta<double>(a, S.s)) != cudaSuccess) return e;
     return cudaSuccess;
