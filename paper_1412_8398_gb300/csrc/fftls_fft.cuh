@@ -139,10 +139,109 @@ __device__ __forceinline__ void dft_r(T2* v, int R, bool inv) {
   }
 }
 
-// In-place transform of a tile (see the file comment).  tw[t] = e^{-2 pi i t / L}
-// (shared memory).  Ends with __syncthreads().
+// Division by a runtime divisor 1 <= d < 2^31 through a multiply-high and a
+// shift (Granlund and Montgomery 1994), exact for 0 <= n < 2^31.
+struct FastDiv {
+  unsigned int m, s;
+  int d;
+};
+
+__host__ __device__ inline FastDiv make_fastdiv(int d) {
+  unsigned int l = 0;
+  while ((1u << l) < (unsigned int)d) ++l;
+  const unsigned long long m = ((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d + 1ull;
+  FastDiv f;
+  f.m = (unsigned int)m;
+  f.s = l;
+  f.d = d;
+  return f;
+}
+
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+  return (int)((__umulhi((unsigned int)n, f.m) + (unsigned int)n) >> f.s);
+}
+
+// Radix plan of a power-of-two length, identical to the host plan: radix 8
+// stages, led by one radix-4 stage (log2 L = 2 mod 3), two radix-4 stages
+// (log2 L = 1 mod 3, L >= 16) or a single radix-2 stage (L = 2).
+__host__ __device__ constexpr int p2_log(int L) { return L <= 1 ? 0 : 1 + p2_log(L / 2); }
+__host__ __device__ constexpr int p2_nst(int L) {
+  return p2_log(L) % 3 == 0 ? p2_log(L) / 3 : (p2_log(L) % 3 == 2 ? p2_log(L) / 3 + 1 : (p2_log(L) < 3 ? 1 : p2_log(L) / 3 + 1));
+}
+__host__ __device__ constexpr int p2_radix(int L, int s) {
+  return p2_log(L) % 3 == 0 ? 8
+       : p2_log(L) % 3 == 2 ? (s == 0 ? 4 : 8)
+       : p2_log(L) < 3 ? 2
+       : (s < 2 ? 4 : 8);
+}
+__host__ __device__ constexpr int p2_msize(int L, int s) { return s == 0 ? L : p2_msize(L, s - 1) / p2_radix(L, s - 1); }
+
+template <int R, typename T2>
+__device__ __forceinline__ void dft_fixed(T2* v, bool inv) {
+  if (R == 2) dft2(v);
+  else if (R == 4) dft4(v, inv);
+  else dft8(v, inv);
+}
+
+template <int L, int S, typename T2>
+__device__ __forceinline__ void p2_stage(T2* buf, int nblk, int BS, int C, const FastDiv& fc, int ncols, const T2* tw,
+                                         bool inv) {
+  constexpr int R = p2_radix(L, S);
+  constexpr int M = p2_msize(L, S);
+  constexpr int MR = M / R;
+  constexpr int NB = L / R;
+  constexpr int TSTR = L / M;
+  const int total = nblk * NB * ncols;
+  const int rs = MR * C;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int rest = fdiv(idx, fc);
+    const int c = idx - rest * ncols;
+    const int bf = rest & (NB - 1);
+    const int blk = rest / NB;
+    const int b = bf / MR, j = bf & (MR - 1);
+    T2* base = buf + blk * BS + (b * M + j) * C + c;
+    T2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = base[r * rs];
+    if (!inv) {
+      dft_fixed<R>(v, false);
+      if (MR > 1 && j) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * TSTR]);
+      }
+    } else {
+      if (MR > 1 && j) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], tw[j * r * TSTR]);
+      }
+      dft_fixed<R>(v, true);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[r * rs] = v[r];
+  }
+  __syncthreads();
+}
+
+template <int L, typename T2>
+__device__ void tile_fft_p2(T2* buf, int nblk, int BS, int C, int ncols, const T2* tw, bool inv) {
+  constexpr int NST = p2_nst(L);
+  const FastDiv fc = make_fastdiv(ncols);
+  if (!inv) {
+    if constexpr (NST > 0) p2_stage<L, 0>(buf, nblk, BS, C, fc, ncols, tw, false);
+    if constexpr (NST > 1) p2_stage<L, 1>(buf, nblk, BS, C, fc, ncols, tw, false);
+    if constexpr (NST > 2) p2_stage<L, 2>(buf, nblk, BS, C, fc, ncols, tw, false);
+    if constexpr (NST > 3) p2_stage<L, 3>(buf, nblk, BS, C, fc, ncols, tw, false);
+  } else {
+    if constexpr (NST > 3) p2_stage<L, 3>(buf, nblk, BS, C, fc, ncols, tw, true);
+    if constexpr (NST > 2) p2_stage<L, 2>(buf, nblk, BS, C, fc, ncols, tw, true);
+    if constexpr (NST > 1) p2_stage<L, 1>(buf, nblk, BS, C, fc, ncols, tw, true);
+    if constexpr (NST > 0) p2_stage<L, 0>(buf, nblk, BS, C, fc, ncols, tw, true);
+  }
+}
+
+// Mixed-radix transform for any supported length (runtime plan).
 template <typename T2>
-__device__ void tile_fft(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv) {
+__device__ void tile_fft_generic(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv) {
   const int L = p.L;
   for (int si = 0; si < p.nst; ++si) {
     const int s = inv ? p.nst - 1 - si : si;
@@ -184,6 +283,27 @@ __device__ void tile_fft(T2* buf, int nblk, int BS, int C, int ncols, const Axis
         if (r < R) base[r * rs] = v[r];
     }
     __syncthreads();
+  }
+}
+
+// In-place transform of a tile (see the file comment).  tw[t] = e^{-2 pi i t / L}
+// (shared memory).  Power-of-two lengths up to 1024 run a compile-time plan.
+// Ends with __syncthreads() when the length has at least one stage.
+template <typename T2>
+__device__ void tile_fft(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv) {
+  switch (p.L) {
+    case 1: return;
+    case 2: tile_fft_p2<2>(buf, nblk, BS, C, ncols, tw, inv); return;
+    case 4: tile_fft_p2<4>(buf, nblk, BS, C, ncols, tw, inv); return;
+    case 8: tile_fft_p2<8>(buf, nblk, BS, C, ncols, tw, inv); return;
+    case 16: tile_fft_p2<16>(buf, nblk, BS, C, ncols, tw, inv); return;
+    case 32: tile_fft_p2<32>(buf, nblk, BS, C, ncols, tw, inv); return;
+    case 64: tile_fft_p2<64>(buf, nblk, BS, C, ncols, tw, inv); return;
+    case 128: tile_fft_p2<128>(buf, nblk, BS, C, ncols, tw, inv); return;
+    case 256: tile_fft_p2<256>(buf, nblk, BS, C, ncols, tw, inv); return;
+    case 512: tile_fft_p2<512>(buf, nblk, BS, C, ncols, tw, inv); return;
+    case 1024: tile_fft_p2<1024>(buf, nblk, BS, C, ncols, tw, inv); return;
+    default: tile_fft_generic(buf, nblk, BS, C, ncols, p, tw, inv); return;
   }
 }
 

@@ -106,11 +106,67 @@ __device__ __forceinline__ T2* load_twiddles(const T2* __restrict__ tw, int L, T
 
 __host__ __device__ constexpr int odd_stride(int n) { return (n & 1) ? n : n + 1; }
 
+// 16-byte asynchronous copy global -> shared (bypasses registers and L1), so a
+// block keeps all loads of a tile in flight at once.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy `rows` rows of `cols` complex values between a tile (row stride C) and
+// global memory (row stride gstride, in complex values).  Rows of whole 16-byte
+// units with 16-byte aligned starts go through cp.async (loads) and 16-byte
+// vector accesses; anything else element by element.
+template <typename T2>
+__device__ __forceinline__ void tile_load(T2* tile, int C, const T2* g, long long gstride, int rows, int cols) {
+  const bool vec = ((cols * sizeof(T2)) % 16 == 0) && ((C * sizeof(T2)) % 16 == 0) &&
+                   ((gstride * sizeof(T2)) % 16 == 0) && (((size_t)g & 15) == 0);
+  if (vec) {
+    constexpr int PER = 16 / sizeof(T2);
+    const int U = cols / PER;
+    const FastDiv fu = make_fastdiv(U);
+    for (int idx = threadIdx.x; idx < rows * U; idx += blockDim.x) {
+      const int r = fdiv(idx, fu), u = idx - r * U;
+      cp_async16(tile + r * C + u * PER, g + r * gstride + u * PER);
+    }
+    cp_async_wait_all();
+  } else {
+    const FastDiv fc = make_fastdiv(cols);
+    for (int idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
+      const int r = fdiv(idx, fc), cc = idx - r * cols;
+      tile[r * C + cc] = g[r * gstride + cc];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T2>
+__device__ __forceinline__ void tile_store(const T2* tile, int C, T2* g, long long gstride, int rows, int cols) {
+  const bool vec = ((cols * sizeof(T2)) % 16 == 0) && ((C * sizeof(T2)) % 16 == 0) &&
+                   ((gstride * sizeof(T2)) % 16 == 0) && (((size_t)g & 15) == 0);
+  if (vec) {
+    constexpr int PER = 16 / sizeof(T2);
+    const int U = cols / PER;
+    const FastDiv fu = make_fastdiv(U);
+    for (int idx = threadIdx.x; idx < rows * U; idx += blockDim.x) {
+      const int r = fdiv(idx, fu), u = idx - r * U;
+      *reinterpret_cast<float4*>(g + r * gstride + u * PER) = *reinterpret_cast<const float4*>(tile + r * C + u * PER);
+    }
+  } else {
+    const FastDiv fc = make_fastdiv(cols);
+    for (int idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
+      const int r = fdiv(idx, fc), cc = idx - r * cols;
+      g[r * gstride + cc] = tile[r * C + cc];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K1: constitutive law + forward x1 transform (real -> half complex)
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void __launch_bounds__(512) k_fwd_x(IterArgs<T> a) {
+__global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
   if (a.ctrl->state != kRunning) return;
@@ -129,19 +185,37 @@ __global__ void __launch_bounds__(512) k_fwd_x(IterArgs<T> a) {
 #pragma unroll
   for (int c = 0; c < 2 * NC; ++c) acc[c] = 0.0;
 
+  const FastDiv fL = make_fastdiv(L1), fH = make_fastdiv(H), fNP = make_fastdiv(NP);
   for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
     const int nl = (int)min((long long)G, nlines - l0);
     T accf[2 * NC];
 #pragma unroll
     for (int c = 0; c < 2 * NC; ++c) accf[c] = (T)0;
-    for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
-      const int gl = idx / L1, x = idx - gl * L1;
-      const long long vox = (l0 + gl) * (long long)L1 + x;
-      const T* cf = a.coef + (int)a.phase[vox] * kCoef;
+    constexpr int VB = 4;  // voxels per thread whose loads are issued together
+    for (int ib = threadIdx.x; ib < nl * L1; ib += VB * blockDim.x) {
+      T ev[VB][NC];
+      int phv[VB];
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+        const int idx = ib + v * blockDim.x;
+        if (idx < nl * L1) {
+          const int gl = fdiv(idx, fL), x = idx - gl * L1;
+          const long long vox = (l0 + gl) * (long long)L1 + x;
+          phv[v] = a.phase[vox];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ev[v][c] = a.eps[(long long)c * g.N + vox];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+      const int idx = ib + v * blockDim.x;
+      if (idx >= nl * L1) break;
+      const int gl = fdiv(idx, fL), x = idx - gl * L1;
+      const T* cf = a.coef + phv[v] * kCoef;
       const T lam = cf[0], mu2 = cf[1], dlam = cf[2], dmu2 = cf[3];
       T e[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) e[c] = a.eps[(long long)c * g.N + vox];
+      for (int c = 0; c < NC; ++c) e[c] = ev[v][c];
       T tr = e[0] + e[1];
       if (DIM == 3) tr += e[2];
       T out[2 * NC];
@@ -162,11 +236,12 @@ __global__ void __launch_bounds__(512) k_fwd_x(IterArgs<T> a) {
 #pragma unroll
       for (int p = 0; p < NC; ++p) {
         if (p < NP) {
-          T2 v;
-          v.x = out[2 * p];
-          v.y = (2 * p + 1 < nout) ? out[2 * p + 1] : (T)0;
-          row[p] = v;
+          T2 w;
+          w.x = out[2 * p];
+          w.y = (2 * p + 1 < nout) ? out[2 * p + 1] : (T)0;
+          row[p] = w;
         }
+      }
       }
     }
 #pragma unroll
@@ -174,9 +249,9 @@ __global__ void __launch_bounds__(512) k_fwd_x(IterArgs<T> a) {
     __syncthreads();
     tile_fft(tile, nl, BS, CP, NP, a.pl[0], tws, false);
     for (int idx = threadIdx.x; idx < nl * H * NP; idx += blockDim.x) {
-      const int p = idx % NP;
-      const int rest = idx / NP;
-      const int k = rest % H, gl = rest / H;
+      const int rest = fdiv(idx, fNP);
+      const int p = idx - rest * NP;
+      const int gl = fdiv(rest, fH), k = rest - gl * H;
       const T2 Z = tile[gl * BS + __ldg(&pos[k]) * CP + p];
       const T2 Zm = tile[gl * BS + __ldg(&pos[k == 0 ? 0 : L1 - k]) * CP + p];
       T2 A, B;
@@ -216,16 +291,9 @@ __global__ void __launch_bounds__(512) k_mid_y(IterArgs<T> a, int inv) {
   T2* spec = blockIdx.z ? a.specB : a.specA;
   const long long base = ((long long)blockIdx.y * n2 * g.H + x0) * NC;
   const long long rstride = (long long)g.H * NC;
-  for (int idx = threadIdx.x; idx < n2 * cols; idx += blockDim.x) {
-    const int y = idx / cols, cc = idx - y * cols;
-    tile[y * C + cc] = spec[base + y * rstride + cc];
-  }
-  __syncthreads();
+  tile_load(tile, C, spec + base, rstride, n2, cols);
   tile_fft(tile, 1, 0, C, cols, a.pl[1], tws, inv != 0);
-  for (int idx = threadIdx.x; idx < n2 * cols; idx += blockDim.x) {
-    const int y = idx / cols, cc = idx - y * cols;
-    spec[base + y * rstride + cc] = tile[y * C + cc];
-  }
+  tile_store(tile, C, spec + base, rstride, n2, cols);
 }
 
 // ---------------------------------------------------------------------------
@@ -479,16 +547,69 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   T2* spec = kind ? a.specB : a.specA;
   const long long base = ((long long)py * g.H + x0) * NC;
   const long long zstride = (long long)g.n2 * g.H * NC;
-  for (int idx = threadIdx.x; idx < n3 * cols; idx += blockDim.x) {
-    const int z = idx / cols, cc = idx - z * cols;
-    tile[z * C + cc] = spec[base + z * zstride + cc];
-  }
-  __syncthreads();
-  tile_fft(tile, 1, 0, C, cols, a.pl[2], tws, false);
+  const FastDiv fnx = make_fastdiv(nx);
+  tile_load(tile, C, spec + base, zstride, n3, cols);
   const int ym = __ldg(&a.perm[1][py]);
+  if (DIM == 3 && !do_green && !a.corr && !a.write_d64 && a.green != kMS) {
+    // eta only, without the x3 transform: for G^C, G^W, G^R the x3 factor of
+    // k*(q) is a two-point stencil along x3, so by Parseval along x3
+    // sum_{q3} |k*.sigma_hat|^2 = n3 sum_{x3} |f(x3)|^2 with f the divergence in
+    // mixed space (x1, x2 spectral, x3 real).
+    T eta_acc = (T)0;
+    for (int idx = threadIdx.x; idx < n3 * nx; idx += blockDim.x) {
+      const int z = fdiv(idx, fnx), xc = idx - z * nx;
+      const int x = x0 + xc;
+      const int zm = z == 0 ? n3 - 1 : z - 1, zp = z + 1 == n3 ? 0 : z + 1;
+      const KTab<T> tx = a.kt[0][x], ty = a.kt[1][ym];
+      const T2* c0 = tile + z * C + xc * NC;
+      const T2* cm = tile + zm * C + xc * NC;
+      const T2* cp = tile + zp * C + xc * NC;
+      // components (11, 22, 33, 23, 13, 12): row i of the symmetric tensor
+      const int ix[3] = {0, 5, 4}, iy[3] = {5, 1, 3}, iz[3] = {4, 3, 2};
+      T2 bx, by, bz;  // coefficients of sigma_x., sigma_y., sigma_z. (x3 stencil applied below)
+      const T2 ex = cmk<T2>((T)1 + tx.cm1, -tx.sn), ey = cmk<T2>((T)1 + ty.cm1, -ty.sn);  // e^{-iq}
+      if (a.green == kWillot) {
+        bx = cmk<T2>(tx.cm1, -tx.sn);
+        by = cmk<T2>(ty.cm1, -ty.sn);
+      } else if (a.green == kCentered) {
+        bx = cmk<T2>((T)0, -tx.sn);
+        by = cmk<T2>((T)0, -ty.sn);
+      } else {
+        const T2 exm1 = cmk<T2>(tx.cm1, -tx.sn), eym1 = cmk<T2>(ty.cm1, -ty.sn);
+        const T2 exp1 = cmk<T2>((T)1 + ex.x, ex.y), eyp1 = cmk<T2>((T)1 + ey.x, ey.y);
+        bx = cscale(cmul(exm1, eyp1), (T)0.25);
+        by = cscale(cmul(exp1, eym1), (T)0.25);
+        bz = cscale(cmul(exp1, eyp1), (T)0.25);
+      }
+      T sum = (T)0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T2 f;
+        if (a.green == kWillot) {
+          f = cadd(cmul(bx, c0[ix[j]]), cmul(by, c0[iy[j]]));
+          f = cadd(f, csub(cm[iz[j]], c0[iz[j]]));
+        } else if (a.green == kCentered) {
+          f = cadd(cmul(bx, c0[ix[j]]), cmul(by, c0[iy[j]]));
+          f = csub(f, cscale(csub(cp[iz[j]], cm[iz[j]]), (T)0.5));
+        } else {
+          f = cadd(cmul(bx, cadd(c0[ix[j]], cm[ix[j]])), cmul(by, cadd(c0[iy[j]], cm[iy[j]])));
+          f = cadd(f, cmul(bz, csub(cm[iz[j]], c0[iz[j]])));
+        }
+        sum += f.x * f.x + f.y * f.y;
+      }
+      const T wq = (x == 0 || 2 * x == g.n1) ? (T)1 : (T)2;
+      eta_acc += wq * (T)n3 * sum;
+    }
+    double e1[1] = {(double)eta_acc};
+    block_sum<1>(e1);
+    if (threadIdx.x == 0)
+      a.part_eta[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = e1[0];
+    return;
+  }
+  tile_fft(tile, 1, 0, C, cols, a.pl[2], tws, false);
   T eta_acc = (T)0;
   for (int idx = threadIdx.x; idx < n3 * nx; idx += blockDim.x) {
-    const int pz = idx / nx, xc = idx - pz * nx;
+    const int pz = fdiv(idx, fnx), xc = idx - pz * nx;
     const int zm = __ldg(&a.perm[2][pz]);
     T2* mp = tile + pz * C + xc * NC;
     T2 X[NC];
@@ -503,10 +624,7 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   __syncthreads();
   if (do_green) {
     tile_fft(tile, 1, 0, C, cols, a.pl[2], tws, true);
-    for (int idx = threadIdx.x; idx < n3 * cols; idx += blockDim.x) {
-      const int z = idx / cols, cc = idx - z * cols;
-      spec[base + z * zstride + cc] = tile[z * C + cc];
-    }
+    tile_store(tile, C, spec + base, zstride, n3, cols);
   }
   double e1[1] = {(double)eta_acc};
   block_sum<1>(e1);
@@ -582,7 +700,7 @@ __global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts) {
 // K5: inverse x1 transform (half complex -> real) + scheme update
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void __launch_bounds__(512) k_inv_x(IterArgs<T> a) {
+__global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
   constexpr int NPI = (NC + 1) / 2;
@@ -598,12 +716,13 @@ __global__ void __launch_bounds__(512) k_inv_x(IterArgs<T> a) {
   const long long nlines = (long long)g.n2 * g.n3;
   const int G = a.x_lines;
   double dmax[2] = {0.0, 0.0};
+  const FastDiv fL = make_fastdiv(L1), fH = make_fastdiv(H);
   for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
     const int nl = (int)min((long long)G, nlines - l0);
     for (int idx = threadIdx.x; idx < nl * H * NPI; idx += blockDim.x) {
       const int p = idx % NPI;
       const int rest = idx / NPI;
-      const int k = rest % H, gl = rest / H;
+      const int gl = fdiv(rest, fH), k = rest - gl * H;
       const long long m = (l0 + gl) * (long long)H + k;
       T2 A = a.specA[m * NC + 2 * p];
       T2 B;
@@ -624,7 +743,7 @@ __global__ void __launch_bounds__(512) k_inv_x(IterArgs<T> a) {
     __syncthreads();
     tile_fft(tile, nl, BS, CP, NPI, a.pl[0], tws, true);
     for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
-      const int gl = idx / L1, x = idx - gl * L1;
+      const int gl = fdiv(idx, fL), x = idx - gl * L1;
       const long long vox = (l0 + gl) * (long long)L1 + x;
       T e[NC];
 #pragma unroll
