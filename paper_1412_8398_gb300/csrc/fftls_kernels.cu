@@ -273,6 +273,176 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
+// K1 (3D, G^C / G^W / G^R): x1 pass with the equilibrium norm in real space
+// ---------------------------------------------------------------------------
+// For the finite-difference operators the divergence k*(q).sigma_hat(q) is the
+// transform of a stencil applied to sigma on the grid (eq. mul1, wil071 and the
+// rotated stencil of eq. disc3dsig, each scaled to match its k), so by Parseval
+// sum_q |k*.sigma_hat|^2 = N sum_x |div sigma(x)|^2 (eq. criterion).  A block
+// owns m_lines x2-lines and marches over m_planes x3-planes; per plane it
+// computes sigma on its lines plus halo lines, splits each divergence into an
+// in-plane part U and an x3 part V, and keeps one ring entry per voxel so that
+//   W: div(z) = U(z) + V(z) - V(z-1)                  (backward differences)
+//   R: div(z) = U(z) + V(z) + [U - V](z-1)             (backward differences averaged
+//                                                       over the other two axes)
+//   C: div(z-1) = U(z-1) + (V(z) - V(z-2)) / 2         (centred differences)
+// Only tau goes through the transform (then x2, x3 and Gamma as usual).
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_x_march(IterArgs<T> a) {
+  typedef typename Cplx<T>::type T2;
+  constexpr int NC = 6, NP = 3, CP = 3;
+  if (a.ctrl->state != kRunning) return;
+  const Geom g = a.g;
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3, H = g.H;
+  const int green = a.green;
+  const bool cen = green == kCentered;
+  const int G = a.m_lines, Z = a.m_planes;
+  const int nyg = (n2 + G - 1) / G;
+  const int yg = blockIdx.x % nyg, zs = blockIdx.x / nyg;
+  const int y0 = yg * G, ny = min(G, n2 - y0);
+  const int z0 = zs * Z, z1 = min(n3, z0 + Z);
+  const int NL = ny + 1 + (cen ? 1 : 0);  // lines of sigma per plane: y0-1 .. y0+ny-1 (+ y0+ny for C)
+  T2* region;
+  const T2* tws = load_twiddles(a.tw[0], n1, &region);
+  T* S = reinterpret_cast<T*>(region);          // [G + 2][6][n1] sigma of one plane
+  T* ring = S + (size_t)(G + 2) * NC * n1;       // [3 or 9][G][n1]
+  T2* tile = region;                             // tau pairs [G][n1][CP], reuses S
+  const int RS = G * n1;                         // stride between ring components
+  const long long N = g.N;
+  const int* __restrict__ pos = a.pos[0];
+  const FastDiv fL = make_fastdiv(n1), fH = make_fastdiv(H);
+  const int IDX[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+  double accm[2 * NC];
+#pragma unroll
+  for (int c = 0; c < 2 * NC; ++c) accm[c] = 0.0;
+  double acce = 0.0;
+  const int zstart = z0 - (cen ? 2 : 1);
+  const int zend = cen ? z1 : z1 - 1;
+  for (int zz = zstart; zz <= zend; ++zz) {
+    const int z = ((zz % n3) + n3) % n3;
+    const bool core = zz >= z0 && zz < z1;
+    // 1. sigma on the lines of this plane
+    T accf[2 * NC];
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) accf[c] = (T)0;
+    for (int idx = threadIdx.x; idx < NL * n1; idx += blockDim.x) {
+      const int l = fdiv(idx, fL), x = idx - l * n1;
+      const int y = (y0 - 1 + l + n2) % n2;
+      const long long vox = ((long long)z * n2 + y) * n1 + x;
+      const T* cf = a.coef + (int)a.phase[vox] * kCoef;
+      T e[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) e[c] = a.eps[(long long)c * N + vox];
+      const T tr = e[0] + e[1] + e[2];
+      const bool own = core && l >= 1 && l <= ny;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T sg = cf[1] * e[c] + (c < 3 ? cf[0] * tr : (T)0);
+        S[((size_t)l * NC + c) * n1 + x] = sg;
+        if (own) { accf[c] += sg; accf[NC + c] += e[c]; }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) accm[c] += (double)accf[c];
+    __syncthreads();
+    // 2. divergence of the core lines
+    T se = (T)0;
+    const bool valid = cen ? (zz - 1 >= z0) : (zz >= z0);
+    const int zdiv = cen ? ((((zz - 1) % n3) + n3) % n3) : z;
+    for (int idx = threadIdx.x; idx < ny * n1; idx += blockDim.x) {
+      const int li = fdiv(idx, fL), x = idx - li * n1;
+      const int xm = x == 0 ? n1 - 1 : x - 1, xp = x + 1 == n1 ? 0 : x + 1;
+      const T* Lc = S + (size_t)(li + 1) * NC * n1;   // line y
+      const T* Lm = S + (size_t)li * NC * n1;         // line y - 1
+      const T* Lp = S + (size_t)(li + 2) * NC * n1;   // line y + 1 (C only)
+      const int r = li * n1 + x;
+      const long long vdiv = ((long long)zdiv * n2 + (y0 + li)) * n1 + x;
+      T d[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int c0 = IDX[0][j], c1 = IDX[1][j], c2 = IDX[2][j];
+        T U, V;
+        if (green == kWillot) {
+          U = (Lc[c0 * n1 + x] - Lc[c0 * n1 + xm]) + (Lc[c1 * n1 + x] - Lm[c1 * n1 + x]);
+          V = Lc[c2 * n1 + x];
+          d[j] = U + V - ring[j * RS + r];
+          ring[j * RS + r] = V;
+        } else if (green == kRotated) {
+          U = (T)0.25 * ((Lc[c0 * n1 + x] - Lc[c0 * n1 + xm]) + (Lm[c0 * n1 + x] - Lm[c0 * n1 + xm]) +
+                         (Lc[c1 * n1 + x] - Lm[c1 * n1 + x]) + (Lc[c1 * n1 + xm] - Lm[c1 * n1 + xm]));
+          V = (T)0.25 * (Lc[c2 * n1 + x] + Lc[c2 * n1 + xm] + Lm[c2 * n1 + x] + Lm[c2 * n1 + xm]);
+          d[j] = U + V + ring[j * RS + r];
+          ring[j * RS + r] = U - V;
+        } else {
+          U = (T)0.5 * (Lc[c0 * n1 + xp] - Lc[c0 * n1 + xm]) + (T)0.5 * (Lp[c1 * n1 + x] - Lm[c1 * n1 + x]);
+          V = Lc[c2 * n1 + x];
+          // ring: [0..2] U(z-1), [3..5] V(z-1), [6..8] V(z-2)
+          d[j] = ring[j * RS + r] + (T)0.5 * (V - ring[(6 + j) * RS + r]);
+          ring[(6 + j) * RS + r] = ring[(3 + j) * RS + r];
+          ring[(3 + j) * RS + r] = V;
+          ring[j * RS + r] = U;
+        }
+      }
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (a.write_d64) reinterpret_cast<float*>(a.d64)[(long long)j * N + vdiv] = (float)d[j];
+          if (a.corr) d[j] += (T)reinterpret_cast<const float*>(a.d64)[(long long)j * N + vdiv];
+          se += d[j] * d[j];
+        }
+      }
+    }
+    acce += (double)se;
+    __syncthreads();
+    if (!core) continue;
+    // 3. tau of the core lines, x1 transform, half spectrum of tau
+    for (int idx = threadIdx.x; idx < ny * n1; idx += blockDim.x) {
+      const int li = fdiv(idx, fL), x = idx - li * n1;
+      const long long vox = ((long long)z * n2 + (y0 + li)) * n1 + x;
+      const T* cf = a.coef + (int)a.phase[vox] * kCoef;
+      T e[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) e[c] = a.eps[(long long)c * N + vox];
+      const T tr = e[0] + e[1] + e[2];
+      T2* row = tile + ((size_t)li * n1 + x) * CP;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        T2 w;
+        w.x = cf[3] * e[2 * p] + (2 * p < 3 ? cf[2] * tr : (T)0);
+        w.y = cf[3] * e[2 * p + 1] + (2 * p + 1 < 3 ? cf[2] * tr : (T)0);
+        row[p] = w;
+      }
+    }
+    __syncthreads();
+    tile_fft(tile, ny, n1 * CP, CP, NP, a.pl[0], tws, false);
+    for (int idx = threadIdx.x; idx < ny * H * NP; idx += blockDim.x) {
+      const int rest = idx / NP;
+      const int p = idx - rest * NP;
+      const int li = fdiv(rest, fH), k = rest - li * H;
+      const T2 Zv = tile[((size_t)li * n1 + __ldg(&pos[k])) * CP + p];
+      const T2 Zm = tile[((size_t)li * n1 + __ldg(&pos[k == 0 ? 0 : n1 - k])) * CP + p];
+      T2 A, B;
+      A.x = (T)0.5 * (Zv.x + Zm.x);
+      A.y = (T)0.5 * (Zv.y - Zm.y);
+      B.x = (T)0.5 * (Zv.y + Zm.y);
+      B.y = (T)-0.5 * (Zv.x - Zm.x);
+      const long long m = ((long long)z * n2 + (y0 + li)) * H + k;
+      a.specA[m * NC + 2 * p] = A;
+      a.specA[m * NC + 2 * p + 1] = B;
+    }
+    __syncthreads();
+  }
+  block_sum<2 * NC>(accm);
+  double e1[1] = {acce * (double)N};
+  block_sum<1>(e1);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) a.part_mean[(size_t)blockIdx.x * 2 * NC + c] = accm[c];
+    a.part_eta[blockIdx.x] = e1[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K2: transform along x2, in place; tiles of y_w modes x n2 rows x n_c
 // ---------------------------------------------------------------------------
 template <typename T, int NC>
@@ -415,7 +585,7 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
     }
     if (q0) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) { E[c].x = (a.dual && !a.corr) ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
+      for (int c = 0; c < NC; ++c) { E[c].x = (a.tauform && !a.corr) ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
     } else if (nyq) {
       // -C0^{-1}:x / N,  C0^{-1} = I/(2 mu0) - lam0 / (2 mu0 (d lam0 + 2 mu0)) dd
       T2 tr;
@@ -488,7 +658,7 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
     if (!do_green) return;
     if (q0) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) { E[c].x = (a.dual && !a.corr) ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
+      for (int c = 0; c < NC; ++c) { E[c].x = (a.tauform && !a.corr) ? (T)a.eps_bar[c] : (T)0; E[c].y = (T)0; }
     } else {
       T K = (T)0;
       T2 gk, p, r;
@@ -541,7 +711,7 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   const int py = blockIdx.y;
   const int kind = blockIdx.z;
   const bool do_green = kind == 0;
-  const bool do_eta = a.dual ? (kind == 1) : true;
+  const bool do_eta = !a.eta_real && (a.dual ? (kind == 1) : true);
   const int nx = min(W, g.H - x0);
   const int C = W * NC, cols = nx * NC;
   T2* spec = kind ? a.specB : a.specA;
@@ -550,62 +720,6 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   const FastDiv fnx = make_fastdiv(nx);
   tile_load(tile, C, spec + base, zstride, n3, cols);
   const int ym = __ldg(&a.perm[1][py]);
-  if (DIM == 3 && !do_green && !a.corr && !a.write_d64 && a.green != kMS) {
-    // eta only, without the x3 transform: for G^C, G^W, G^R the x3 factor of
-    // k*(q) is a two-point stencil along x3, so by Parseval along x3
-    // sum_{q3} |k*.sigma_hat|^2 = n3 sum_{x3} |f(x3)|^2 with f the divergence in
-    // mixed space (x1, x2 spectral, x3 real).
-    T eta_acc = (T)0;
-    for (int idx = threadIdx.x; idx < n3 * nx; idx += blockDim.x) {
-      const int z = fdiv(idx, fnx), xc = idx - z * nx;
-      const int x = x0 + xc;
-      const int zm = z == 0 ? n3 - 1 : z - 1, zp = z + 1 == n3 ? 0 : z + 1;
-      const KTab<T> tx = a.kt[0][x], ty = a.kt[1][ym];
-      const T2* c0 = tile + z * C + xc * NC;
-      const T2* cm = tile + zm * C + xc * NC;
-      const T2* cp = tile + zp * C + xc * NC;
-      // components (11, 22, 33, 23, 13, 12): row i of the symmetric tensor
-      const int ix[3] = {0, 5, 4}, iy[3] = {5, 1, 3}, iz[3] = {4, 3, 2};
-      T2 bx, by, bz;  // coefficients of sigma_x., sigma_y., sigma_z. (x3 stencil applied below)
-      const T2 ex = cmk<T2>((T)1 + tx.cm1, -tx.sn), ey = cmk<T2>((T)1 + ty.cm1, -ty.sn);  // e^{-iq}
-      if (a.green == kWillot) {
-        bx = cmk<T2>(tx.cm1, -tx.sn);
-        by = cmk<T2>(ty.cm1, -ty.sn);
-      } else if (a.green == kCentered) {
-        bx = cmk<T2>((T)0, -tx.sn);
-        by = cmk<T2>((T)0, -ty.sn);
-      } else {
-        const T2 exm1 = cmk<T2>(tx.cm1, -tx.sn), eym1 = cmk<T2>(ty.cm1, -ty.sn);
-        const T2 exp1 = cmk<T2>((T)1 + ex.x, ex.y), eyp1 = cmk<T2>((T)1 + ey.x, ey.y);
-        bx = cscale(cmul(exm1, eyp1), (T)0.25);
-        by = cscale(cmul(exp1, eym1), (T)0.25);
-        bz = cscale(cmul(exp1, eyp1), (T)0.25);
-      }
-      T sum = (T)0;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        T2 f;
-        if (a.green == kWillot) {
-          f = cadd(cmul(bx, c0[ix[j]]), cmul(by, c0[iy[j]]));
-          f = cadd(f, csub(cm[iz[j]], c0[iz[j]]));
-        } else if (a.green == kCentered) {
-          f = cadd(cmul(bx, c0[ix[j]]), cmul(by, c0[iy[j]]));
-          f = csub(f, cscale(csub(cp[iz[j]], cm[iz[j]]), (T)0.5));
-        } else {
-          f = cadd(cmul(bx, cadd(c0[ix[j]], cm[ix[j]])), cmul(by, cadd(c0[iy[j]], cm[iy[j]])));
-          f = cadd(f, cmul(bz, csub(cm[iz[j]], c0[iz[j]])));
-        }
-        sum += f.x * f.x + f.y * f.y;
-      }
-      const T wq = (x == 0 || 2 * x == g.n1) ? (T)1 : (T)2;
-      eta_acc += wq * (T)n3 * sum;
-    }
-    double e1[1] = {(double)eta_acc};
-    block_sum<1>(e1);
-    if (threadIdx.x == 0)
-      a.part_eta[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = e1[0];
-    return;
-  }
   tile_fft(tile, 1, 0, C, cols, a.pl[2], tws, false);
   T eta_acc = (T)0;
   for (int idx = threadIdx.x; idx < n3 * nx; idx += blockDim.x) {
@@ -626,17 +740,19 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
     tile_fft(tile, 1, 0, C, cols, a.pl[2], tws, true);
     tile_store(tile, C, spec + base, zstride, n3, cols);
   }
-  double e1[1] = {(double)eta_acc};
-  block_sum<1>(e1);
-  if (threadIdx.x == 0)
-    a.part_eta[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = e1[0];
+  if (!a.eta_real) {  // with the real-space eta the x1 pass owns part_eta
+    double e1[1] = {(double)eta_acc};
+    block_sum<1>(e1);
+    if (threadIdx.x == 0)
+      a.part_eta[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = e1[0];
+  }
 }
 
 // ---------------------------------------------------------------------------
 // R: eta, <sigma>, history and stop decision (single block)
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts) {
+__global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts, int n_mean_parts) {
   constexpr int NC = Comp<DIM>::NC;
   Ctrl* ctl = a.ctrl;
   const int st = ctl->state;
@@ -647,7 +763,7 @@ __global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts) {
   double s[2 * NC + 1];
 #pragma unroll
   for (int c = 0; c < 2 * NC + 1; ++c) s[c] = 0.0;
-  for (int b = threadIdx.x; b < a.x_blocks; b += blockDim.x)
+  for (int b = threadIdx.x; b < n_mean_parts; b += blockDim.x)
 #pragma unroll
     for (int c = 0; c < 2 * NC; ++c) s[c] += a.part_mean[(size_t)b * 2 * NC + c];
   for (int b = threadIdx.x; b < n_eta_parts; b += blockDim.x) s[2 * NC] += a.part_eta[b];
@@ -901,7 +1017,8 @@ __global__ void k_sum_parts(const double* part, int blocks, int width, double* o
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) {
-  if (a.dim == 3) k_fwd_x<T, 3><<<a.x_blocks, a.x_threads, a.x1_smem, s>>>(a);
+  if (a.eta_real) k_fwd_x_march<T><<<a.m_blocks, 256, a.m_smem, s>>>(a);
+  else if (a.dim == 3) k_fwd_x<T, 3><<<a.x_blocks, a.x_threads, a.x1_smem, s>>>(a);
   else k_fwd_x<T, 2><<<a.x_blocks, a.x_threads, a.x1_smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -909,7 +1026,7 @@ cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s) {
   if (a.g.n2 == 1) return cudaSuccess;
-  dim3 grid((a.g.H + a.y_w - 1) / a.y_w, a.g.n3, (!inv && a.dual) ? 2 : 1);
+  dim3 grid((a.g.H + a.y_w - 1) / a.y_w, a.g.n3, (!inv && a.dual && !a.eta_real) ? 2 : 1);
   if (a.dim == 3) k_mid_y<T, 6><<<grid, a.y_threads, a.y_smem, s>>>(a, inv ? 1 : 0);
   else k_mid_y<T, 3><<<grid, a.y_threads, a.y_smem, s>>>(a, inv ? 1 : 0);
   return cudaGetLastError();
@@ -917,7 +1034,7 @@ cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s) {
-  dim3 grid((a.g.H + a.z_w - 1) / a.z_w, a.g.n2, a.dual ? 2 : 1);
+  dim3 grid((a.g.H + a.z_w - 1) / a.z_w, a.g.n2, (a.dual && !a.eta_real) ? 2 : 1);
   if (a.dim == 3) k_fourier_z<T, 3><<<grid, a.z_threads, a.z_smem, s>>>(a);
   else k_fourier_z<T, 2><<<grid, a.z_threads, a.z_smem, s>>>(a);
   return cudaGetLastError();
@@ -925,9 +1042,10 @@ cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaStream_t s) {
-  const int nparts = ((a.g.H + a.z_w - 1) / a.z_w) * a.g.n2 * (a.dual ? 2 : 1);
-  if (a.dim == 3) k_reduce_eta<T, 3><<<1, 512, 0, s>>>(a, nparts);
-  else k_reduce_eta<T, 2><<<1, 512, 0, s>>>(a, nparts);
+  const int nparts = a.eta_real ? a.m_blocks : ((a.g.H + a.z_w - 1) / a.z_w) * a.g.n2 * (a.dual ? 2 : 1);
+  const int mparts = a.eta_real ? a.m_blocks : a.x_blocks;
+  if (a.dim == 3) k_reduce_eta<T, 3><<<1, 512, 0, s>>>(a, nparts, mparts);
+  else k_reduce_eta<T, 2><<<1, 512, 0, s>>>(a, nparts, mparts);
   return cudaGetLastError();
 }
 
@@ -949,6 +1067,7 @@ cudaError_t set_kernel_attributes(const IterArgs<T>& a) {
   cudaError_t e = cudaSuccess;
 #define FFTLS_ATTR(fn, bytes)                                                                    \
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));
+  if (a.eta_real) FFTLS_ATTR((k_fwd_x_march<T>), a.m_smem);
   if (a.dim == 3) {
     FFTLS_ATTR((k_fwd_x<T, 3>), a.x1_smem);
     FFTLS_ATTR((k_inv_x<T, 3>), a.x5_smem);

@@ -88,7 +88,10 @@ struct IterArgs {
   int update;        // Update
   int corr;          // 1: correction phase (zero mean mode, eta adds d64)
   int want_delta;    // inverse x1 pass computes max |d eps|, |d sigma|
-  int write_d64;     // eta blocks store k*.sigma_hat (FP32) for a later correction phase
+  int write_d64;     // store the FP64 iterate's divergence (FP32) for a later correction phase
+  int eta_real;      // 1: eta from the real-space divergence stencil in the x1 pass (G^C/W/R, 3D);
+                     //    the forward transform then carries tau only
+  int tauform;       // 1: the transformed field is tau (mean mode = eps_bar); 0: sigma
   T* eps;            // n_c x N (the iterate, or the correction delta)
   const uint8_t* phase;
   const T* coef;     // 256 x kCoef
@@ -108,11 +111,14 @@ struct IterArgs {
   double* eta_hist;    // [max_it]
   double* ms_hist;     // [max_it][nc]
   float* rfield;       // n_c x N defect r (written by kUpdResidual, read by corrections)
-  float2* d64;         // [modes][3]: k*.sigma_hat of the FP64 iterate (phase-free form)
+  float2* d64;         // [modes][3]: k*.sigma_hat of the FP64 iterate (phase-free form), or with
+                       // eta_real [3][N] floats: its real-space divergence
   // launch shapes (host-computed)
   int x_lines, x_blocks, x_threads;
   int y_w, y_threads, z_w, z_threads;
   size_t x1_smem, x5_smem, y_smem, z_smem;
+  int m_lines, m_planes, m_blocks;  // x1 pass with real-space eta: lines x planes per block
+  size_t m_smem;
 };
 
 // Launchers (fftls_kernels.cu).  All return cudaGetLastError().

@@ -358,6 +358,28 @@ bool plan_launch(const Setup& S, IterArgs<T>& a) {
   if (!pick_w(g.n3, &a.z_w, &a.z_smem)) return false;
   a.y_threads = (long long)g.n2 * a.y_w * nc >= 4096 ? 512 : 256;
   a.z_threads = (long long)g.n3 * a.z_w * nc >= 4096 ? 512 : 256;
+  // x1 pass with real-space eta (3D, G^C / G^W / G^R): m_lines lines x m_planes planes
+  a.m_lines = a.m_planes = a.m_blocks = 0;
+  a.m_smem = 0;
+  if (S.dim == 3 && S.green != kMS) {
+    const size_t st = sizeof(T);
+    const int rmul = S.green == kCentered ? 9 : 3;
+    auto need = [&](int G) { return twx + (size_t)(G + 2) * 6 * g.n1 * st + (size_t)rmul * G * g.n1 * st; };
+    int G = 8;
+    while (G > 1 && need(G) > std::min<size_t>(lim, 110 * 1024)) --G;
+    if (G < 2 && need(2) <= lim) G = 2;
+    G = std::min(G, g.n2);
+    if (need(G) <= lim) {
+      const int nyg = (g.n2 + G - 1) / G;
+      const int nzs_want = std::max(1, (2 * S.num_sms + nyg - 1) / nyg);
+      int Z = (g.n3 + nzs_want - 1) / nzs_want;
+      Z = std::max(std::min(Z, 32), std::min(4, g.n3));
+      a.m_lines = G;
+      a.m_planes = Z;
+      a.m_blocks = nyg * ((g.n3 + Z - 1) / Z);
+      a.m_smem = need(G);
+    }
+  }
   return true;
 }
 
@@ -391,7 +413,8 @@ struct Runner {
   }
 
   fftls_status iteration(bool dual, int update, bool prof) {
-    a.dual = dual ? 1 : 0;
+    a.dual = (dual && !a.eta_real) ? 1 : 0;
+    a.tauform = (a.dual || a.eta_real) ? 1 : 0;
     a.update = update;
     fftls_status st;
     if ((st = launch(0, [](Runner* r, cudaStream_t s) { return launch_fwd_x<T>(r->a, s); }, prof))) return st;
@@ -455,7 +478,8 @@ struct Runner {
     const int chunk = (int)std::max<long long>(1, std::min<long long>(32, 40000000LL / std::max<long long>(N, 1)));
     cudaGraphExec_t exec = nullptr;
     if (S.graphs && !S.profile) {
-      a.dual = dual ? 1 : 0;
+      a.dual = (dual && !a.eta_real) ? 1 : 0;
+      a.tauform = (a.dual || a.eta_real) ? 1 : 0;
       a.update = update;
       GraphCache& gc = c->graphs[Prec<T>::idx];
       std::vector<unsigned char> key(sizeof(a) + sizeof(int));
@@ -542,9 +566,11 @@ fftls_status prepare(fftls_ctx* c, const Setup& S, const fftls_problem* p, const
   a.eta_hist = (double*)c->eta_hist.p;
   a.ms_hist = (double*)c->ms_hist.p;
   a.want_delta = o->stop == FFTLS_STOP_MAXDELTA ? 1 : 0;
+  a.eta_real = a.m_blocks > 0 ? 1 : 0;
   const int ntz = (S.g.H + a.z_w - 1) / a.z_w;
-  CUDA_TRY(c, c->part_mean.ensure((size_t)a.x_blocks * 2 * S.nc * sizeof(double)));
-  CUDA_TRY(c, c->part_eta.ensure((size_t)ntz * S.g.n2 * 2 * sizeof(double)));
+  const size_t nparts = std::max<size_t>((size_t)ntz * S.g.n2 * 2, (size_t)a.m_blocks);
+  CUDA_TRY(c, c->part_mean.ensure((size_t)std::max(a.x_blocks, a.m_blocks) * 2 * S.nc * sizeof(double)));
+  CUDA_TRY(c, c->part_eta.ensure(nparts * sizeof(double)));
   CUDA_TRY(c, c->part_delta.ensure((size_t)a.x_blocks * 2 * sizeof(double)));
   a.part_mean = (double*)c->part_mean.p;
   a.part_eta = (double*)c->part_eta.p;
@@ -725,7 +751,7 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
   if (use64 || o->eps_init) CUDA_TRY(c, c->eps64.ensure((size_t)nc * N * sizeof(double)));
   if (ladder) {
     CUDA_TRY(c, c->rfield.ensure((size_t)nc * N * sizeof(float)));
-    CUDA_TRY(c, c->d64.ensure((size_t)S.g.modes * 3 * sizeof(float2)));
+    CUDA_TRY(c, c->d64.ensure(std::max<size_t>((size_t)S.g.modes * 3 * sizeof(float2), (size_t)(3 * N) * sizeof(float))));
   }
   CUDA_TRY(c, c->eta_hist.ensure((size_t)o->max_iter * sizeof(double)));
   CUDA_TRY(c, c->ms_hist.ensure((size_t)o->max_iter * nc * sizeof(double)));
@@ -751,7 +777,10 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
     c->launches += 1;
   }
   const bool direct = p->scheme == FFTLS_DIRECT;
-  const int upd_steady = direct ? kUpdDirectSig : kUpdAccel;
+  // G^C / G^W / G^R in 3D take eta from the real-space stencil and transform tau
+  // only (tau form for both schemes); otherwise AS transforms tau and sigma and
+  // DS uses the sigma form while its iterate is compatible.
+  auto upd_of = [&](bool er) { return direct ? (er ? (int)kUpdDirectTau : (int)kUpdDirectSig) : (int)kUpdAccel; };
   const bool dual_steady = !direct;
   Ctrl ctl;
   memset(&ctl, 0, sizeof(ctl));
@@ -767,11 +796,13 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
   if (o->precision == FFTLS_FP64) {
     Runner<double> R64(c, S);
     if ((st = prepare<double>(c, S, p, o, R64, (double*)c->eps64.p, tab, d_perms))) return st;
-    if ((st = R64.run(ctl, direct && warm, dual_steady, upd_steady, &state))) return st;
+    const bool er = R64.a.eta_real;
+    if ((st = R64.run(ctl, direct && warm && !er, dual_steady, upd_of(er), &state))) return st;
   } else if (o->precision == FFTLS_FP32) {
     Runner<float> R32(c, S);
     if ((st = prepare<float>(c, S, p, o, R32, (float*)c->eps32.p, tab, d_perms))) return st;
-    if ((st = R32.run(ctl, direct && warm, dual_steady, upd_steady, &state))) return st;
+    const bool er = R32.a.eta_real;
+    if ((st = R32.run(ctl, direct && warm && !er, dual_steady, upd_of(er), &state))) return st;
     it32 = c->h_ctrl->it;
   } else {
     // Ladder.  A: plain FP32 iterations until eta <= refine_switch (or a stall).
@@ -779,13 +810,16 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
     if ((st = prepare<float>(c, S, p, o, R32, (float*)c->eps32.p, tab, d_perms))) return st;
     Runner<double> R64(c, S);
     if ((st = prepare<double>(c, S, p, o, R64, (double*)c->eps64.p, tab, d_perms))) return st;
+    // both precisions must measure eta the same way (the FP64 divergence feeds the FP32 estimate)
+    if (R32.a.eta_real != R64.a.eta_real) R32.a.eta_real = R64.a.eta_real = 0;
     Ctrl ca = ctl;
     ca.stop_rule = 0;
     ca.tol = o->refine_switch > 0.0 ? o->refine_switch : std::max(o->tol, 3e-5);
     ca.switch_mode = 1;
     ca.stall_window = 32;
     R32.a.want_delta = 0;
-    if ((st = R32.run(ca, direct && warm, dual_steady, upd_steady, &state))) return st;
+    const bool er = R32.a.eta_real;
+    if ((st = R32.run(ca, direct && warm && !er, dual_steady, upd_of(er), &state))) return st;
     it32 = c->h_ctrl->it;
     ctl = *c->h_ctrl;
     if (state == kSwitch) {
@@ -1076,6 +1110,7 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   NA_TRY(cudaMemcpyAsync(a.ctrl, &ctl, sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
   auto iteration = [&](bool dual, int update) -> cudaError_t {
     a.dual = dual ? 1 : 0;
+    a.tauform = a.dual;
     a.update = update;
     cudaError_t e;
     if ((e = launch_fwd_x<double>(a, S.s)) != cudaSuccess) return e;
