@@ -157,12 +157,12 @@ class ClockSampler:
 
 
 # Algorithmic bytes per launch of each kernel (FP32 bulk; FP64 doubles the
-# scalar size).  The model counts every field read and written once by the pass:
-# fwd_x reads eps (n_c scalars) + phase (1 B) per voxel and writes 2 n_c half-spectrum
-# components (tau and sigma); mid_y_fwd reads and writes 2 n_c components;
-# fourier_z reads and writes the n_c tau components and reads the n_c sigma
-# components; mid_y_inv reads and writes n_c components; inv_x reads n_c
-# components, eps and phase and writes eps.
+# scalar size), for the path the workload takes (3D, G^R: eta from the
+# real-space divergence in the x1 pass, so only tau is transformed).  Every
+# field a pass must touch is counted once: fwd_x reads eps (n_c scalars) and the
+# phase (1 B) per voxel and writes n_c half-spectrum components; mid_y_fwd,
+# fourier_z and mid_y_inv read and write n_c components; inv_x reads n_c
+# components, eps and the phase and writes eps.  Halo re-reads are not counted.
 def kernel_bytes(kind, n, nc=6):
     prec = 8 if kind.endswith("f64") else 4
     cplx = 2 * prec
@@ -170,12 +170,8 @@ def kernel_bytes(kind, n, nc=6):
     half = n * n * (n // 2 + 1)
     k = kind.rsplit("_", 1)[0]
     if k == "fwd_x":
-        return N * (nc * prec + 1) + 2 * nc * half * cplx
-    if k == "mid_y_fwd":
-        return 2 * (2 * nc) * half * cplx
-    if k == "fourier_z":
-        return (2 * nc + nc) * half * cplx
-    if k == "mid_y_inv":
+        return N * (nc * prec + 1) + nc * half * cplx
+    if k in ("mid_y_fwd", "fourier_z", "mid_y_inv"):
         return 2 * nc * half * cplx
     if k == "inv_x":
         return nc * half * cplx + N * (2 * nc * prec + 1)

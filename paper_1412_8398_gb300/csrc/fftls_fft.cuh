@@ -139,6 +139,11 @@ __device__ __forceinline__ void dft_r(T2* v, int R, bool inv) {
   }
 }
 
+// Tiles of x1-lines (few columns) pad one row every 8 rows so that the strided
+// butterflies of the late stages spread over the shared-memory banks.
+__host__ __device__ constexpr int padded_rows(int n) { return n + ((n + 7) >> 3); }
+__device__ __forceinline__ int prow(int e, int pad) { return pad ? e + (e >> 3) : e; }
+
 // Division by a runtime divisor 1 <= d < 2^31 through a multiply-high and a
 // shift (Granlund and Montgomery 1994), exact for 0 <= n < 2^31.
 struct FastDiv {
@@ -185,7 +190,7 @@ __device__ __forceinline__ void dft_fixed(T2* v, bool inv) {
 
 template <int L, int S, typename T2>
 __device__ __forceinline__ void p2_stage(T2* buf, int nblk, int BS, int C, const FastDiv& fc, int ncols, const T2* tw,
-                                         bool inv) {
+                                         bool inv, int pad) {
   constexpr int R = p2_radix(L, S);
   constexpr int M = p2_msize(L, S);
   constexpr int MR = M / R;
@@ -199,10 +204,14 @@ __device__ __forceinline__ void p2_stage(T2* buf, int nblk, int BS, int C, const
     const int bf = rest & (NB - 1);
     const int blk = rest / NB;
     const int b = bf / MR, j = bf & (MR - 1);
-    T2* base = buf + blk * BS + (b * M + j) * C + c;
+    T2* base = buf + blk * BS + c;
+    const int e0 = b * M + j;
+    int off[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) off[r] = pad ? prow(e0 + r * MR, 1) * C : (e0 * C + r * rs);
     T2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = base[r * rs];
+    for (int r = 0; r < R; ++r) v[r] = base[off[r]];
     if (!inv) {
       dft_fixed<R>(v, false);
       if (MR > 1 && j) {
@@ -217,31 +226,32 @@ __device__ __forceinline__ void p2_stage(T2* buf, int nblk, int BS, int C, const
       dft_fixed<R>(v, true);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) base[r * rs] = v[r];
+    for (int r = 0; r < R; ++r) base[off[r]] = v[r];
   }
   __syncthreads();
 }
 
 template <int L, typename T2>
-__device__ void tile_fft_p2(T2* buf, int nblk, int BS, int C, int ncols, const T2* tw, bool inv) {
+__device__ void tile_fft_p2(T2* buf, int nblk, int BS, int C, int ncols, const T2* tw, bool inv, int pad) {
   constexpr int NST = p2_nst(L);
   const FastDiv fc = make_fastdiv(ncols);
   if (!inv) {
-    if constexpr (NST > 0) p2_stage<L, 0>(buf, nblk, BS, C, fc, ncols, tw, false);
-    if constexpr (NST > 1) p2_stage<L, 1>(buf, nblk, BS, C, fc, ncols, tw, false);
-    if constexpr (NST > 2) p2_stage<L, 2>(buf, nblk, BS, C, fc, ncols, tw, false);
-    if constexpr (NST > 3) p2_stage<L, 3>(buf, nblk, BS, C, fc, ncols, tw, false);
+    if constexpr (NST > 0) p2_stage<L, 0>(buf, nblk, BS, C, fc, ncols, tw, false, pad);
+    if constexpr (NST > 1) p2_stage<L, 1>(buf, nblk, BS, C, fc, ncols, tw, false, pad);
+    if constexpr (NST > 2) p2_stage<L, 2>(buf, nblk, BS, C, fc, ncols, tw, false, pad);
+    if constexpr (NST > 3) p2_stage<L, 3>(buf, nblk, BS, C, fc, ncols, tw, false, pad);
   } else {
-    if constexpr (NST > 3) p2_stage<L, 3>(buf, nblk, BS, C, fc, ncols, tw, true);
-    if constexpr (NST > 2) p2_stage<L, 2>(buf, nblk, BS, C, fc, ncols, tw, true);
-    if constexpr (NST > 1) p2_stage<L, 1>(buf, nblk, BS, C, fc, ncols, tw, true);
-    if constexpr (NST > 0) p2_stage<L, 0>(buf, nblk, BS, C, fc, ncols, tw, true);
+    if constexpr (NST > 3) p2_stage<L, 3>(buf, nblk, BS, C, fc, ncols, tw, true, pad);
+    if constexpr (NST > 2) p2_stage<L, 2>(buf, nblk, BS, C, fc, ncols, tw, true, pad);
+    if constexpr (NST > 1) p2_stage<L, 1>(buf, nblk, BS, C, fc, ncols, tw, true, pad);
+    if constexpr (NST > 0) p2_stage<L, 0>(buf, nblk, BS, C, fc, ncols, tw, true, pad);
   }
 }
 
 // Mixed-radix transform for any supported length (runtime plan).
 template <typename T2>
-__device__ void tile_fft_generic(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv) {
+__device__ void tile_fft_generic(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv,
+                                 int pad) {
   const int L = p.L;
   for (int si = 0; si < p.nst; ++si) {
     const int s = inv ? p.nst - 1 - si : si;
@@ -258,11 +268,12 @@ __device__ void tile_fft_generic(T2* buf, int nblk, int BS, int C, int ncols, co
       const int bf = rest % nb;
       const int blk = rest / nb;
       const int b = bf / MR, j = bf - b * MR;
-      T2* base = buf + blk * BS + (b * M + j) * C + c;
+      T2* base = buf + blk * BS + c;
+      const int e0 = b * M + j;
       T2 v[kMaxRadix];
 #pragma unroll
       for (int r = 0; r < kMaxRadix; ++r)
-        if (r < R) v[r] = base[r * rs];
+        if (r < R) v[r] = base[pad ? prow(e0 + r * MR, 1) * C : e0 * C + r * rs];
       if (!inv) {
         dft_r(v, R, false);
         if (j) {
@@ -280,7 +291,7 @@ __device__ void tile_fft_generic(T2* buf, int nblk, int BS, int C, int ncols, co
       }
 #pragma unroll
       for (int r = 0; r < kMaxRadix; ++r)
-        if (r < R) base[r * rs] = v[r];
+        if (r < R) base[pad ? prow(e0 + r * MR, 1) * C : e0 * C + r * rs] = v[r];
     }
     __syncthreads();
   }
@@ -289,21 +300,23 @@ __device__ void tile_fft_generic(T2* buf, int nblk, int BS, int C, int ncols, co
 // In-place transform of a tile (see the file comment).  tw[t] = e^{-2 pi i t / L}
 // (shared memory).  Power-of-two lengths up to 1024 run a compile-time plan.
 // Ends with __syncthreads() when the length has at least one stage.
+// pad = 1: row e of the tile is stored at prow(e) (x1-line tiles).
 template <typename T2>
-__device__ void tile_fft(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv) {
+__device__ void tile_fft(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv,
+                         int pad = 0) {
   switch (p.L) {
     case 1: return;
-    case 2: tile_fft_p2<2>(buf, nblk, BS, C, ncols, tw, inv); return;
-    case 4: tile_fft_p2<4>(buf, nblk, BS, C, ncols, tw, inv); return;
-    case 8: tile_fft_p2<8>(buf, nblk, BS, C, ncols, tw, inv); return;
-    case 16: tile_fft_p2<16>(buf, nblk, BS, C, ncols, tw, inv); return;
-    case 32: tile_fft_p2<32>(buf, nblk, BS, C, ncols, tw, inv); return;
-    case 64: tile_fft_p2<64>(buf, nblk, BS, C, ncols, tw, inv); return;
-    case 128: tile_fft_p2<128>(buf, nblk, BS, C, ncols, tw, inv); return;
-    case 256: tile_fft_p2<256>(buf, nblk, BS, C, ncols, tw, inv); return;
-    case 512: tile_fft_p2<512>(buf, nblk, BS, C, ncols, tw, inv); return;
-    case 1024: tile_fft_p2<1024>(buf, nblk, BS, C, ncols, tw, inv); return;
-    default: tile_fft_generic(buf, nblk, BS, C, ncols, p, tw, inv); return;
+    case 2: tile_fft_p2<2>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    case 4: tile_fft_p2<4>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    case 8: tile_fft_p2<8>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    case 16: tile_fft_p2<16>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    case 32: tile_fft_p2<32>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    case 64: tile_fft_p2<64>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    case 128: tile_fft_p2<128>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    case 256: tile_fft_p2<256>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    case 512: tile_fft_p2<512>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    case 1024: tile_fft_p2<1024>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
+    default: tile_fft_generic(buf, nblk, BS, C, ncols, p, tw, inv, pad); return;
   }
 }
 

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
   const int nout = a.dual ? 2 * NC : NC;
   const int NP = (nout + 1) / 2;
   const int CP = odd_stride(NP);
-  const int BS = L1 * CP;
+  const int BS = padded_rows(L1) * CP;
   const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
   const int G = a.x_lines;
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
           out[c] = s;
         }
       }
-      T2* row = tile + gl * BS + x * CP;
+      T2* row = tile + gl * BS + prow(x, 1) * CP;
 #pragma unroll
       for (int p = 0; p < NC; ++p) {
         if (p < NP) {
@@ -247,13 +247,13 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
 #pragma unroll
     for (int c = 0; c < 2 * NC; ++c) acc[c] += (double)accf[c];
     __syncthreads();
-    tile_fft(tile, nl, BS, CP, NP, a.pl[0], tws, false);
+    tile_fft(tile, nl, BS, CP, NP, a.pl[0], tws, false, 1);
     for (int idx = threadIdx.x; idx < nl * H * NP; idx += blockDim.x) {
       const int rest = fdiv(idx, fNP);
       const int p = idx - rest * NP;
       const int gl = fdiv(rest, fH), k = rest - gl * H;
-      const T2 Z = tile[gl * BS + __ldg(&pos[k]) * CP + p];
-      const T2 Zm = tile[gl * BS + __ldg(&pos[k == 0 ? 0 : L1 - k]) * CP + p];
+      const T2 Z = tile[gl * BS + prow(__ldg(&pos[k]), 1) * CP + p];
+      const T2 Zm = tile[gl * BS + prow(__ldg(&pos[k == 0 ? 0 : L1 - k]), 1) * CP + p];
       T2 A, B;
       A.x = (T)0.5 * (Z.x + Zm.x);
       A.y = (T)0.5 * (Z.y - Zm.y);
@@ -279,14 +279,28 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
 // transform of a stencil applied to sigma on the grid (eq. mul1, wil071 and the
 // rotated stencil of eq. disc3dsig, each scaled to match its k), so by Parseval
 // sum_q |k*.sigma_hat|^2 = N sum_x |div sigma(x)|^2 (eq. criterion).  A block
-// owns m_lines x2-lines and marches over m_planes x3-planes; per plane it
-// computes sigma on its lines plus halo lines, splits each divergence into an
-// in-plane part U and an x3 part V, and keeps one ring entry per voxel so that
+// owns m_lines x2-lines and marches over m_planes x3-planes.  Each thread owns
+// x1-columns and walks the block's lines (plus halo lines) in x2 order:
+// neighbours along x1 come from warp shuffles, the previous line stays in
+// registers.  The divergence splits into an in-plane part U and an x3 part V,
+// with one ring entry per voxel carried from plane to plane:
 //   W: div(z) = U(z) + V(z) - V(z-1)                  (backward differences)
 //   R: div(z) = U(z) + V(z) + [U - V](z-1)             (backward differences averaged
 //                                                       over the other two axes)
 //   C: div(z-1) = U(z-1) + (V(z) - V(z-2)) / 2         (centred differences)
-// Only tau goes through the transform (then x2, x3 and Gamma as usual).
+// Only tau goes through the x1 transform (then x2, x3 and Gamma as usual).
+template <typename T>
+__device__ __forceinline__ void sigma_of(const T* __restrict__ eps, const uint8_t* __restrict__ phase,
+                                         const T* __restrict__ coef, long long N, long long v, T* s) {
+  const T* cf = coef + (int)phase[v] * kCoef;
+  T e[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) e[c] = eps[(long long)c * N + v];
+  const T tr = e[0] + e[1] + e[2];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s[c] = cf[1] * e[c] + (c < 3 ? cf[0] * tr : (T)0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd_x_march(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
@@ -301,16 +315,19 @@ __global__ void __launch_bounds__(256) k_fwd_x_march(IterArgs<T> a) {
   const int yg = blockIdx.x % nyg, zs = blockIdx.x / nyg;
   const int y0 = yg * G, ny = min(G, n2 - y0);
   const int z0 = zs * Z, z1 = min(n3, z0 + Z);
-  const int NL = ny + 1 + (cen ? 1 : 0);  // lines of sigma per plane: y0-1 .. y0+ny-1 (+ y0+ny for C)
-  T2* region;
-  const T2* tws = load_twiddles(a.tw[0], n1, &region);
-  T* S = reinterpret_cast<T*>(region);          // [G + 2][6][n1] sigma of one plane
-  T* ring = S + (size_t)(G + 2) * NC * n1;       // [3 or 9][G][n1]
-  T2* tile = region;                             // tau pairs [G][n1][CP], reuses S
-  const int RS = G * n1;                         // stride between ring components
+  const int NL = ny + (cen ? 2 : 1);  // lines walked per plane: y0-1 .. y0+ny-1 (+ y0+ny for C)
+  T2* tile;
+  const T2* tws = load_twiddles(a.tw[0], n1, &tile);
+  const int BS = padded_rows(n1) * CP;
+  T* ring = reinterpret_cast<T*>(tile + (size_t)G * BS);  // [3 or 9][G][n1]
+  const int RS = G * n1;
   const long long N = g.N;
   const int* __restrict__ pos = a.pos[0];
-  const FastDiv fL = make_fastdiv(n1), fH = make_fastdiv(H);
+  const FastDiv fH = make_fastdiv(H);
+  const int lane = threadIdx.x & 31;
+  const T* __restrict__ eps = a.eps;
+  const uint8_t* __restrict__ phase = a.phase;
+  const T* __restrict__ coef = a.coef;
   const int IDX[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
   double accm[2 * NC];
 #pragma unroll
@@ -321,106 +338,148 @@ __global__ void __launch_bounds__(256) k_fwd_x_march(IterArgs<T> a) {
   for (int zz = zstart; zz <= zend; ++zz) {
     const int z = ((zz % n3) + n3) % n3;
     const bool core = zz >= z0 && zz < z1;
-    // 1. sigma on the lines of this plane
+    const bool valid = cen ? (zz - 1 >= z0) : (zz >= z0);
+    const int zdiv = cen ? ((((zz - 1) % n3) + n3) % n3) : z;
     T accf[2 * NC];
 #pragma unroll
     for (int c = 0; c < 2 * NC; ++c) accf[c] = (T)0;
-    for (int idx = threadIdx.x; idx < NL * n1; idx += blockDim.x) {
-      const int l = fdiv(idx, fL), x = idx - l * n1;
-      const int y = (y0 - 1 + l + n2) % n2;
-      const long long vox = ((long long)z * n2 + y) * n1 + x;
-      const T* cf = a.coef + (int)a.phase[vox] * kCoef;
-      T e[NC];
+    T se = (T)0;
+    for (int xb = 0; xb < n1; xb += blockDim.x) {
+      const int x = xb + threadIdx.x;
+      const bool inx = x < n1;
+      const int xl = inx ? x : n1 - 1;
+      const int xm = xl == 0 ? n1 - 1 : xl - 1, xp = xl + 1 == n1 ? 0 : xl + 1;
+      const bool own_m = lane == 0 || xl == 0;
+      const bool own_p = lane == 31 || xl + 1 == n1;
+      T p1[6], p1m[6], p1p[6], p2[6];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) e[c] = a.eps[(long long)c * N + vox];
-      const T tr = e[0] + e[1] + e[2];
-      const bool own = core && l >= 1 && l <= ny;
+      for (int c = 0; c < 6; ++c) p1[c] = p1m[c] = p1p[c] = p2[c] = (T)0;
+      // prefetch of the first line's voxel
+      T en[6];
+      int phn;
+      const long long plane = (long long)z * n2;
+      int y = y0 == 0 ? n2 - 1 : y0 - 1;  // first line of the walk (halo), periodic
+      {
+        const long long v = (plane + y) * n1 + xl;
+        phn = phase[v];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const T sg = cf[1] * e[c] + (c < 3 ? cf[0] * tr : (T)0);
-        S[((size_t)l * NC + c) * n1 + x] = sg;
-        if (own) { accf[c] += sg; accf[NC + c] += e[c]; }
+        for (int c = 0; c < 6; ++c) en[c] = eps[(long long)c * N + v];
+      }
+      for (int l = 0; l < NL; ++l) {
+        const long long vrow = (plane + y) * n1;
+        const int ynext = y + 1 == n2 ? 0 : y + 1;
+        T e[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) e[c] = en[c];
+        const int ph = phn;
+        if (l + 1 < NL) {  // issue the next line's loads before working on this one
+          const long long v = (plane + ynext) * n1 + xl;
+          phn = phase[v];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) en[c] = eps[(long long)c * N + v];
+        }
+        const T* cf = coef + ph * kCoef;
+        const T tr = e[0] + e[1] + e[2];
+        T s0[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s0[c] = cf[1] * e[c] + (c < 3 ? cf[0] * tr : (T)0);
+        const bool coreline = core && l >= 1 && l <= ny;
+        if (coreline && inx) {
+          T2* row = tile + (size_t)(l - 1) * BS + prow(x, 1) * CP;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            T2 w;
+            w.x = cf[3] * e[2 * p] + (2 * p < 3 ? cf[2] * tr : (T)0);
+            w.y = cf[3] * e[2 * p + 1] + (2 * p + 1 < 3 ? cf[2] * tr : (T)0);
+            row[p] = w;
+          }
+#pragma unroll
+          for (int c = 0; c < 6; ++c) { accf[c] += s0[c]; accf[NC + c] += e[c]; }
+        }
+        // neighbours along x1
+        T sm[6], sp[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sm[c] = __shfl_up_sync(0xffffffffu, s0[c], 1);
+        if (own_m) sigma_of(eps, phase, coef, N, vrow + xm, sm);
+        if (cen) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) sp[c] = __shfl_down_sync(0xffffffffu, s0[c], 1);
+          if (own_p) sigma_of(eps, phase, coef, N, vrow + xp, sp);
+        }
+        int li = -1;
+        T d[3];
+        if (!cen && l >= 1) {
+          li = l - 1;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const int c0 = IDX[0][j], c1 = IDX[1][j], c2 = IDX[2][j];
+            if (green == kWillot) {
+              const T U = (s0[c0] - sm[c0]) + (s0[c1] - p1[c1]);
+              const T V = s0[c2];
+              if (inx) {
+                T& rg = ring[j * RS + li * n1 + x];
+                d[j] = U + V - rg;
+                rg = V;
+              }
+            } else {
+              const T U = (T)0.25 * ((s0[c0] - sm[c0]) + (p1[c0] - p1m[c0]) + (s0[c1] - p1[c1]) + (sm[c1] - p1m[c1]));
+              const T V = (T)0.25 * (s0[c2] + sm[c2] + p1[c2] + p1m[c2]);
+              if (inx) {
+                T& rg = ring[j * RS + li * n1 + x];
+                d[j] = U + V + rg;
+                rg = U - V;
+              }
+            }
+          }
+        } else if (cen && l >= 2) {
+          li = l - 2;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const int c0 = IDX[0][j], c1 = IDX[1][j], c2 = IDX[2][j];
+            const T U = (T)0.5 * (p1p[c0] - p1m[c0]) + (T)0.5 * (s0[c1] - p2[c1]);
+            const T V = p1[c2];
+            if (inx) {
+              // ring: [0..2] U(z-1), [3..5] V(z-1), [6..8] V(z-2)
+              const int r = li * n1 + x;
+              d[j] = ring[j * RS + r] + (T)0.5 * (V - ring[(6 + j) * RS + r]);
+              ring[(6 + j) * RS + r] = ring[(3 + j) * RS + r];
+              ring[(3 + j) * RS + r] = V;
+              ring[j * RS + r] = U;
+            }
+          }
+        }
+        if (li >= 0 && valid && inx) {
+          const long long vdiv = ((long long)zdiv * n2 + (y0 + li)) * n1 + x;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            if (a.write_d64) reinterpret_cast<float*>(a.d64)[(long long)j * N + vdiv] = (float)d[j];
+            if (a.corr) d[j] += (T)reinterpret_cast<const float*>(a.d64)[(long long)j * N + vdiv];
+            se += d[j] * d[j];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          p2[c] = p1[c];
+          p1[c] = s0[c];
+          p1m[c] = sm[c];
+          if (cen) p1p[c] = sp[c];
+        }
+        y = ynext;
       }
     }
 #pragma unroll
     for (int c = 0; c < 2 * NC; ++c) accm[c] += (double)accf[c];
-    __syncthreads();
-    // 2. divergence of the core lines
-    T se = (T)0;
-    const bool valid = cen ? (zz - 1 >= z0) : (zz >= z0);
-    const int zdiv = cen ? ((((zz - 1) % n3) + n3) % n3) : z;
-    for (int idx = threadIdx.x; idx < ny * n1; idx += blockDim.x) {
-      const int li = fdiv(idx, fL), x = idx - li * n1;
-      const int xm = x == 0 ? n1 - 1 : x - 1, xp = x + 1 == n1 ? 0 : x + 1;
-      const T* Lc = S + (size_t)(li + 1) * NC * n1;   // line y
-      const T* Lm = S + (size_t)li * NC * n1;         // line y - 1
-      const T* Lp = S + (size_t)(li + 2) * NC * n1;   // line y + 1 (C only)
-      const int r = li * n1 + x;
-      const long long vdiv = ((long long)zdiv * n2 + (y0 + li)) * n1 + x;
-      T d[3];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int c0 = IDX[0][j], c1 = IDX[1][j], c2 = IDX[2][j];
-        T U, V;
-        if (green == kWillot) {
-          U = (Lc[c0 * n1 + x] - Lc[c0 * n1 + xm]) + (Lc[c1 * n1 + x] - Lm[c1 * n1 + x]);
-          V = Lc[c2 * n1 + x];
-          d[j] = U + V - ring[j * RS + r];
-          ring[j * RS + r] = V;
-        } else if (green == kRotated) {
-          U = (T)0.25 * ((Lc[c0 * n1 + x] - Lc[c0 * n1 + xm]) + (Lm[c0 * n1 + x] - Lm[c0 * n1 + xm]) +
-                         (Lc[c1 * n1 + x] - Lm[c1 * n1 + x]) + (Lc[c1 * n1 + xm] - Lm[c1 * n1 + xm]));
-          V = (T)0.25 * (Lc[c2 * n1 + x] + Lc[c2 * n1 + xm] + Lm[c2 * n1 + x] + Lm[c2 * n1 + xm]);
-          d[j] = U + V + ring[j * RS + r];
-          ring[j * RS + r] = U - V;
-        } else {
-          U = (T)0.5 * (Lc[c0 * n1 + xp] - Lc[c0 * n1 + xm]) + (T)0.5 * (Lp[c1 * n1 + x] - Lm[c1 * n1 + x]);
-          V = Lc[c2 * n1 + x];
-          // ring: [0..2] U(z-1), [3..5] V(z-1), [6..8] V(z-2)
-          d[j] = ring[j * RS + r] + (T)0.5 * (V - ring[(6 + j) * RS + r]);
-          ring[(6 + j) * RS + r] = ring[(3 + j) * RS + r];
-          ring[(3 + j) * RS + r] = V;
-          ring[j * RS + r] = U;
-        }
-      }
-      if (valid) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          if (a.write_d64) reinterpret_cast<float*>(a.d64)[(long long)j * N + vdiv] = (float)d[j];
-          if (a.corr) d[j] += (T)reinterpret_cast<const float*>(a.d64)[(long long)j * N + vdiv];
-          se += d[j] * d[j];
-        }
-      }
-    }
     acce += (double)se;
     __syncthreads();
     if (!core) continue;
-    // 3. tau of the core lines, x1 transform, half spectrum of tau
-    for (int idx = threadIdx.x; idx < ny * n1; idx += blockDim.x) {
-      const int li = fdiv(idx, fL), x = idx - li * n1;
-      const long long vox = ((long long)z * n2 + (y0 + li)) * n1 + x;
-      const T* cf = a.coef + (int)a.phase[vox] * kCoef;
-      T e[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) e[c] = a.eps[(long long)c * N + vox];
-      const T tr = e[0] + e[1] + e[2];
-      T2* row = tile + ((size_t)li * n1 + x) * CP;
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        T2 w;
-        w.x = cf[3] * e[2 * p] + (2 * p < 3 ? cf[2] * tr : (T)0);
-        w.y = cf[3] * e[2 * p + 1] + (2 * p + 1 < 3 ? cf[2] * tr : (T)0);
-        row[p] = w;
-      }
-    }
-    __syncthreads();
-    tile_fft(tile, ny, n1 * CP, CP, NP, a.pl[0], tws, false);
+    // x1 transform of tau on the core lines, half spectrum of tau
+    tile_fft(tile, ny, BS, CP, NP, a.pl[0], tws, false, 1);
     for (int idx = threadIdx.x; idx < ny * H * NP; idx += blockDim.x) {
       const int rest = idx / NP;
       const int p = idx - rest * NP;
       const int li = fdiv(rest, fH), k = rest - li * H;
-      const T2 Zv = tile[((size_t)li * n1 + __ldg(&pos[k])) * CP + p];
-      const T2 Zm = tile[((size_t)li * n1 + __ldg(&pos[k == 0 ? 0 : n1 - k])) * CP + p];
+      const T2 Zv = tile[(size_t)li * BS + prow(__ldg(&pos[k]), 1) * CP + p];
+      const T2 Zm = tile[(size_t)li * BS + prow(__ldg(&pos[k == 0 ? 0 : n1 - k]), 1) * CP + p];
       T2 A, B;
       A.x = (T)0.5 * (Zv.x + Zm.x);
       A.y = (T)0.5 * (Zv.y - Zm.y);
@@ -827,7 +886,7 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
   const int L1 = g.n1, H = g.H;
   T2* tile;
   const T2* tws = load_twiddles(a.tw[0], L1, &tile);
-  const int BS = L1 * CP;
+  const int BS = padded_rows(L1) * CP;
   const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
   const int G = a.x_lines;
@@ -848,23 +907,23 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
       T2 z;
       z.x = A.x - B.y;
       z.y = A.y + B.x;
-      tile[gl * BS + __ldg(&pos[k]) * CP + p] = z;
+      tile[gl * BS + prow(__ldg(&pos[k]), 1) * CP + p] = z;
       if (k > 0 && L1 - k >= H) {
         T2 zm;
         zm.x = A.x + B.y;
         zm.y = B.x - A.y;
-        tile[gl * BS + __ldg(&pos[L1 - k]) * CP + p] = zm;
+        tile[gl * BS + prow(__ldg(&pos[L1 - k]), 1) * CP + p] = zm;
       }
     }
     __syncthreads();
-    tile_fft(tile, nl, BS, CP, NPI, a.pl[0], tws, true);
+    tile_fft(tile, nl, BS, CP, NPI, a.pl[0], tws, true, 1);
     for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
       const int gl = fdiv(idx, fL), x = idx - gl * L1;
       const long long vox = (l0 + gl) * (long long)L1 + x;
       T e[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const T2 v = tile[gl * BS + x * CP + c / 2];
+        const T2 v = tile[gl * BS + prow(x, 1) * CP + c / 2];
         e[c] = (c & 1) ? v.y : v.x;
       }
       T o[NC], n[NC];

@@ -331,8 +331,8 @@ bool plan_launch(const Setup& S, IterArgs<T>& a) {
   const long long nlines = (long long)g.n2 * g.n3;
   // x kernels: lines per block so that a tile is ~64 KB (at least one line)
   const size_t twx = (size_t)even_up(g.n1) * cb;
-  const size_t line1 = (size_t)g.n1 * odd_up(nc) * cb;             // forward, tau and sigma pairs
-  const size_t line5 = (size_t)g.n1 * odd_up((nc + 1) / 2) * cb;  // inverse
+  const size_t line1 = (size_t)padded_rows(g.n1) * odd_up(nc) * cb;             // forward, tau and sigma pairs
+  const size_t line5 = (size_t)padded_rows(g.n1) * odd_up((nc + 1) / 2) * cb;  // inverse
   if (twx + line1 > lim) return false;
   int G = (int)std::max<size_t>(1, (64 * 1024) / line1);
   G = (int)std::min<long long>(G, nlines);
@@ -364,9 +364,9 @@ bool plan_launch(const Setup& S, IterArgs<T>& a) {
   if (S.dim == 3 && S.green != kMS) {
     const size_t st = sizeof(T);
     const int rmul = S.green == kCentered ? 9 : 3;
-    auto need = [&](int G) { return twx + (size_t)(G + 2) * 6 * g.n1 * st + (size_t)rmul * G * g.n1 * st; };
+    auto need = [&](int G) { return twx + (size_t)G * padded_rows(g.n1) * 3 * cb + (size_t)rmul * G * g.n1 * st; };
     int G = 8;
-    while (G > 1 && need(G) > std::min<size_t>(lim, 110 * 1024)) --G;
+    while (G > 1 && need(G) > std::min<size_t>(lim, 100 * 1024)) --G;
     if (G < 2 && need(2) <= lim) G = 2;
     G = std::min(G, g.n2);
     if (need(G) <= lim) {
