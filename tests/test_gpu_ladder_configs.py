@@ -1,0 +1,184 @@
+"""GPU: the FP32 -> FP64 precision ladder, the configuration shapes and
+full-size properties, against the FP64 oracle or against what holds exactly.
+
+* Ladder: the returned field's eta is recomputed by the oracle (FP64, from the
+  field alone) and must be <= tol; moduli agree with the FP64 solve to 1e-6.
+* 2D 128^2 centred disc and 3D 128^3 Boolean spheres (three contrasts): parity
+  with the oracle (fields 1e-9 max-abs, <sigma> 1e-10 relative).
+* 512^3, the benchmark's launch configuration: a homogeneous medium converges
+  in one iteration to eps_bar exactly; a laminate reproduces the exact
+  piecewise-constant solution (G^R and G^W are exact for any layer widths).
+"""
+import numpy as np
+import pytest
+
+from oracle import fftls_oracle as O
+from paper_1412_8398_gb300 import microstructure as MS
+
+pytestmark = pytest.mark.gpu
+FIELD_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def solver():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_8398_gb300 import build, fftls
+    build.build()
+    s = fftls.Solver(0)
+    yield s
+    s.close()
+
+
+def comps(t):
+    d = t.shape[0]
+    if d == 3:
+        return np.stack([t[0, 0], t[1, 1], t[2, 2], t[1, 2], t[0, 2], t[0, 1]])
+    return np.stack([t[0, 0], t[1, 1], t[0, 1]])
+
+
+def tensor(f):
+    if f.shape[0] == 6:
+        t = np.zeros((3, 3) + f.shape[1:])
+        t[0, 0], t[1, 1], t[2, 2] = f[0], f[1], f[2]
+        t[1, 2] = t[2, 1] = f[3]
+        t[0, 2] = t[2, 0] = f[4]
+        t[0, 1] = t[1, 0] = f[5]
+    else:
+        t = np.zeros((2, 2) + f.shape[1:])
+        t[0, 0], t[1, 1] = f[0], f[1]
+        t[0, 1] = t[1, 0] = f[2]
+    return t
+
+
+def oracle_eta(ph, lam, mu, strain, green):
+    """eta of eq. criterion recomputed by the oracle from a strain field."""
+    d = ph.ndim
+    eps = tensor(np.asarray(strain))
+    Cs = [O.stiffness_tensor(lam[a], mu[a], d) for a in range(len(lam))]
+    sig = O._contract(Cs, ph, eps)
+    k = O.wave_vector(O.grid_shape_xyz(ph), green)
+    return O.equilibrium_eta(sig, k)[0]
+
+
+GREENS = ["MS", "C", "W", "R"]
+
+
+@pytest.mark.parametrize("green", range(4))
+@pytest.mark.parametrize("scheme", ["AS", "DS"])
+def test_ladder_reaches_tolerance_and_matches_fp64(solver, green, scheme):
+    ph, _ = MS.boolean_spheres((32, 32, 32), 3.0, 0.3, seed=21)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (1000.0, 0.2)] if scheme == "AS" else [(1.0, 0.3), (20.0, 0.3)])
+    eb = np.diag([1.0, 0.0, 0.0])
+    tol = 1e-6
+    mix = solver.solve(ph, lam, mu, eb, GREENS[green], scheme, tol=tol, max_iter=5000, precision="fp32_refine64")
+    f64 = solver.solve(ph, lam, mu, eb, GREENS[green], scheme, tol=tol, max_iter=5000, precision="fp64")
+    assert mix.converged and f64.converged
+    assert mix.iterations_fp32 >= mix.iterations - 4      # the bulk of the work runs in FP32
+    assert oracle_eta(ph, lam, mu, mix.strain, green) <= tol * 1.0001
+    rel = np.abs(mix.mean_stress - f64.mean_stress).max() / np.abs(f64.mean_stress).max()
+    assert rel < 1e-6
+    assert abs(mix.mean_strain[0] - 1.0) < tol
+
+
+def test_fp32_only_floor(solver):
+    """Plain FP32 stalls above a tight tolerance (its rounding floor); the ladder does not."""
+    ph, _ = MS.boolean_spheres((32, 32, 32), 3.0, 0.3, seed=22)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (1000.0, 0.2)])
+    r32 = solver.solve(ph, lam, mu, np.diag([1.0, 0, 0]), "R", "AS", tol=1e-9, max_iter=1500, precision="fp32")
+    rmix = solver.solve(ph, lam, mu, np.diag([1.0, 0, 0]), "R", "AS", tol=1e-9, max_iter=1500,
+                        precision="fp32_refine64")
+    assert not r32.converged
+    assert rmix.converged
+
+
+def test_config_2d_disc(solver):
+    """128^2 centred disc, f = 0.25, E 1 / 100, nu 0.3, eps_bar_12 = 1, G^R direct scheme (FP64)."""
+    ph = MS.centered_disc(128, 0.25)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (100.0, 0.3)])
+    eb = np.array([[0.0, 1.0], [1.0, 0.0]])
+    ref = O.solve(ph, lam, mu, eb, O.ROTATED, O.DIRECT, tol=1e-8, max_iter=5000)
+    got = solver.solve(ph, lam, mu, eb, "R", "DS", tol=1e-8, max_iter=5000)
+    assert ref["converged"] and got.converged and got.iterations == ref["iterations"]
+    assert np.abs(got.strain - comps(ref["strain"])).max() < FIELD_TOL
+    ms = np.array([ref["mean_stress"][0, 0], ref["mean_stress"][1, 1], ref["mean_stress"][0, 1]])
+    assert np.abs(got.mean_stress - ms).max() < 1e-10 * np.abs(ms).max()
+    # the symmetric discretisations keep the disc's symmetry, G^W does not (Sec. 4.1)
+    for green, sym in [("MS", True), ("C", True), ("W", False)]:
+        r = solver.solve(ph, lam, mu, eb, green, "AS", tol=1e-8, max_iter=5000)
+        s12 = r.stress[2]
+        asym = max(np.abs(s12 - s12[::-1, ::-1]).max(), np.abs(s12 - s12.T).max())
+        assert (asym < 1e-6) if sym else (asym > 1e-3)
+
+
+@pytest.mark.parametrize("contrast", [0.01, 10.0, 1000.0])
+def test_config_128_boolean_parity(solver, contrast):
+    """128^3 Boolean spheres (radius 6, f = 0.3): two iterations of every discretisation agree with the oracle."""
+    ph, _ = MS.boolean_spheres((128, 128, 128), 6.0, 0.3, seed=1)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (contrast, 0.3)])
+    eb = np.diag([1.0, 0.0, 0.0])
+    green, scheme = {0.01: (O.ROTATED, O.ACCELERATED), 10.0: (O.WILLOT, O.DIRECT),
+                     1000.0: (O.ROTATED, O.ACCELERATED)}[contrast]
+    ref = O.solve(ph, lam, mu, eb, green, scheme, tol=0.0, max_iter=2)
+    got = solver.solve(ph, lam, mu, eb, GREENS[green], ["DS", "AS"][scheme], tol=0.0, max_iter=2)
+    assert np.abs(got.strain - comps(ref["strain"])).max() < FIELD_TOL
+    np.testing.assert_allclose(got.eta_history, ref["eta_history"], rtol=1e-9)
+
+
+def _laminate_exact(layers, lam, mu, eb):
+    lam_x, mu_x = lam[layers], mu[layers]
+    M = lam_x + 2 * mu_x
+    others = eb[1, 1] + eb[2, 2]
+    S = (eb[0, 0] + np.mean(lam_x / M) * others) / np.mean(1 / M)
+    out = np.zeros((6, layers.size))
+    out[0] = (S - lam_x * others) / M
+    out[1], out[2], out[3] = eb[1, 1], eb[2, 2], eb[1, 2]
+    out[4] = (2 * eb[0, 2] / np.mean(1 / mu_x)) / (2 * mu_x)
+    out[5] = (2 * eb[0, 1] / np.mean(1 / mu_x)) / (2 * mu_x)
+    return out
+
+
+def test_full_size_512_properties(solver):
+    """512^3 (the benchmark's size and launch configuration): exact special cases."""
+    torch = pytest.importorskip("torch")
+    n = 512
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (1000.0, 0.2)])
+    eb = np.array([[1.0, 0.2, 0.1], [0.2, -0.3, 0.05], [0.1, 0.05, 0.4]])
+    # homogeneous medium: eps = eps_bar exactly after one eta evaluation per precision
+    # (the ladder certifies the FP32 result with one FP64 evaluation)
+    hom = torch.zeros((n, n, n), dtype=torch.uint8, device="cuda")
+    r = solver.solve(hom, lam[:1], mu[:1], eb, "R", "AS", tol=1e-6, precision="fp32_refine64",
+                     want_stress=False)
+    assert r.converged and r.iterations_fp32 == 1 and r.iterations == 2
+    ebv = np.array([eb[0, 0], eb[1, 1], eb[2, 2], eb[1, 2], eb[0, 2], eb[0, 1]])
+    assert float((r.strain - torch.tensor(ebv, device="cuda").view(6, 1, 1, 1)).abs().max()) < 1e-7
+    del r
+    # laminate with uneven layer widths along x1: exact solution for G^R
+    rng = np.random.default_rng(5)
+    layers = (rng.random(n) < 0.4).astype(np.uint8)
+    img = np.broadcast_to(layers, (n, n, n)).copy()
+    dph = torch.from_numpy(img).cuda()
+    r = solver.solve(dph, lam, mu, eb, "R", "AS", tol=1e-9, max_iter=3000, precision="fp32_refine64",
+                     want_stress=False)
+    assert r.converged
+    exact = _laminate_exact(layers, lam, mu, eb)
+    got = r.strain[:, 0, 0, :].cpu().numpy()                     # any (x2, x3): fields depend on x1 only
+    assert np.abs(got - exact).max() < 1e-7 * np.abs(exact).max()
+    spread = float((r.strain - r.strain[:, :1, :1, :]).abs().max())
+    assert spread < 1e-7 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("shape_np", [(1, 1, 1), (1, 1), (1, 2, 1024), (3, 1, 1)])
+def test_degenerate_and_maximum_lengths(solver, shape_np):
+    """Single voxel, single-pixel 2D grid, the longest supported axis, unit axes."""
+    rng = np.random.default_rng(0)
+    ph = (rng.random(shape_np) < 0.5).astype(np.uint8)
+    d = ph.ndim
+    lam, mu = MS.binary_moduli(7.0, d)
+    eb = np.eye(d) * 0.5
+    eb[0, d - 1] = eb[d - 1, 0] = 0.25
+    for g in range(4):
+        ref = O.solve(ph, lam, mu, eb, g, O.ACCELERATED, tol=0.0, max_iter=3)
+        got = solver.solve(ph, lam, mu, eb, GREENS[g], "AS", tol=0.0, max_iter=3)
+        assert np.abs(got.strain - comps(ref["strain"])).max() < FIELD_TOL
