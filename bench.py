@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=128)
-    ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--cpu-iters", type=int, default=5)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 time-to-tolerance solve")
     return ap.parse_args()
 
 
@@ -70,6 +71,18 @@ def mandel_load(J):
     e = np.zeros(6)
     e[J] = 1.0 if J < 3 else 1.0 / math.sqrt(2.0)
     return e
+
+
+def load_case(rank, i, world):
+    """Mandel load index of step i on this rank: ranks interleave over the six loads."""
+    return (rank + i * world) % 6
+
+
+def replica_totals(ms, voxel_iters, world):
+    """Whole-job figures of independent replicas: max time over ranks, summed work."""
+    ms_max = allreduce([ms], _max_op(world), world)[0]
+    vox_total = allreduce([float(voxel_iters)], _sum_op(world), world)[0]
+    return ms_max, vox_total, vox_total / (ms_max / 1e3)
 
 
 def dist_setup():
@@ -289,7 +302,7 @@ def main():
               want_strain=False, want_stress=False, history=False, device_outputs=True, stream=stream)
 
     def step(i, **extra):
-        J = (rank + i * world) % 6
+        J = load_case(rank, i, world)
         opts = dict(kw)
         opts.update(extra)
         r = solver.solve(dph, lam, mu, mandel_load(J), **opts)
@@ -319,9 +332,7 @@ def main():
     clocks = clk.stop()
     k1, _ = solver.counters()
     ms = ev0.elapsed_time(ev1)
-    ms_max = allreduce([ms], _max_op(world), world)[0]
-    vox_total = allreduce([float(N) * iters], _sum_op(world), world)[0]
-    value = vox_total / (ms_max / 1e3)
+    ms_max, vox_total, value = replica_totals(ms, float(N) * iters, world)
 
     # roofline: the same steps again with per-kernel CUDA events
     prof = {}
@@ -352,16 +363,33 @@ def main():
         t = time.perf_counter()
         e_iters = 0
         for i in range(args.steps):
-            J = (rank + i * world) % 6
+            J = load_case(rank, i, world)
             r = solver.solve(hph, lam, mu, mandel_load(J), green="R", scheme="AS", tol=1e-6,
                              max_iter=args.max_iter, precision=args.precision, want_strain=False,
                              want_stress=False, history=False, device_outputs=False)
             e_iters += r.iterations
         dt = time.perf_counter() - t
-        dt_max = allreduce([dt], _max_op(world), world)[0]
-        e_tot = allreduce([float(N) * e_iters], _sum_op(world), world)[0]
-        e2e = {"value": e_tot / dt_max, "unit": UNIT, "h2d_bytes_per_step": int(N),
+        _, _, e_value = replica_totals(dt * 1e3, float(N) * e_iters, world)
+        e2e = {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": int(N),
                "d2h_bytes_per_step": 2 * 6 * 8}
+
+    # the metric's comparison: one load case solved with plain FP64 iterations, same tolerance
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64":
+        J = load_case(rank, 0, world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r64 = solver.solve(dph, lam, mu, mandel_load(J), **dict(kw, precision="fp64"))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rl = solver.solve(dph, lam, mu, mandel_load(J), **kw)
+        rel = float(np.abs(rl.mean_stress - r64.mean_stress).max() / np.abs(r64.mean_stress).max())
+        fp64 = {"load": int(J), "fp64_time_to_tol_s": e0.elapsed_time(e1) / 1e3,
+                "fp64_iterations": int(r64.iterations), "fp64_converged": bool(r64.converged),
+                "fp64_voxel_iters_per_s": float(N) * r64.iterations / (e0.elapsed_time(e1) / 1e3),
+                "ladder_vs_fp64_mean_stress_rel": rel}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -378,6 +406,7 @@ def main():
                        "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "single GPU"},
             "iterations_per_step": iters / args.steps, "fp32_iterations_per_step": its32 / args.steps,
             "time_to_tol_s": ms_max / 1e3 / args.steps,
+            "vs_fp64": fp64,
             "gpu_launches": k1 - k0,
             "clocks": clocks,
             "roofline": roofline,
