@@ -171,17 +171,20 @@ class ClockSampler:
 
 # Algorithmic bytes per launch of each kernel (FP32 bulk; FP64 doubles the
 # scalar size), for the path the workload takes (3D, G^R: eta from the
-# real-space divergence in the x1 pass, so only tau is transformed).  Every
-# field a pass must touch is counted once: fwd_x reads eps (n_c scalars) and the
-# phase (1 B) per voxel and writes n_c half-spectrum components; mid_y_fwd,
-# fourier_z and mid_y_inv read and write n_c components; inv_x reads n_c
-# components, eps and the phase and writes eps.  Halo re-reads are not counted.
+# real-space divergence stencil, so only tau is transformed).  Every field a
+# pass must touch is counted once: eta_x reads eps (n_c scalars) and the phase
+# (1 B) per voxel; fwd_x reads the same and writes n_c half-spectrum
+# components; mid_y_fwd, fourier_z and mid_y_inv read and write n_c components;
+# inv_x reads n_c components, eps and the phase and writes eps.  Halo re-reads
+# are not counted.
 def kernel_bytes(kind, n, nc=6):
     prec = 8 if kind.endswith("f64") else 4
     cplx = 2 * prec
     N = n ** 3
     half = n * n * (n // 2 + 1)
     k = kind.rsplit("_", 1)[0]
+    if k == "eta_x":
+        return N * (nc * prec + 1)
     if k == "fwd_x":
         return N * (nc * prec + 1) + nc * half * cplx
     if k in ("mid_y_fwd", "fourier_z", "mid_y_inv"):
@@ -408,6 +411,7 @@ def main():
             "time_to_tol_s": ms_max / 1e3 / args.steps,
             "vs_fp64": fp64,
             "gpu_launches": k1 - k0,
+            "tile_plans": solver.tile_plans(),
             "clocks": clocks,
             "roofline": roofline,
             "e2e": e2e,

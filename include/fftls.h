@@ -88,13 +88,17 @@ typedef struct {
   int stop;                 /* FFTLS_STOP_* */
   int max_iter;             /* >= 1; caps `iterations` over all precision phases */
   int precision;            /* FFTLS_FP64, FFTLS_FP32_REFINE64, FFTLS_FP32 */
-  double refine_switch;     /* FP32_REFINE64: eta at which float hands over to double; <= 0 means tol */
+  double refine_switch;     /* FP32_REFINE64: eta at which float hands over to double; <= 0 selects max(tol, 3e-5) */
   const double* eps_init;   /* optional initial strain (n_c x N, FP64); NULL starts from eps_bar */
   int eps_init_on_device;   /* 1: eps_init is a device pointer */
   int fields_on_device;     /* 1: result->strain / stress are device pointers */
   void* stream;             /* cudaStream_t to run on; NULL uses the context's own stream */
   int use_graphs;           /* 1 (default): capture chunks of iterations as CUDA graphs */
   int profile;              /* 1: time every kernel with CUDA events (no graphs); see fftls_profile */
+  int autotune;             /* 1 (default): on the first solve of a grid, operator and precision on this
+                               context, time candidate tile schedules of every kernel on the device and keep
+                               the fastest (see fftls_tile_plans); 0: built-in schedule.  The schedule changes
+                               no per-line or per-mode arithmetic, only the grouping of partial sums. */
 } fftls_options;
 
 typedef struct {
@@ -172,6 +176,16 @@ fftls_status fftls_supported_length(int L);
  * names[i] (static strings), total_ms[i], launches[i] for i < *count;
  * *count is the capacity on entry and the number of kernels on return. */
 fftls_status fftls_profile(const fftls_ctx* ctx, const char** names, double* total_ms, int* launches, int* count);
+
+/* Tile schedules held by this context, one row of FFTLS_PLAN_FIELDS ints per grid,
+ * operator and precision: {precision (0 float, 1 double), n1, n2, n3, green,
+ * lines per block of the forward x1 pass, of the inverse x1 pass, modes per tile
+ * of the x2 pass, of the x3 pass, x3-planes per block of the real-space eta
+ * kernel, 1 if tuned on the device else 0}.  Copies min(*count, held) rows into
+ * `rows` (may be NULL when *count is 0) and returns the number held in *count.
+ * The paper has no counterpart (an implementation detail of the GPU path). */
+#define FFTLS_PLAN_FIELDS 11
+fftls_status fftls_tile_plans(const fftls_ctx* ctx, int* rows, int* count);
 
 /* Kernels launched on this context since creation (nodes of CUDA graphs
  * counted one by one, including kernels that exit early once the solve has

@@ -165,7 +165,7 @@ __device__ __forceinline__ void tile_store(const T2* tile, int C, T2* g, long lo
 // ---------------------------------------------------------------------------
 // K1: constitutive law + forward x1 transform (real -> half complex)
 // ---------------------------------------------------------------------------
-template <typename T, int DIM>
+template <typename T, int DIM, bool DUAL>
 __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
@@ -174,13 +174,13 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
   const int L1 = g.n1, H = g.H;
   T2* tile;
   const T2* tws = load_twiddles(a.tw[0], L1, &tile);
-  const int nout = a.dual ? 2 * NC : NC;
-  const int NP = (nout + 1) / 2;
+  constexpr int nout = DUAL ? 2 * NC : NC;
+  constexpr int NP = (nout + 1) / 2;
   const int CP = odd_stride(NP);
   const int BS = padded_rows(L1) * CP;
   const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
-  const int G = a.x_lines;
+  const int G = a.x1_lines;
   double acc[2 * NC];
 #pragma unroll
   for (int c = 0; c < 2 * NC; ++c) acc[c] = 0.0;
@@ -218,18 +218,18 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
       for (int c = 0; c < NC; ++c) e[c] = ev[v][c];
       T tr = e[0] + e[1];
       if (DIM == 3) tr += e[2];
-      T out[2 * NC];
+      T out[nout];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const bool diag = c < DIM;
         const T s = mu2 * e[c] + (diag ? lam * tr : (T)0);
         accf[c] += s;
         accf[NC + c] += e[c];
-        if (a.dual) {
+        if (DUAL) {
           out[c] = dmu2 * e[c] + (diag ? dlam * tr : (T)0);
           out[NC + c] = s;
         } else {
-          out[c] = s;
+          out[c] = a.tauform ? dmu2 * e[c] + (diag ? dlam * tr : (T)0) : s;
         }
       }
       T2* row = tile + gl * BS + prow(x, 1) * CP;
@@ -273,22 +273,26 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
-// K1 (3D, G^C / G^W / G^R): x1 pass with the equilibrium norm in real space
+// E (3D, G^C / G^W / G^R): the equilibrium norm from the real-space divergence
 // ---------------------------------------------------------------------------
 // For the finite-difference operators the divergence k*(q).sigma_hat(q) is the
 // transform of a stencil applied to sigma on the grid (eq. mul1, wil071 and the
 // rotated stencil of eq. disc3dsig, each scaled to match its k), so by Parseval
-// sum_q |k*.sigma_hat|^2 = N sum_x |div sigma(x)|^2 (eq. criterion).  A block
-// owns m_lines x2-lines and marches over m_planes x3-planes.  Each thread owns
-// x1-columns and walks the block's lines (plus halo lines) in x2 order:
-// neighbours along x1 come from warp shuffles, the previous line stays in
-// registers.  The divergence splits into an in-plane part U and an x3 part V,
-// with one ring entry per voxel carried from plane to plane:
+// sum_q |k*.sigma_hat|^2 = N sum_x |div sigma(x)|^2 (eq. criterion) and only tau
+// has to go through the FFT.  A block owns a tile of kEX x1-columns by kEY
+// x2-rows and marches over e_planes x3-planes: per plane it evaluates sigma on
+// the tile and its halo into shared memory (double-buffered, one barrier per
+// plane), then each thread forms the in-plane part U and the x3 part V of the
+// divergence of its voxels and combines them with a per-voxel ring carried in
+// registers from plane to plane:
 //   W: div(z) = U(z) + V(z) - V(z-1)                  (backward differences)
 //   R: div(z) = U(z) + V(z) + [U - V](z-1)             (backward differences averaged
 //                                                       over the other two axes)
 //   C: div(z-1) = U(z-1) + (V(z) - V(z-2)) / 2         (centred differences)
-// Only tau goes through the x1 transform (then x2, x3 and Gamma as usual).
+constexpr int kEX = kEtaTileX, kEY = kEtaTileY, kEThreads = 256;
+constexpr int kERows = kEThreads / kEX;     // thread rows; each thread owns kEY / kERows voxels
+constexpr int kEOwn = kEY / kERows;
+
 template <typename T>
 __device__ __forceinline__ void sigma_of(const T* __restrict__ eps, const uint8_t* __restrict__ phase,
                                          const T* __restrict__ coef, long long N, long long v, T* s) {
@@ -301,204 +305,104 @@ __device__ __forceinline__ void sigma_of(const T* __restrict__ eps, const uint8_
   for (int c = 0; c < 6; ++c) s[c] = cf[1] * e[c] + (c < 3 ? cf[0] * tr : (T)0);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_x_march(IterArgs<T> a) {
-  typedef typename Cplx<T>::type T2;
-  constexpr int NC = 6, NP = 3, CP = 3;
+__device__ __forceinline__ int wrap_index(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+template <typename T, bool CEN>
+__global__ void __launch_bounds__(kEThreads) k_eta_stencil(IterArgs<T> a) {
   if (a.ctrl->state != kRunning) return;
   const Geom g = a.g;
-  const int n1 = g.n1, n2 = g.n2, n3 = g.n3, H = g.H;
-  const int green = a.green;
-  const bool cen = green == kCentered;
-  const int G = a.m_lines, Z = a.m_planes;
-  const int nyg = (n2 + G - 1) / G;
-  const int yg = blockIdx.x % nyg, zs = blockIdx.x / nyg;
-  const int y0 = yg * G, ny = min(G, n2 - y0);
-  const int z0 = zs * Z, z1 = min(n3, z0 + Z);
-  const int NL = ny + (cen ? 2 : 1);  // lines walked per plane: y0-1 .. y0+ny-1 (+ y0+ny for C)
-  T2* tile;
-  const T2* tws = load_twiddles(a.tw[0], n1, &tile);
-  const int BS = padded_rows(n1) * CP;
-  T* ring = reinterpret_cast<T*>(tile + (size_t)G * BS);  // [3 or 9][G][n1]
-  const int RS = G * n1;
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
   const long long N = g.N;
-  const int* __restrict__ pos = a.pos[0];
-  const FastDiv fH = make_fastdiv(H);
-  const int lane = threadIdx.x & 31;
+  const int ntx = (n1 + kEX - 1) / kEX, nty = (n2 + kEY - 1) / kEY;
+  const int bx = blockIdx.x % ntx, rest = blockIdx.x / ntx;
+  const int by = rest % nty, bz = rest / nty;
+  const int x0 = bx * kEX, y0 = by * kEY;
+  const int z0 = bz * a.e_planes, z1 = min(n3, z0 + a.e_planes);
+  // shared tile of sigma: [2 buffers][6][SY][SX]; tile voxel (xl, yl) at (yl + 1, xl + 1)
+  constexpr int SX = kEX + 2, SY = kEY + 2;
+  constexpr int HC = CEN ? SX : SX - 1, HR = CEN ? SY : SY - 1;  // filled halo: both sides (C) or -1 only
+  constexpr int PL = SY * SX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sS = reinterpret_cast<T*>(smem_raw);
   const T* __restrict__ eps = a.eps;
   const uint8_t* __restrict__ phase = a.phase;
   const T* __restrict__ coef = a.coef;
+  const int tx = threadIdx.x % kEX, ty = threadIdx.x / kEX;
   const int IDX[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
-  double accm[2 * NC];
+  // smem x offsets of the halo columns: column i of the tile is x0 - 1 + i (wrapped)
+  T rg[kEOwn][CEN ? 9 : 3];
 #pragma unroll
-  for (int c = 0; c < 2 * NC; ++c) accm[c] = 0.0;
+  for (int k = 0; k < kEOwn; ++k)
+#pragma unroll
+    for (int i = 0; i < (CEN ? 9 : 3); ++i) rg[k][i] = (T)0;
   double acce = 0.0;
-  const int zstart = z0 - (cen ? 2 : 1);
-  const int zend = cen ? z1 : z1 - 1;
+  const int zstart = z0 - (CEN ? 2 : 1);
+  const int zend = CEN ? z1 : z1 - 1;
   for (int zz = zstart; zz <= zend; ++zz) {
-    const int z = ((zz % n3) + n3) % n3;
-    const bool core = zz >= z0 && zz < z1;
-    const bool valid = cen ? (zz - 1 >= z0) : (zz >= z0);
-    const int zdiv = cen ? ((((zz - 1) % n3) + n3) % n3) : z;
-    T accf[2 * NC];
+    const int z = wrap_index(zz, n3);
+    T* S = sS + ((zz - zstart) & 1) * 6 * PL;
+    const long long plane = (long long)z * n2;
+    for (int e = threadIdx.x; e < HR * HC; e += kEThreads) {
+      const int r = e / HC, ci = e - r * HC;
+      const int y = wrap_index(y0 - 1 + r, n2), x = wrap_index(x0 - 1 + ci, n1);
+      T s[6];
+      sigma_of(eps, phase, coef, N, (plane + y) * n1 + x, s);
 #pragma unroll
-    for (int c = 0; c < 2 * NC; ++c) accf[c] = (T)0;
+      for (int c = 0; c < 6; ++c) S[c * PL + r * SX + ci] = s[c];
+    }
+    __syncthreads();
+    const bool valid = CEN ? (zz - 1 >= z0) : (zz >= z0);
+    const int zdiv = CEN ? wrap_index(zz - 1, n3) : z;
     T se = (T)0;
-    for (int xb = 0; xb < n1; xb += blockDim.x) {
-      const int x = xb + threadIdx.x;
-      const bool inx = x < n1;
-      const int xl = inx ? x : n1 - 1;
-      const int xm = xl == 0 ? n1 - 1 : xl - 1, xp = xl + 1 == n1 ? 0 : xl + 1;
-      const bool own_m = lane == 0 || xl == 0;
-      const bool own_p = lane == 31 || xl + 1 == n1;
-      T p1[6], p1m[6], p1p[6], p2[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) p1[c] = p1m[c] = p1p[c] = p2[c] = (T)0;
-      // prefetch of the first line's voxel
-      T en[6];
-      int phn;
-      const long long plane = (long long)z * n2;
-      int y = y0 == 0 ? n2 - 1 : y0 - 1;  // first line of the walk (halo), periodic
-      {
-        const long long v = (plane + y) * n1 + xl;
-        phn = phase[v];
+    for (int k = 0; k < kEOwn; ++k) {
+      const int yl = ty + k * kERows;
+      const int x = x0 + tx, y = y0 + yl;
+      const T* P = S + (yl + 1) * SX + (tx + 1);  // this voxel's sigma, component stride PL
+      T d[3];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) en[c] = eps[(long long)c * N + v];
+      for (int j = 0; j < 3; ++j) {
+        const int c0 = IDX[0][j], c1 = IDX[1][j], c2 = IDX[2][j];
+        if (CEN) {
+          const T U = (T)0.5 * (P[c0 * PL + 1] - P[c0 * PL - 1]) + (T)0.5 * (P[c1 * PL + SX] - P[c1 * PL - SX]);
+          const T V = P[c2 * PL];
+          // ring: [j] U(z-1), [3 + j] V(z-1), [6 + j] V(z-2)
+          d[j] = rg[k][j] + (T)0.5 * (V - rg[k][6 + j]);
+          rg[k][6 + j] = rg[k][3 + j];
+          rg[k][3 + j] = V;
+          rg[k][j] = U;
+        } else if (a.green == kWillot) {
+          const T U = (P[c0 * PL] - P[c0 * PL - 1]) + (P[c1 * PL] - P[c1 * PL - SX]);
+          const T V = P[c2 * PL];
+          d[j] = U + V - rg[k][j];
+          rg[k][j] = V;
+        } else {
+          const T s00 = P[c0 * PL], s0m = P[c0 * PL - 1], s0y = P[c0 * PL - SX], s0my = P[c0 * PL - SX - 1];
+          const T s10 = P[c1 * PL], s1m = P[c1 * PL - 1], s1y = P[c1 * PL - SX], s1my = P[c1 * PL - SX - 1];
+          const T U = (T)0.25 * ((s00 - s0m) + (s0y - s0my) + (s10 - s1y) + (s1m - s1my));
+          const T V = (T)0.25 * (P[c2 * PL] + P[c2 * PL - 1] + P[c2 * PL - SX] + P[c2 * PL - SX - 1]);
+          d[j] = U + V + rg[k][j];
+          rg[k][j] = U - V;
+        }
       }
-      for (int l = 0; l < NL; ++l) {
-        const long long vrow = (plane + y) * n1;
-        const int ynext = y + 1 == n2 ? 0 : y + 1;
-        T e[6];
+      if (valid && x < n1 && y < n2) {
+        const long long vdiv = ((long long)zdiv * n2 + y) * n1 + x;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) e[c] = en[c];
-        const int ph = phn;
-        if (l + 1 < NL) {  // issue the next line's loads before working on this one
-          const long long v = (plane + ynext) * n1 + xl;
-          phn = phase[v];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) en[c] = eps[(long long)c * N + v];
+        for (int j = 0; j < 3; ++j) {
+          if (a.write_d64) reinterpret_cast<float*>(a.d64)[(long long)j * N + vdiv] = (float)d[j];
+          if (a.corr) d[j] += (T)reinterpret_cast<const float*>(a.d64)[(long long)j * N + vdiv];
+          se += d[j] * d[j];
         }
-        const T* cf = coef + ph * kCoef;
-        const T tr = e[0] + e[1] + e[2];
-        T s0[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) s0[c] = cf[1] * e[c] + (c < 3 ? cf[0] * tr : (T)0);
-        const bool coreline = core && l >= 1 && l <= ny;
-        if (coreline && inx) {
-          T2* row = tile + (size_t)(l - 1) * BS + prow(x, 1) * CP;
-#pragma unroll
-          for (int p = 0; p < NP; ++p) {
-            T2 w;
-            w.x = cf[3] * e[2 * p] + (2 * p < 3 ? cf[2] * tr : (T)0);
-            w.y = cf[3] * e[2 * p + 1] + (2 * p + 1 < 3 ? cf[2] * tr : (T)0);
-            row[p] = w;
-          }
-#pragma unroll
-          for (int c = 0; c < 6; ++c) { accf[c] += s0[c]; accf[NC + c] += e[c]; }
-        }
-        // neighbours along x1
-        T sm[6], sp[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) sm[c] = __shfl_up_sync(0xffffffffu, s0[c], 1);
-        if (own_m) sigma_of(eps, phase, coef, N, vrow + xm, sm);
-        if (cen) {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) sp[c] = __shfl_down_sync(0xffffffffu, s0[c], 1);
-          if (own_p) sigma_of(eps, phase, coef, N, vrow + xp, sp);
-        }
-        int li = -1;
-        T d[3];
-        if (!cen && l >= 1) {
-          li = l - 1;
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            const int c0 = IDX[0][j], c1 = IDX[1][j], c2 = IDX[2][j];
-            if (green == kWillot) {
-              const T U = (s0[c0] - sm[c0]) + (s0[c1] - p1[c1]);
-              const T V = s0[c2];
-              if (inx) {
-                T& rg = ring[j * RS + li * n1 + x];
-                d[j] = U + V - rg;
-                rg = V;
-              }
-            } else {
-              const T U = (T)0.25 * ((s0[c0] - sm[c0]) + (p1[c0] - p1m[c0]) + (s0[c1] - p1[c1]) + (sm[c1] - p1m[c1]));
-              const T V = (T)0.25 * (s0[c2] + sm[c2] + p1[c2] + p1m[c2]);
-              if (inx) {
-                T& rg = ring[j * RS + li * n1 + x];
-                d[j] = U + V + rg;
-                rg = U - V;
-              }
-            }
-          }
-        } else if (cen && l >= 2) {
-          li = l - 2;
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            const int c0 = IDX[0][j], c1 = IDX[1][j], c2 = IDX[2][j];
-            const T U = (T)0.5 * (p1p[c0] - p1m[c0]) + (T)0.5 * (s0[c1] - p2[c1]);
-            const T V = p1[c2];
-            if (inx) {
-              // ring: [0..2] U(z-1), [3..5] V(z-1), [6..8] V(z-2)
-              const int r = li * n1 + x;
-              d[j] = ring[j * RS + r] + (T)0.5 * (V - ring[(6 + j) * RS + r]);
-              ring[(6 + j) * RS + r] = ring[(3 + j) * RS + r];
-              ring[(3 + j) * RS + r] = V;
-              ring[j * RS + r] = U;
-            }
-          }
-        }
-        if (li >= 0 && valid && inx) {
-          const long long vdiv = ((long long)zdiv * n2 + (y0 + li)) * n1 + x;
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            if (a.write_d64) reinterpret_cast<float*>(a.d64)[(long long)j * N + vdiv] = (float)d[j];
-            if (a.corr) d[j] += (T)reinterpret_cast<const float*>(a.d64)[(long long)j * N + vdiv];
-            se += d[j] * d[j];
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          p2[c] = p1[c];
-          p1[c] = s0[c];
-          p1m[c] = sm[c];
-          if (cen) p1p[c] = sp[c];
-        }
-        y = ynext;
       }
     }
-#pragma unroll
-    for (int c = 0; c < 2 * NC; ++c) accm[c] += (double)accf[c];
     acce += (double)se;
-    __syncthreads();
-    if (!core) continue;
-    // x1 transform of tau on the core lines, half spectrum of tau
-    tile_fft(tile, ny, BS, CP, NP, a.pl[0], tws, false, 1);
-    for (int idx = threadIdx.x; idx < ny * H * NP; idx += blockDim.x) {
-      const int rest = idx / NP;
-      const int p = idx - rest * NP;
-      const int li = fdiv(rest, fH), k = rest - li * H;
-      const T2 Zv = tile[(size_t)li * BS + prow(__ldg(&pos[k]), 1) * CP + p];
-      const T2 Zm = tile[(size_t)li * BS + prow(__ldg(&pos[k == 0 ? 0 : n1 - k]), 1) * CP + p];
-      T2 A, B;
-      A.x = (T)0.5 * (Zv.x + Zm.x);
-      A.y = (T)0.5 * (Zv.y - Zm.y);
-      B.x = (T)0.5 * (Zv.y + Zm.y);
-      B.y = (T)-0.5 * (Zv.x - Zm.x);
-      const long long m = ((long long)z * n2 + (y0 + li)) * H + k;
-      a.specA[m * NC + 2 * p] = A;
-      a.specA[m * NC + 2 * p + 1] = B;
-    }
-    __syncthreads();
   }
-  block_sum<2 * NC>(accm);
   double e1[1] = {acce * (double)N};
   block_sum<1>(e1);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int c = 0; c < 2 * NC; ++c) a.part_mean[(size_t)blockIdx.x * 2 * NC + c] = accm[c];
-    a.part_eta[blockIdx.x] = e1[0];
-  }
+  if (threadIdx.x == 0) a.part_eta[blockIdx.x] = e1[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -889,7 +793,7 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
   const int BS = padded_rows(L1) * CP;
   const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
-  const int G = a.x_lines;
+  const int G = a.x5_lines;
   double dmax[2] = {0.0, 0.0};
   const FastDiv fL = make_fastdiv(L1), fH = make_fastdiv(H);
   for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
@@ -993,7 +897,7 @@ __global__ void k_reduce_delta(IterArgs<T> a) {
   const int st = ctl->state;
   if (st != kRunning && st != kLast) return;
   double m[2] = {0.0, 0.0};
-  for (int b = threadIdx.x; b < a.x_blocks; b += blockDim.x) {
+  for (int b = threadIdx.x; b < a.x5_blocks; b += blockDim.x) {
     m[0] = fmax(m[0], a.part_delta[(size_t)b * 2]);
     m[1] = fmax(m[1], a.part_delta[(size_t)b * 2 + 1]);
   }
@@ -1076,9 +980,20 @@ __global__ void k_sum_parts(const double* part, int blocks, int width, double* o
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) {
-  if (a.eta_real) k_fwd_x_march<T><<<a.m_blocks, 256, a.m_smem, s>>>(a);
-  else if (a.dim == 3) k_fwd_x<T, 3><<<a.x_blocks, a.x_threads, a.x1_smem, s>>>(a);
-  else k_fwd_x<T, 2><<<a.x_blocks, a.x_threads, a.x1_smem, s>>>(a);
+  if (a.dim == 3) {
+    if (a.dual) k_fwd_x<T, 3, true><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a);
+    else k_fwd_x<T, 3, false><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a);
+  } else {
+    if (a.dual) k_fwd_x<T, 2, true><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a);
+    else k_fwd_x<T, 2, false><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_eta_stencil(const IterArgs<T>& a, cudaStream_t s) {
+  if (a.green == kCentered) k_eta_stencil<T, true><<<a.e_blocks, kEThreads, a.e_smem, s>>>(a);
+  else k_eta_stencil<T, false><<<a.e_blocks, kEThreads, a.e_smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1101,8 +1016,8 @@ cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaStream_t s) {
-  const int nparts = a.eta_real ? a.m_blocks : ((a.g.H + a.z_w - 1) / a.z_w) * a.g.n2 * (a.dual ? 2 : 1);
-  const int mparts = a.eta_real ? a.m_blocks : a.x_blocks;
+  const int nparts = a.eta_real ? a.e_blocks : ((a.g.H + a.z_w - 1) / a.z_w) * a.g.n2 * (a.dual ? 2 : 1);
+  const int mparts = a.x1_blocks;
   if (a.dim == 3) k_reduce_eta<T, 3><<<1, 512, 0, s>>>(a, nparts, mparts);
   else k_reduce_eta<T, 2><<<1, 512, 0, s>>>(a, nparts, mparts);
   return cudaGetLastError();
@@ -1110,8 +1025,8 @@ cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_inv_x(const IterArgs<T>& a, cudaStream_t s) {
-  if (a.dim == 3) k_inv_x<T, 3><<<a.x_blocks, a.x_threads, a.x5_smem, s>>>(a);
-  else k_inv_x<T, 2><<<a.x_blocks, a.x_threads, a.x5_smem, s>>>(a);
+  if (a.dim == 3) k_inv_x<T, 3><<<a.x5_blocks, a.x_threads, a.x5_smem, s>>>(a);
+  else k_inv_x<T, 2><<<a.x5_blocks, a.x_threads, a.x5_smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1121,23 +1036,26 @@ cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Every kernel of the iteration may take up to smax bytes of dynamic shared
+// memory (any tile schedule the host picks stays below it).
 template <typename T>
-cudaError_t set_kernel_attributes(const IterArgs<T>& a) {
+cudaError_t set_kernel_attributes(const IterArgs<T>& a, size_t smax) {
   cudaError_t e = cudaSuccess;
-#define FFTLS_ATTR(fn, bytes)                                                                    \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));
-  if (a.eta_real) FFTLS_ATTR((k_fwd_x_march<T>), a.m_smem);
-  if (a.dim == 3) {
-    FFTLS_ATTR((k_fwd_x<T, 3>), a.x1_smem);
-    FFTLS_ATTR((k_inv_x<T, 3>), a.x5_smem);
-    FFTLS_ATTR((k_fourier_z<T, 3>), a.z_smem);
-    FFTLS_ATTR((k_mid_y<T, 6>), a.y_smem);
-  } else {
-    FFTLS_ATTR((k_fwd_x<T, 2>), a.x1_smem);
-    FFTLS_ATTR((k_inv_x<T, 2>), a.x5_smem);
-    FFTLS_ATTR((k_fourier_z<T, 2>), a.z_smem);
-    FFTLS_ATTR((k_mid_y<T, 3>), a.y_smem);
-  }
+  (void)a;
+#define FFTLS_ATTR(fn)                                                                                          \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+  FFTLS_ATTR((k_eta_stencil<T, true>));
+  FFTLS_ATTR((k_eta_stencil<T, false>));
+  FFTLS_ATTR((k_fwd_x<T, 3, true>));
+  FFTLS_ATTR((k_fwd_x<T, 3, false>));
+  FFTLS_ATTR((k_inv_x<T, 3>));
+  FFTLS_ATTR((k_fourier_z<T, 3>));
+  FFTLS_ATTR((k_mid_y<T, 6>));
+  FFTLS_ATTR((k_fwd_x<T, 2, true>));
+  FFTLS_ATTR((k_fwd_x<T, 2, false>));
+  FFTLS_ATTR((k_inv_x<T, 2>));
+  FFTLS_ATTR((k_fourier_z<T, 2>));
+  FFTLS_ATTR((k_mid_y<T, 3>));
 #undef FFTLS_ATTR
   return e;
 }
@@ -1184,12 +1102,13 @@ cudaError_t launch_sum_parts(const double* part, int blocks, int width, double* 
 
 #define FFTLS_INST(T)                                                                                   \
   template cudaError_t launch_fwd_x<T>(const IterArgs<T>&, cudaStream_t);                              \
+  template cudaError_t launch_eta_stencil<T>(const IterArgs<T>&, cudaStream_t);                        \
   template cudaError_t launch_mid_y<T>(const IterArgs<T>&, bool, cudaStream_t);                        \
   template cudaError_t launch_fourier_z<T>(const IterArgs<T>&, cudaStream_t);                          \
   template cudaError_t launch_reduce_eta<T>(const IterArgs<T>&, cudaStream_t);                         \
   template cudaError_t launch_inv_x<T>(const IterArgs<T>&, cudaStream_t);                              \
   template cudaError_t launch_reduce_delta<T>(const IterArgs<T>&, cudaStream_t);                       \
-  template cudaError_t set_kernel_attributes<T>(const IterArgs<T>&);                                    \
+  template cudaError_t set_kernel_attributes<T>(const IterArgs<T>&, size_t);                            \
   template cudaError_t launch_fill_eps<T>(T*, int, long long, const double*, cudaStream_t);            \
   template cudaError_t launch_stress<T>(const T*, const uint8_t*, const T*, int, long long, double*,   \
                                         double*, int, cudaStream_t);

@@ -89,7 +89,7 @@ struct IterArgs {
   int corr;          // 1: correction phase (zero mean mode, eta adds d64)
   int want_delta;    // inverse x1 pass computes max |d eps|, |d sigma|
   int write_d64;     // store the FP64 iterate's divergence (FP32) for a later correction phase
-  int eta_real;      // 1: eta from the real-space divergence stencil in the x1 pass (G^C/W/R, 3D);
+  int eta_real;      // 1: eta from the real-space divergence stencil (G^C/W/R, 3D, k_eta_stencil);
                      //    the forward transform then carries tau only
   int tauform;       // 1: the transformed field is tau (mean mode = eps_bar); 0: sigma
   T* eps;            // n_c x N (the iterate, or the correction delta)
@@ -105,30 +105,35 @@ struct IterArgs {
   double lam0, mu0;
   double eps_bar[6];
   Ctrl* ctrl;
-  double* part_mean;   // [x_blocks][2 nc]: sums of sigma and eps per block
-  double* part_eta;    // [z blocks]: sums of |k*.sigma_hat|^2 per block
-  double* part_delta;  // [x_blocks][2]: max |d eps|, max |d sigma| per block
+  double* part_mean;   // [x1_blocks][2 nc]: sums of sigma and eps per block
+  double* part_eta;    // [z blocks or eta blocks]: sums of |k*.sigma_hat|^2 per block
+  double* part_delta;  // [x5_blocks][2]: max |d eps|, max |d sigma| per block
   double* eta_hist;    // [max_it]
   double* ms_hist;     // [max_it][nc]
   float* rfield;       // n_c x N defect r (written by kUpdResidual, read by corrections)
   float2* d64;         // [modes][3]: k*.sigma_hat of the FP64 iterate (phase-free form), or with
                        // eta_real [3][N] floats: its real-space divergence
   // launch shapes (host-computed)
-  int x_lines, x_blocks, x_threads;
+  int x1_lines, x1_blocks;  // forward x1 pass: lines per batch, blocks (grid-stride over batches)
+  int x5_lines, x5_blocks;  // inverse x1 pass
+  int x_threads;
   int y_w, y_threads, z_w, z_threads;
   size_t x1_smem, x5_smem, y_smem, z_smem;
-  int m_lines, m_planes, m_blocks;  // x1 pass with real-space eta: lines x planes per block
-  size_t m_smem;
+  int e_planes, e_blocks;  // real-space eta: x3-planes per block, blocks (tiles x slabs)
+  size_t e_smem;
 };
 
 // Launchers (fftls_kernels.cu).  All return cudaGetLastError().
 template <typename T> cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_eta_stencil(const IterArgs<T>& a, cudaStream_t s);
+// tile of the real-space eta kernel (x1 columns x x2 rows) and its threads
+constexpr int kEtaTileX = 64, kEtaTileY = 8;
 template <typename T> cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s);
 template <typename T> cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_inv_x(const IterArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t set_kernel_attributes(const IterArgs<T>& a);
+template <typename T> cudaError_t set_kernel_attributes(const IterArgs<T>& a, size_t smax);
 
 // Elementwise helpers.
 template <typename T> cudaError_t launch_fill_eps(T* eps, int nc, long long N, const double* eps_bar6, cudaStream_t s);

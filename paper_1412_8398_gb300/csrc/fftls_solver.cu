@@ -17,12 +17,12 @@ using namespace fftls;
 namespace {
 
 constexpr int kMaxL = 1024;
-constexpr int kNumKinds = 7;
+constexpr int kNumKinds = 8;
 const char* const kKindNames[2][kNumKinds] = {
     {"fwd_x_f32", "mid_y_fwd_f32", "fourier_z_f32", "reduce_eta_f32", "mid_y_inv_f32", "inv_x_f32",
-     "reduce_delta_f32"},
+     "reduce_delta_f32", "eta_x_f32"},
     {"fwd_x_f64", "mid_y_fwd_f64", "fourier_z_f64", "reduce_eta_f64", "mid_y_inv_f64", "inv_x_f64",
-     "reduce_delta_f64"}};
+     "reduce_delta_f64", "eta_x_f64"}};
 constexpr int kMaxOuter = 8;  // FP64 residual evaluations of the refinement ladder
 
 struct DevBuf {
@@ -131,6 +131,21 @@ void axis_tables(int L, double* tw, double* kt) {
   }
 }
 
+// Tile schedule of one iteration: lines per batch of the forward and inverse x1
+// passes, modes per tile of the x2 and x3 passes, x3-planes per block of the
+// real-space eta kernel.  Any schedule that fits shared memory gives the same
+// arithmetic per line and per mode; only the partial-sum grouping of the
+// reductions changes.
+struct TilePlan {
+  int x1_lines, x5_lines, y_w, z_w, e_planes;
+  int tuned;  // 1: chosen by timing candidates on the device
+};
+
+struct PlanKey {
+  int prec, n1, n2, n3, dim, green, real_eta;
+  bool operator==(const PlanKey& o) const { return memcmp(this, &o, sizeof(PlanKey)) == 0; }
+};
+
 }  // namespace
 
 struct fftls_ctx {
@@ -148,6 +163,7 @@ struct fftls_ctx {
   long long graph_launches = 0;
   double prof_ms[2][kNumKinds];
   int prof_n[2][kNumKinds];
+  std::vector<std::pair<PlanKey, TilePlan>> plans;  // tile schedules per grid and precision
   struct ProfEv { cudaEvent_t a, b; int kind; };
   std::vector<ProfEv> ev;
 };
@@ -321,66 +337,95 @@ void build_tables(const Setup& S, std::vector<double>& tab, std::vector<int>& pe
 }
 
 // Launch shapes for precision T; false if a size does not fit in shared memory.
-template <typename T>
-bool plan_launch(const Setup& S, IterArgs<T>& a) {
-  typedef typename Cplx<T>::type T2;
-  const size_t cb = sizeof(T2);
-  const size_t lim = (size_t)S.smem_optin - 4096;  // static reduction arrays
+// real_eta: 3D G^C/W/R take eta from the real-space stencil and the forward x1
+// pass carries tau alone (rows half as wide); dual: the forward pass carries tau
+// and sigma (no real-space eta, accelerated scheme).
+struct PlanGeom {
+  size_t cb, lim, twx, line1, line5;
+  long long nlines, tiles;
+};
+
+PlanGeom plan_geom(const Setup& S, size_t cb, bool real_eta) {
+  PlanGeom G;
   const int nc = S.nc;
-  const Geom& g = S.g;
-  const long long nlines = (long long)g.n2 * g.n3;
-  // x kernels: lines per block so that a tile is ~64 KB (at least one line)
-  const size_t twx = (size_t)even_up(g.n1) * cb;
-  const size_t line1 = (size_t)padded_rows(g.n1) * odd_up(nc) * cb;             // forward, tau and sigma pairs
-  const size_t line5 = (size_t)padded_rows(g.n1) * odd_up((nc + 1) / 2) * cb;  // inverse
-  if (twx + line1 > lim) return false;
-  int G = (int)std::max<size_t>(1, (64 * 1024) / line1);
-  G = (int)std::min<long long>(G, nlines);
-  while (G > 1 && twx + G * line1 > lim) --G;
-  a.x_lines = G;
-  a.x1_smem = twx + G * line1;
-  a.x5_smem = twx + G * line5;
-  a.x_threads = 256;
-  const long long nbatches = (nlines + G - 1) / G;
-  a.x_blocks = (int)std::min<long long>(nbatches, (long long)S.num_sms * 4);
-  // strided kernels: W modes x L rows x n_c, <= ~100 KB so two blocks fit an SM
-  auto pick_w = [&](int L, int* W, size_t* smem) {
-    const size_t tw = (size_t)even_up(L) * cb;
+  G.cb = cb;
+  G.lim = (size_t)S.smem_optin - 4096;  // static reduction arrays
+  G.twx = (size_t)even_up(S.g.n1) * cb;
+  G.line1 = (size_t)padded_rows(S.g.n1) * odd_up(real_eta ? (nc + 1) / 2 : nc) * cb;
+  G.line5 = (size_t)padded_rows(S.g.n1) * odd_up((nc + 1) / 2) * cb;
+  G.nlines = (long long)S.g.n2 * S.g.n3;
+  G.tiles = (long long)((S.g.n1 + kEtaTileX - 1) / kEtaTileX) * ((S.g.n2 + kEtaTileY - 1) / kEtaTileY);
+  return G;
+}
+
+size_t strided_smem(int L, int w, int nc, size_t cb) { return (size_t)even_up(L) * cb + (size_t)L * w * nc * cb; }
+
+// Built-in schedule: x1 tiles of about 32 KB (64 KB for the two-field forward
+// tile), x2/x3 tiles of at most 16 modes and about 100 KB, eta slabs of up to 32
+// planes with enough slabs for several waves of blocks.
+TilePlan default_plan(const Setup& S, size_t cb, bool real_eta) {
+  const PlanGeom G = plan_geom(S, cb, real_eta);
+  TilePlan P;
+  P.tuned = 0;
+  P.x1_lines = (int)std::max<size_t>(1, (real_eta ? 32 * 1024 : 64 * 1024) / G.line1);
+  P.x5_lines = (int)std::max<size_t>(1, (32 * 1024) / G.line5);
+  auto pick_w = [&](int L) {
     int w = 16;
-    while (w > 1 && tw + (size_t)L * w * nc * cb > std::min<size_t>(lim, 100 * 1024)) w /= 2;
-    while (w > 1 && w / 2 >= g.H) w /= 2;
-    if (tw + (size_t)L * w * nc * cb > lim) return false;
-    *W = w;
-    *smem = tw + (size_t)L * w * nc * cb;
-    return true;
+    while (w > 1 && strided_smem(L, w, S.nc, cb) > std::min<size_t>(G.lim, 100 * 1024)) w /= 2;
+    while (w > 1 && w / 2 >= S.g.H) w /= 2;
+    return w;
   };
-  if (!pick_w(g.n2, &a.y_w, &a.y_smem)) return false;
-  if (!pick_w(g.n3, &a.z_w, &a.z_smem)) return false;
-  a.y_threads = (long long)g.n2 * a.y_w * nc >= 4096 ? 512 : 256;
-  a.z_threads = (long long)g.n3 * a.z_w * nc >= 4096 ? 512 : 256;
-  // x1 pass with real-space eta (3D, G^C / G^W / G^R): m_lines lines x m_planes planes
-  a.m_lines = a.m_planes = a.m_blocks = 0;
-  a.m_smem = 0;
-  if (S.dim == 3 && S.green != kMS) {
-    const size_t st = sizeof(T);
-    const int rmul = S.green == kCentered ? 9 : 3;
-    auto need = [&](int G) { return twx + (size_t)G * padded_rows(g.n1) * 3 * cb + (size_t)rmul * G * g.n1 * st; };
-    int G = 8;
-    while (G > 1 && need(G) > std::min<size_t>(lim, 100 * 1024)) --G;
-    if (G < 2 && need(2) <= lim) G = 2;
-    G = std::min(G, g.n2);
-    if (need(G) <= lim) {
-      const int nyg = (g.n2 + G - 1) / G;
-      const int nzs_want = std::max(1, (2 * S.num_sms + nyg - 1) / nyg);
-      int Z = (g.n3 + nzs_want - 1) / nzs_want;
-      Z = std::max(std::min(Z, 32), std::min(4, g.n3));
-      a.m_lines = G;
-      a.m_planes = Z;
-      a.m_blocks = nyg * ((g.n3 + Z - 1) / Z);
-      a.m_smem = need(G);
-    }
+  P.y_w = pick_w(S.g.n2);
+  P.z_w = pick_w(S.g.n3);
+  const long long want_slabs = std::max<long long>(1, (8LL * S.num_sms + G.tiles - 1) / G.tiles);
+  int Z = (int)((S.g.n3 + want_slabs - 1) / want_slabs);
+  P.e_planes = std::max(std::min(Z, 32), std::min(4, S.g.n3));
+  return P;
+}
+
+// Derive launch shapes and shared-memory sizes from a schedule; false when it
+// does not fit.
+template <typename T>
+bool apply_plan(const Setup& S, IterArgs<T>& a, bool real_eta, const TilePlan& P) {
+  typedef typename Cplx<T>::type T2;
+  const PlanGeom G = plan_geom(S, sizeof(T2), real_eta);
+  const Geom& g = S.g;
+  if (P.x1_lines < 1 || P.x5_lines < 1 || P.y_w < 1 || P.z_w < 1) return false;
+  const int G1 = (int)std::min<long long>(P.x1_lines, G.nlines);
+  const int G5 = (int)std::min<long long>(P.x5_lines, G.nlines);
+  if (G.twx + G1 * G.line1 > G.lim || G.twx + G5 * G.line5 > G.lim) return false;
+  a.x1_lines = G1;
+  a.x5_lines = G5;
+  a.x1_smem = G.twx + G1 * G.line1;
+  a.x5_smem = G.twx + G5 * G.line5;
+  a.x_threads = 256;
+  a.x1_blocks = (int)std::min<long long>((G.nlines + G1 - 1) / G1, (long long)S.num_sms * 8);
+  a.x5_blocks = (int)std::min<long long>((G.nlines + G5 - 1) / G5, (long long)S.num_sms * 8);
+  a.y_smem = strided_smem(g.n2, P.y_w, S.nc, sizeof(T2));
+  a.z_smem = strided_smem(g.n3, P.z_w, S.nc, sizeof(T2));
+  if (a.y_smem > G.lim || a.z_smem > G.lim) return false;
+  a.y_w = P.y_w;
+  a.z_w = P.z_w;
+  a.y_threads = (long long)g.n2 * a.y_w * S.nc >= 4096 ? 512 : 256;
+  a.z_threads = (long long)g.n3 * a.z_w * S.nc >= 4096 ? 512 : 256;
+  a.e_planes = a.e_blocks = 0;
+  a.e_smem = 0;
+  if (real_eta) {
+    const int Z = std::max(1, std::min(P.e_planes, g.n3));
+    a.e_planes = Z;
+    a.e_blocks = (int)(G.tiles * ((g.n3 + Z - 1) / Z));
+    a.e_smem = (size_t)2 * 6 * (kEtaTileY + 2) * (kEtaTileX + 2) * sizeof(T);
   }
   return true;
+}
+
+// Largest block counts over every schedule apply_plan accepts (partial-sum buffers).
+size_t max_x_blocks(const Setup& S) {
+  return (size_t)std::min<long long>((long long)S.g.n2 * S.g.n3, (long long)S.num_sms * 8);
+}
+size_t max_eta_parts(const Setup& S) {
+  const PlanGeom G = plan_geom(S, 8, true);
+  return std::max<size_t>((size_t)S.g.H * S.g.n2 * 2, (size_t)(G.tiles * S.g.n3));
 }
 
 template <typename T>
@@ -391,7 +436,7 @@ struct Runner {
   bool capturing = false;
   Runner(fftls_ctx* c_, const Setup& S_) : c(c_), S(S_) { memset(&a, 0, sizeof(a)); }
 
-  int kernels_per_iter() const { return 4 + (S.g.n2 > 1 ? 2 : 0) + (a.want_delta ? 1 : 0); }
+  int kernels_per_iter() const { return 4 + (S.g.n2 > 1 ? 2 : 0) + (a.want_delta ? 1 : 0) + (a.eta_real ? 1 : 0); }
 
   fftls_status launch(int kind, cudaError_t (*fn)(Runner*, cudaStream_t), bool prof) {
     const int pi = Prec<T>::idx;
@@ -417,6 +462,8 @@ struct Runner {
     a.tauform = (a.dual || a.eta_real) ? 1 : 0;
     a.update = update;
     fftls_status st;
+    if (a.eta_real)
+      if ((st = launch(7, [](Runner* r, cudaStream_t s) { return launch_eta_stencil<T>(r->a, s); }, prof))) return st;
     if ((st = launch(0, [](Runner* r, cudaStream_t s) { return launch_fwd_x<T>(r->a, s); }, prof))) return st;
     if ((st = launch(1, [](Runner* r, cudaStream_t s) { return launch_mid_y<T>(r->a, false, s); }, prof))) return st;
     if ((st = launch(2, [](Runner* r, cudaStream_t s) { return launch_fourier_z<T>(r->a, s); }, prof))) return st;
@@ -523,6 +570,82 @@ struct Runner {
   }
 };
 
+// Autotuner: time the candidate schedules of each kernel on the live buffers and
+// keep the fastest, one kernel at a time (the kernels of an iteration are
+// separate launches, so their schedules are independent).  It runs before the
+// first iteration: the forward passes and the eta kernel only read the iterate,
+// the strided passes work in place on the spectrum, and the inverse x1 pass
+// writes its update into specB (unused at that point) instead of the iterate.
+template <typename T>
+fftls_status tune_plan(fftls_ctx* c, const Setup& S, IterArgs<T>& a, bool real_eta, TilePlan& P) {
+  typedef cudaError_t (*LaunchFn)(const IterArgs<T>&, cudaStream_t);
+  const IterArgs<T> keep = a;
+  cudaStream_t s = S.s;
+  Ctrl run;
+  memset(&run, 0, sizeof(run));
+  run.state = kRunning;
+  CUDA_TRY(c, cudaMemcpyAsync(a.ctrl, &run, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+  a.dual = (!real_eta && S.scheme == FFTLS_ACCELERATED) ? 1 : 0;
+  a.tauform = (a.dual || real_eta) ? 1 : 0;
+  a.update = kUpdAccel;
+  a.want_delta = a.write_d64 = a.corr = 0;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(c, cudaEventCreate(&e0));
+  CUDA_TRY(c, cudaEventCreate(&e1));
+  constexpr int kReps = 2;
+  auto timed = [&](LaunchFn fn, float* ms) -> cudaError_t {
+    cudaError_t e = fn(a, s);  // warm-up
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
+    for (int r = 0; r < kReps; ++r)
+      if ((e = fn(a, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+    return cudaEventElapsedTime(ms, e0, e1);
+  };
+  cudaError_t err = cudaSuccess;
+  auto search = [&](int TilePlan::*field, const std::vector<int>& cands, LaunchFn fn) {
+    float best = INFINITY;
+    int bestv = P.*field;
+    for (int v : cands) {
+      if (err != cudaSuccess) return;
+      TilePlan Q = P;
+      Q.*field = v;
+      if (!apply_plan<T>(S, a, real_eta, Q)) continue;
+      float ms = 0.f;
+      err = timed(fn, &ms);
+      c->launches += 1 + kReps;
+      if (ms < best) {
+        best = ms;
+        bestv = v;
+      }
+    }
+    P.*field = bestv;
+    apply_plan<T>(S, a, real_eta, P);
+  };
+  // tile widths of the strided passes: powers of two up to 16 modes, no wider than the half spectrum needs
+  std::vector<int> widths;
+  for (int w = 1; w <= 16; w *= 2)
+    if (w == 1 || w / 2 < S.g.H) widths.push_back(w);
+  search(&TilePlan::x1_lines, {1, 2, 4, 8}, [](const IterArgs<T>& x, cudaStream_t st) { return launch_fwd_x<T>(x, st); });
+  if (S.g.n2 > 1)
+    search(&TilePlan::y_w, widths, [](const IterArgs<T>& x, cudaStream_t st) { return launch_mid_y<T>(x, false, st); });
+  search(&TilePlan::z_w, widths, [](const IterArgs<T>& x, cudaStream_t st) { return launch_fourier_z<T>(x, st); });
+  a.eps = (T*)c->specB.p;  // scratch target of the inverse pass's update
+  search(&TilePlan::x5_lines, {1, 2, 4, 8}, [](const IterArgs<T>& x, cudaStream_t st) { return launch_inv_x<T>(x, st); });
+  a.eps = keep.eps;
+  if (real_eta)
+    search(&TilePlan::e_planes, {4, 8, 16, 32, 64},
+           [](const IterArgs<T>& x, cudaStream_t st) { return launch_eta_stencil<T>(x, st); });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return set_err(c, FFTLS_E_CUDA, "autotune: %s", cudaGetErrorString(err));
+  P.tuned = 1;
+  a = keep;
+  apply_plan<T>(S, a, real_eta, P);
+  return FFTLS_OK;
+}
+
 template <typename T>
 fftls_status prepare(fftls_ctx* c, const Setup& S, const fftls_problem* p, const fftls_options* o, Runner<T>& R,
                      T* eps, const std::vector<double>& tab, const int* d_perms) {
@@ -535,7 +658,13 @@ fftls_status prepare(fftls_ctx* c, const Setup& S, const fftls_problem* p, const
   a.lam0 = S.lam0;
   a.mu0 = S.mu0;
   for (int i = 0; i < 6; ++i) a.eps_bar[i] = S.eps_bar[i];
-  if (!plan_launch<T>(S, a))
+  const bool real_eta = S.dim == 3 && S.green != kMS;
+  const PlanKey key{Prec<T>::idx, S.g.n1, S.g.n2, S.g.n3, S.dim, S.green, real_eta ? 1 : 0};
+  int cached = -1;
+  for (size_t i = 0; i < c->plans.size(); ++i)
+    if (c->plans[i].first == key) cached = (int)i;
+  TilePlan P = cached >= 0 ? c->plans[cached].second : default_plan(S, sizeof(T2), real_eta);
+  if (!apply_plan<T>(S, a, real_eta, P))
     return set_err(c, FFTLS_E_UNSUPPORTED_SIZE, "grid %dx%dx%d does not fit the shared-memory tiles", S.g.n1, S.g.n2,
                    S.g.n3);
   // coefficients and tables in precision T
@@ -566,18 +695,23 @@ fftls_status prepare(fftls_ctx* c, const Setup& S, const fftls_problem* p, const
   a.eta_hist = (double*)c->eta_hist.p;
   a.ms_hist = (double*)c->ms_hist.p;
   a.want_delta = o->stop == FFTLS_STOP_MAXDELTA ? 1 : 0;
-  a.eta_real = a.m_blocks > 0 ? 1 : 0;
-  const int ntz = (S.g.H + a.z_w - 1) / a.z_w;
-  const size_t nparts = std::max<size_t>((size_t)ntz * S.g.n2 * 2, (size_t)a.m_blocks);
-  CUDA_TRY(c, c->part_mean.ensure((size_t)std::max(a.x_blocks, a.m_blocks) * 2 * S.nc * sizeof(double)));
-  CUDA_TRY(c, c->part_eta.ensure(nparts * sizeof(double)));
-  CUDA_TRY(c, c->part_delta.ensure((size_t)a.x_blocks * 2 * sizeof(double)));
+  a.eta_real = real_eta ? 1 : 0;
+  // partial-sum buffers sized for every schedule the tuner may pick
+  CUDA_TRY(c, c->part_mean.ensure(max_x_blocks(S) * 2 * S.nc * sizeof(double)));
+  CUDA_TRY(c, c->part_eta.ensure(max_eta_parts(S) * sizeof(double)));
+  CUDA_TRY(c, c->part_delta.ensure(max_x_blocks(S) * 2 * sizeof(double)));
   a.part_mean = (double*)c->part_mean.p;
   a.part_eta = (double*)c->part_eta.p;
   a.part_delta = (double*)c->part_delta.p;
   a.rfield = (float*)c->rfield.p;
   a.d64 = (float2*)c->d64.p;
-  CUDA_TRY(c, set_kernel_attributes<T>(a));
+  CUDA_TRY(c, set_kernel_attributes<T>(a, (size_t)S.smem_optin - 4096));
+  if (o->autotune && !P.tuned) {
+    fftls_status st = tune_plan<T>(c, S, a, real_eta, P);
+    if (st) return st;
+  }
+  if (cached >= 0) c->plans[cached].second = P;
+  else c->plans.push_back({key, P});
   return FFTLS_OK;
 }
 
@@ -602,6 +736,21 @@ void fftls_default_options(fftls_options* o) {
   o->precision = FFTLS_FP64;
   o->refine_switch = 0.0;
   o->use_graphs = 1;
+  o->autotune = 1;
+}
+
+fftls_status fftls_tile_plans(const fftls_ctx* c, int* rows, int* count) {
+  if (!c || !count || *count < 0 || (*count > 0 && !rows)) return FFTLS_E_INVALID_ARG;
+  const int held = (int)c->plans.size();
+  for (int i = 0; i < std::min(*count, held); ++i) {
+    const PlanKey& k = c->plans[i].first;
+    const TilePlan& P = c->plans[i].second;
+    const int row[FFTLS_PLAN_FIELDS] = {k.prec, k.n1,       k.n2,       k.n3, k.green, P.x1_lines,
+                                        P.x5_lines, P.y_w, P.z_w, k.real_eta ? P.e_planes : 0, P.tuned};
+    memcpy(rows + (size_t)i * FFTLS_PLAN_FIELDS, row, sizeof(row));
+  }
+  *count = held;
+  return FFTLS_OK;
 }
 
 fftls_status fftls_create(fftls_ctx** out, int device) {
@@ -811,7 +960,8 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
     Runner<double> R64(c, S);
     if ((st = prepare<double>(c, S, p, o, R64, (double*)c->eps64.p, tab, d_perms))) return st;
     // both precisions must measure eta the same way (the FP64 divergence feeds the FP32 estimate)
-    if (R32.a.eta_real != R64.a.eta_real) R32.a.eta_real = R64.a.eta_real = 0;
+    if (R32.a.eta_real != R64.a.eta_real)
+      return set_err(c, FFTLS_E_CUDA, "internal: FP32 and FP64 plans measure eta differently");
     Ctrl ca = ctl;
     ca.stop_rule = 0;
     ca.tol = o->refine_switch > 0.0 ? o->refine_switch : std::max(o->tol, 3e-5);
@@ -1018,7 +1168,7 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   S.num_sms = v;
   IterArgs<double> a;
   memset(&a, 0, sizeof(a));
-  if (!plan_launch<double>(S, a)) return FFTLS_E_UNSUPPORTED_SIZE;
+  if (!apply_plan<double>(S, a, false, default_plan(S, sizeof(double2), false))) return FFTLS_E_UNSUPPORTED_SIZE;
   // scratch layout
   const int ntz = (S.g.H + a.z_w - 1) / a.z_w;
   const int sblocks = (int)std::min<long long>((N + 255) / 256, (long long)S.num_sms * 8);
@@ -1026,9 +1176,9 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   auto take = [&](size_t bytes) { size_t at = off; off = na_align(off + bytes); return at; };
   const size_t o_specA = take((size_t)S.g.modes * nc * 16);
   const size_t o_specB = take((size_t)S.g.modes * nc * 16);
-  const size_t o_pmean = take((size_t)std::max(a.x_blocks, sblocks) * 2 * nc * 8);
+  const size_t o_pmean = take((size_t)std::max(a.x1_blocks, sblocks) * 2 * nc * 8);
   const size_t o_peta = take((size_t)ntz * S.g.n2 * 2 * 8);
-  const size_t o_pdelta = take((size_t)a.x_blocks * 2 * 8);
+  const size_t o_pdelta = take((size_t)a.x5_blocks * 2 * 8);
   const size_t o_sums = take(64 * 8);
   const size_t o_ctrl = take(sizeof(Ctrl));
   const size_t o_eh = take((size_t)o->max_iter * 8);
@@ -1097,7 +1247,7 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   a.eta_hist = (double*)(base + o_eh);
   a.ms_hist = (double*)(base + o_mh);
   a.want_delta = o->stop == FFTLS_STOP_MAXDELTA ? 1 : 0;
-  NA_TRY(set_kernel_attributes<double>(a));
+  NA_TRY(set_kernel_attributes<double>(a, (size_t)S.smem_optin - 4096));
   const bool direct = p->scheme == FFTLS_DIRECT;
   Ctrl ctl;
   memset(&ctl, 0, sizeof(ctl));

@@ -69,6 +69,7 @@ class _Options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("use_graphs", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -109,6 +110,7 @@ _SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_int)]),
     "fftls_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_longlong)]),
+    "fftls_tile_plans": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "fftls_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "fftls_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -245,7 +247,7 @@ class Solver:
         return p, keep, on_dev
 
     def _options(self, tol, max_iter, precision, stop, refine_switch, eps_init, fields_on_device, stream,
-                 use_graphs, profile):
+                 use_graphs, profile, autotune=True):
         o = _Options()
         self.lib.fftls_default_options(ctypes.byref(o))
         o.tol = float(tol)
@@ -256,6 +258,7 @@ class Solver:
         o.fields_on_device = 1 if fields_on_device else 0
         o.use_graphs = 1 if use_graphs else 0
         o.profile = 1 if profile else 0
+        o.autotune = 1 if autotune else 0
         keep = None
         if eps_init is not None:
             if _is_torch(eps_init):
@@ -274,13 +277,13 @@ class Solver:
     def solve(self, phase, lam, mu, eps_bar, green="R", scheme="AS", lam0=None, mu0=None, tol=1e-8,
               max_iter=1000, precision="fp64", stop="eta", refine_switch=0.0, eps_init=None,
               want_strain=True, want_stress=True, history=True, device_outputs=None, stream=None,
-              use_graphs=True, profile=False, raise_on_error=True) -> SolveResult:
+              use_graphs=True, profile=False, autotune=True, raise_on_error=True) -> SolveResult:
         """Solve one load case; see fftls_solve in include/fftls.h."""
         p, keep_p, on_dev = self._problem(phase, lam, mu, eps_bar, green, scheme, lam0, mu0)
         if device_outputs is None:
             device_outputs = on_dev
         o, keep_o = self._options(tol, max_iter, precision, stop, refine_switch, eps_init, device_outputs,
-                                  stream, use_graphs, profile)
+                                  stream, use_graphs, profile, autotune)
         nc = 6 if p.dim == 3 else 3
         shape = (nc,) + tuple(phase.shape)
         r = _Result()
@@ -342,6 +345,15 @@ class Solver:
         g = ctypes.c_longlong()
         self.lib.fftls_counters(self.handle, ctypes.byref(k), ctypes.byref(g))
         return k.value, g.value
+
+    def tile_plans(self) -> list:
+        """Tile schedules held by this context (see fftls_tile_plans), one dict per grid and precision."""
+        n = ctypes.c_int(0)
+        self.lib.fftls_tile_plans(self.handle, None, ctypes.byref(n))
+        rows = (ctypes.c_int * (11 * max(n.value, 1)))()
+        self.lib.fftls_tile_plans(self.handle, rows, ctypes.byref(n))
+        keys = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x5_lines", "y_w", "z_w", "e_planes", "tuned")
+        return [dict(zip(keys, rows[11 * i:11 * i + 11])) for i in range(n.value)]
 
     def profile(self) -> dict:
         """Per-kernel (total ms, launches) of the last solve run with profile=True."""
