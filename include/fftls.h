@@ -179,12 +179,13 @@ fftls_status fftls_profile(const fftls_ctx* ctx, const char** names, double* tot
 
 /* Tile schedules held by this context, one row of FFTLS_PLAN_FIELDS ints per grid,
  * operator and precision: {precision (0 float, 1 double), n1, n2, n3, green,
- * lines per block of the forward x1 pass, of the inverse x1 pass, modes per tile
- * of the x2 pass, of the x3 pass, x3-planes per block of the real-space eta
- * kernel, 1 if tuned on the device else 0}.  Copies min(*count, held) rows into
+ * lines per batch of the forward x1 pass, voxels per thread it loads together,
+ * lines per batch of the inverse x1 pass, modes per tile of the x2 pass, of the
+ * x3 pass, x3-planes per block of the real-space eta kernel (0: not used),
+ * 1 if tuned on the device else 0}.  Copies min(*count, held) rows into
  * `rows` (may be NULL when *count is 0) and returns the number held in *count.
  * The paper has no counterpart (an implementation detail of the GPU path). */
-#define FFTLS_PLAN_FIELDS 11
+#define FFTLS_PLAN_FIELDS 12
 fftls_status fftls_tile_plans(const fftls_ctx* ctx, int* rows, int* count);
 
 /* Kernels launched on this context since creation (nodes of CUDA graphs

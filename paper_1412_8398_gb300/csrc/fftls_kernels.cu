@@ -165,7 +165,9 @@ __device__ __forceinline__ void tile_store(const T2* tile, int C, T2* g, long lo
 // ---------------------------------------------------------------------------
 // K1: constitutive law + forward x1 transform (real -> half complex)
 // ---------------------------------------------------------------------------
-template <typename T, int DIM, bool DUAL>
+// VB: voxels per thread whose loads are issued together (a tuned trade of
+// registers against loads in flight).
+template <typename T, int DIM, bool DUAL, int VB>
 __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
@@ -181,9 +183,11 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
   const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
   const int G = a.x1_lines;
-  double acc[2 * NC];
-#pragma unroll
-  for (int c = 0; c < 2 * NC; ++c) acc[c] = 0.0;
+  // FP64 running sums of <sigma>, <eps> per warp (the FP32 sums of one batch are
+  // reduced over the warp and added here by lane 0)
+  __shared__ double wacc[8][2 * NC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < 8 * 2 * NC; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
 
   const FastDiv fL = make_fastdiv(L1), fH = make_fastdiv(H), fNP = make_fastdiv(NP);
   for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
@@ -191,7 +195,6 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
     T accf[2 * NC];
 #pragma unroll
     for (int c = 0; c < 2 * NC; ++c) accf[c] = (T)0;
-    constexpr int VB = 4;  // voxels per thread whose loads are issued together
     for (int ib = threadIdx.x; ib < nl * L1; ib += VB * blockDim.x) {
       T ev[VB][NC];
       int phv[VB];
@@ -245,7 +248,11 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
       }
     }
 #pragma unroll
-    for (int c = 0; c < 2 * NC; ++c) acc[c] += (double)accf[c];
+    for (int c = 0; c < 2 * NC; ++c) {
+      T x = accf[c];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) wacc[warp][c] += (double)x;
+    }
     __syncthreads();
     tile_fft(tile, nl, BS, CP, NP, a.pl[0], tws, false, 1);
     for (int idx = threadIdx.x; idx < nl * H * NP; idx += blockDim.x) {
@@ -266,10 +273,12 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
     }
     __syncthreads();
   }
-  block_sum<2 * NC>(acc);
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int c = 0; c < 2 * NC; ++c) a.part_mean[(size_t)blockIdx.x * 2 * NC + c] = acc[c];
+  __syncthreads();
+  if (threadIdx.x < 2 * NC) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wacc[w][threadIdx.x];
+    a.part_mean[(size_t)blockIdx.x * 2 * NC + threadIdx.x] = t;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -305,9 +314,11 @@ __device__ __forceinline__ void sigma_of(const T* __restrict__ eps, const uint8_
   for (int c = 0; c < 6; ++c) s[c] = cf[1] * e[c] + (c < 3 ? cf[0] * tr : (T)0);
 }
 
+// Periodic index for i within a few periods of [0, n) (loops instead of a division).
 __device__ __forceinline__ int wrap_index(int i, int n) {
-  i %= n;
-  return i < 0 ? i + n : i;
+  while (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
 }
 
 template <typename T, bool CEN>
@@ -980,13 +991,18 @@ __global__ void k_sum_parts(const double* part, int blocks, int width, double* o
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) {
+#define FFTLS_FWD(D, U, V) k_fwd_x<T, D, U, V><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a)
+#define FFTLS_FWD_VB(D, U) \
+  (a.x1_vb >= 4 ? FFTLS_FWD(D, U, 4) : a.x1_vb == 2 ? FFTLS_FWD(D, U, 2) : FFTLS_FWD(D, U, 1))
   if (a.dim == 3) {
-    if (a.dual) k_fwd_x<T, 3, true><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a);
-    else k_fwd_x<T, 3, false><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a);
+    if (a.dual) FFTLS_FWD_VB(3, true);
+    else FFTLS_FWD_VB(3, false);
   } else {
-    if (a.dual) k_fwd_x<T, 2, true><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a);
-    else k_fwd_x<T, 2, false><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a);
+    if (a.dual) FFTLS_FWD_VB(2, true);
+    else FFTLS_FWD_VB(2, false);
   }
+#undef FFTLS_FWD_VB
+#undef FFTLS_FWD
   return cudaGetLastError();
 }
 
@@ -1046,13 +1062,21 @@ cudaError_t set_kernel_attributes(const IterArgs<T>& a, size_t smax) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
   FFTLS_ATTR((k_eta_stencil<T, true>));
   FFTLS_ATTR((k_eta_stencil<T, false>));
-  FFTLS_ATTR((k_fwd_x<T, 3, true>));
-  FFTLS_ATTR((k_fwd_x<T, 3, false>));
+  FFTLS_ATTR((k_fwd_x<T, 3, true, 1>));
+  FFTLS_ATTR((k_fwd_x<T, 3, true, 2>));
+  FFTLS_ATTR((k_fwd_x<T, 3, true, 4>));
+  FFTLS_ATTR((k_fwd_x<T, 3, false, 1>));
+  FFTLS_ATTR((k_fwd_x<T, 3, false, 2>));
+  FFTLS_ATTR((k_fwd_x<T, 3, false, 4>));
   FFTLS_ATTR((k_inv_x<T, 3>));
   FFTLS_ATTR((k_fourier_z<T, 3>));
   FFTLS_ATTR((k_mid_y<T, 6>));
-  FFTLS_ATTR((k_fwd_x<T, 2, true>));
-  FFTLS_ATTR((k_fwd_x<T, 2, false>));
+  FFTLS_ATTR((k_fwd_x<T, 2, true, 1>));
+  FFTLS_ATTR((k_fwd_x<T, 2, true, 2>));
+  FFTLS_ATTR((k_fwd_x<T, 2, true, 4>));
+  FFTLS_ATTR((k_fwd_x<T, 2, false, 1>));
+  FFTLS_ATTR((k_fwd_x<T, 2, false, 2>));
+  FFTLS_ATTR((k_fwd_x<T, 2, false, 4>));
   FFTLS_ATTR((k_inv_x<T, 2>));
   FFTLS_ATTR((k_fourier_z<T, 2>));
   FFTLS_ATTR((k_mid_y<T, 3>));

@@ -115,6 +115,7 @@ struct IterArgs {
                        // eta_real [3][N] floats: its real-space divergence
   // launch shapes (host-computed)
   int x1_lines, x1_blocks;  // forward x1 pass: lines per batch, blocks (grid-stride over batches)
+  int x1_vb;                // forward x1 pass: voxels per thread loaded together (1, 2 or 4)
   int x5_lines, x5_blocks;  // inverse x1 pass
   int x_threads;
   int y_w, y_threads, z_w, z_threads;

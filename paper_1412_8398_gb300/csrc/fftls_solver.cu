@@ -137,7 +137,7 @@ void axis_tables(int L, double* tw, double* kt) {
 // arithmetic per line and per mode; only the partial-sum grouping of the
 // reductions changes.
 struct TilePlan {
-  int x1_lines, x5_lines, y_w, z_w, e_planes;
+  int x1_lines, x5_lines, y_w, z_w, e_planes, x1_vb;
   int tuned;  // 1: chosen by timing candidates on the device
 };
 
@@ -369,6 +369,7 @@ TilePlan default_plan(const Setup& S, size_t cb, bool real_eta) {
   P.tuned = 0;
   P.x1_lines = (int)std::max<size_t>(1, (real_eta ? 32 * 1024 : 64 * 1024) / G.line1);
   P.x5_lines = (int)std::max<size_t>(1, (32 * 1024) / G.line5);
+  P.x1_vb = 4;
   auto pick_w = [&](int L) {
     int w = 16;
     while (w > 1 && strided_smem(L, w, S.nc, cb) > std::min<size_t>(G.lim, 100 * 1024)) w /= 2;
@@ -396,6 +397,7 @@ bool apply_plan(const Setup& S, IterArgs<T>& a, bool real_eta, const TilePlan& P
   if (G.twx + G1 * G.line1 > G.lim || G.twx + G5 * G.line5 > G.lim) return false;
   a.x1_lines = G1;
   a.x5_lines = G5;
+  a.x1_vb = P.x1_vb >= 4 ? 4 : P.x1_vb == 2 ? 2 : 1;
   a.x1_smem = G.twx + G1 * G.line1;
   a.x5_smem = G.twx + G5 * G.line5;
   a.x_threads = 256;
@@ -627,7 +629,30 @@ fftls_status tune_plan(fftls_ctx* c, const Setup& S, IterArgs<T>& a, bool real_e
   std::vector<int> widths;
   for (int w = 1; w <= 16; w *= 2)
     if (w == 1 || w / 2 < S.g.H) widths.push_back(w);
-  search(&TilePlan::x1_lines, {1, 2, 4, 8}, [](const IterArgs<T>& x, cudaStream_t st) { return launch_fwd_x<T>(x, st); });
+  // forward x1 pass: lines per batch and voxels loaded together, searched jointly
+  {
+    float best = INFINITY;
+    int bl = P.x1_lines, bv = P.x1_vb;
+    for (int lines : {1, 2, 4, 8})
+      for (int vb : {1, 2, 4}) {
+        if (err != cudaSuccess) break;
+        TilePlan Q = P;
+        Q.x1_lines = lines;
+        Q.x1_vb = vb;
+        if (!apply_plan<T>(S, a, real_eta, Q)) continue;
+        float ms = 0.f;
+        err = timed([](const IterArgs<T>& x, cudaStream_t st) { return launch_fwd_x<T>(x, st); }, &ms);
+        c->launches += 1 + kReps;
+        if (ms < best) {
+          best = ms;
+          bl = lines;
+          bv = vb;
+        }
+      }
+    P.x1_lines = bl;
+    P.x1_vb = bv;
+    apply_plan<T>(S, a, real_eta, P);
+  }
   if (S.g.n2 > 1)
     search(&TilePlan::y_w, widths, [](const IterArgs<T>& x, cudaStream_t st) { return launch_mid_y<T>(x, false, st); });
   search(&TilePlan::z_w, widths, [](const IterArgs<T>& x, cudaStream_t st) { return launch_fourier_z<T>(x, st); });
@@ -745,7 +770,7 @@ fftls_status fftls_tile_plans(const fftls_ctx* c, int* rows, int* count) {
   for (int i = 0; i < std::min(*count, held); ++i) {
     const PlanKey& k = c->plans[i].first;
     const TilePlan& P = c->plans[i].second;
-    const int row[FFTLS_PLAN_FIELDS] = {k.prec, k.n1,       k.n2,       k.n3, k.green, P.x1_lines,
+    const int row[FFTLS_PLAN_FIELDS] = {k.prec,     k.n1,  k.n2,  k.n3, k.green, P.x1_lines, P.x1_vb,
                                         P.x5_lines, P.y_w, P.z_w, k.real_eta ? P.e_planes : 0, P.tuned};
     memcpy(rows + (size_t)i * FFTLS_PLAN_FIELDS, row, sizeof(row));
   }

@@ -350,10 +350,12 @@ class Solver:
         """Tile schedules held by this context (see fftls_tile_plans), one dict per grid and precision."""
         n = ctypes.c_int(0)
         self.lib.fftls_tile_plans(self.handle, None, ctypes.byref(n))
-        rows = (ctypes.c_int * (11 * max(n.value, 1)))()
+        keys = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x1_vb", "x5_lines", "y_w", "z_w", "e_planes",
+                "tuned")
+        w = len(keys)
+        rows = (ctypes.c_int * (w * max(n.value, 1)))()
         self.lib.fftls_tile_plans(self.handle, rows, ctypes.byref(n))
-        keys = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x5_lines", "y_w", "z_w", "e_planes", "tuned")
-        return [dict(zip(keys, rows[11 * i:11 * i + 11])) for i in range(n.value)]
+        return [dict(zip(keys, rows[w * i:w * i + w])) for i in range(n.value)]
 
     def profile(self) -> dict:
         """Per-kernel (total ms, launches) of the last solve run with profile=True."""

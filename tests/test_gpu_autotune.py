@@ -44,7 +44,7 @@ def test_tuned_schedule_matches_default(build, green, scheme, shape):
         s_tun.close()
     assert [p["tuned"] for p in plans0] == [0] and [p["tuned"] for p in plans1] == [1]
     p = plans1[0]
-    assert p["x1_lines"] in (1, 2, 4, 8) and p["x5_lines"] in (1, 2, 4, 8)
+    assert p["x1_lines"] in (1, 2, 4, 8) and p["x5_lines"] in (1, 2, 4, 8) and p["x1_vb"] in (1, 2, 4)
     assert p["y_w"] in (1, 2, 4, 8, 16) and p["z_w"] in (1, 2, 4, 8, 16)
     assert np.abs(r1.strain - r0.strain).max() < 1e-12
     np.testing.assert_allclose(r1.eta_history, r0.eta_history, rtol=1e-12)
