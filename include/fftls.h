@@ -177,6 +177,22 @@ fftls_status fftls_supported_length(int L);
  * *count is the capacity on entry and the number of kernels on return. */
 fftls_status fftls_profile(const fftls_ctx* ctx, const char** names, double* total_ms, int* launches, int* count);
 
+/* Solves `count` independent problems (any mix of supported grid sizes, each
+ * with its own phases, moduli, reference medium, operator, scheme and eps_bar)
+ * under the shared options `opt`.  opt->eps_init must be NULL; opt->stream, if
+ * set, is synchronised before the work starts.  The samples run concurrently on
+ * `concurrency` worker contexts (0 selects 8, at most 64), each with its own
+ * stream, device buffers, CUDA graphs and tile schedules, largest grid first;
+ * every sample takes the same path as fftls_solve, so results[i] (caller-owned
+ * buffers as in fftls_solve) and statuses[i] (may be NULL) are what fftls_solve
+ * would give (bit for bit with opt->autotune = 0).  Returns FFTLS_OK when every
+ * sample converged, else the first failing status in sample order, with the
+ * sample named in fftls_last_error.  Blocks until all samples are done.  The
+ * paper solves one problem at a time; batching serves many-sample studies
+ * (its Boolean-model statistics). */
+fftls_status fftls_solve_batched(fftls_ctx* ctx, const fftls_problem* probs, int count, const fftls_options* opt,
+                                 fftls_result* results, fftls_status* statuses, int concurrency);
+
 /* Tile schedules held by this context, one row of FFTLS_PLAN_FIELDS ints per grid,
  * operator and precision: {precision (0 float, 1 double), n1, n2, n3, green,
  * lines per batch of the forward x1 pass, voxels per thread it loads together,

@@ -49,7 +49,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = nvcc_path()
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-I", INCLUDE,
+                    "-I", CSRC]
     if extra_flags:
         flags += list(extra_flags)
 
@@ -66,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["--cudart", "static"]
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["--cudart", "static", "-lpthread"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stdout}\n{p.stderr}")

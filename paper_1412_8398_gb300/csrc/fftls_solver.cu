@@ -6,7 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fftls.h"
@@ -24,6 +27,7 @@ const char* const kKindNames[2][kNumKinds] = {
     {"fwd_x_f64", "mid_y_fwd_f64", "fourier_z_f64", "reduce_eta_f64", "mid_y_inv_f64", "inv_x_f64",
      "reduce_delta_f64", "eta_x_f64"}};
 constexpr int kMaxOuter = 8;  // FP64 residual evaluations of the refinement ladder
+constexpr int kMaxWorkers = 64, kDefaultWorkers = 8;  // concurrent solves of fftls_solve_batched
 
 struct DevBuf {
   void* p = nullptr;
@@ -164,6 +168,7 @@ struct fftls_ctx {
   double prof_ms[2][kNumKinds];
   int prof_n[2][kNumKinds];
   std::vector<std::pair<PlanKey, TilePlan>> plans;  // tile schedules per grid and precision
+  std::vector<fftls_ctx*> workers;  // child contexts of fftls_solve_batched
   struct ProfEv { cudaEvent_t a, b; int kind; };
   std::vector<ProfEv> ev;
 };
@@ -809,6 +814,8 @@ fftls_status fftls_create(fftls_ctx** out, int device) {
 
 void fftls_destroy(fftls_ctx* c) {
   if (!c) return;
+  for (fftls_ctx* w : c->workers) fftls_destroy(w);
+  c->workers.clear();
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
@@ -1117,6 +1124,85 @@ fftls_status fftls_solve(fftls_ctx* c, const fftls_problem* p, const fftls_optio
   fftls_status s = solve_impl(c, p, o, r);
   cudaSetDevice(prev);
   return s;
+}
+
+fftls_status fftls_solve_batched(fftls_ctx* c, const fftls_problem* probs, int count, const fftls_options* o,
+                                 fftls_result* results, fftls_status* statuses, int concurrency) {
+  if (!c) return FFTLS_E_INVALID_ARG;
+  c->err.clear();
+  if (count < 0 || (count > 0 && (!probs || !o || !results)))
+    return set_err(c, FFTLS_E_INVALID_ARG, "batched solve: null arrays or negative count");
+  if (count == 0) return FFTLS_OK;
+  if (o->eps_init) return set_err(c, FFTLS_E_INVALID_ARG, "batched solve: eps_init must be NULL");
+  if (concurrency < 0 || concurrency > kMaxWorkers)
+    return set_err(c, FFTLS_E_INVALID_ARG, "batched solve: concurrency must be in 0..%d", kMaxWorkers);
+  const int nw = std::min(concurrency > 0 ? concurrency : kDefaultWorkers, count);
+  while ((int)c->workers.size() < nw) {
+    fftls_ctx* w = nullptr;
+    const fftls_status s = fftls_create(&w, c->device);
+    if (s != FFTLS_OK) return set_err(c, s, "batched solve: cannot create worker context");
+    w->plans = c->plans;
+    c->workers.push_back(w);
+  }
+  if (o->stream) {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)o->stream);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return set_err(c, FFTLS_E_CUDA, "batched solve: %s", cudaGetErrorString(e));
+  }
+  // largest grids first (longest-processing-time order balances the workers)
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  auto voxels = [&](int i) { return (long long)probs[i].n[0] * probs[i].n[1] * probs[i].n[2]; };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return voxels(x) > voxels(y); });
+  fftls_options wo = *o;
+  wo.stream = nullptr;  // each worker runs on its own stream
+  std::atomic<int> next(0);
+  std::vector<fftls_status> st(count, FFTLS_OK);
+  std::vector<std::string> msg(count);
+  std::vector<long long> k0(nw), g0(nw);
+  for (int t = 0; t < nw; ++t) {
+    k0[t] = c->workers[t]->launches;
+    g0[t] = c->workers[t]->graph_launches;
+  }
+  auto work = [&](fftls_ctx* w) {
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= count) break;
+      const int i = order[k];
+      st[i] = fftls_solve(w, &probs[i], &wo, &results[i]);
+      if (st[i] != FFTLS_OK) msg[i] = w->err;
+    }
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(nw);
+  for (int t = 0; t < nw; ++t) pool.emplace_back(work, c->workers[t]);
+  for (auto& t : pool) t.join();
+  for (int t = 0; t < nw; ++t) {
+    fftls_ctx* w = c->workers[t];
+    c->launches += w->launches - k0[t];
+    c->graph_launches += w->graph_launches - g0[t];
+    for (auto& kv : w->plans) {
+      bool have = false;
+      for (auto& mine : c->plans)
+        if (mine.first == kv.first) {
+          have = true;
+          if (kv.second.tuned && !mine.second.tuned) mine.second = kv.second;
+        }
+      if (!have) c->plans.push_back(kv);
+    }
+  }
+  fftls_status worst = FFTLS_OK;
+  for (int i = 0; i < count; ++i) {
+    if (statuses) statuses[i] = st[i];
+    if (st[i] != FFTLS_OK && worst == FFTLS_OK) {
+      worst = st[i];
+      set_err(c, worst, "sample %d: %s", i, msg[i].c_str());
+    }
+  }
+  return worst;
 }
 
 fftls_status fftls_effective_stiffness(fftls_ctx* c, const fftls_problem* p, const fftls_options* o, double* C_eff,

@@ -111,6 +111,9 @@ _SIGNATURES = {
     "fftls_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "fftls_tile_plans": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "fftls_solve_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Problem), ctypes.c_int,
+                                           ctypes.POINTER(_Options), ctypes.POINTER(_Result),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "fftls_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "fftls_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -284,9 +287,22 @@ class Solver:
             device_outputs = on_dev
         o, keep_o = self._options(tol, max_iter, precision, stop, refine_switch, eps_init, device_outputs,
                                   stream, use_graphs, profile, autotune)
+        r, out = self._outputs(p, phase.shape, want_strain, want_stress, history, max_iter, device_outputs)
+        st = self.lib.fftls_solve(self.handle, ctypes.byref(p), ctypes.byref(o), ctypes.byref(r))
+        msg = self.last_error()
+        if st not in (OK, E_NOT_CONVERGED, E_DIVERGED):
+            raise FftlsError(st, msg)
+        if raise_on_error and st == E_DIVERGED:
+            raise FftlsError(st, msg)
+        del keep_p, keep_o
+        return self._collect(st, r, out, msg)
+
+    def _outputs(self, p, grid_shape, want_strain, want_stress, history, max_iter, device_outputs, r=None):
+        """Caller-owned result buffers of one solve (numpy, or torch on the device)."""
         nc = 6 if p.dim == 3 else 3
-        shape = (nc,) + tuple(phase.shape)
-        r = _Result()
+        shape = (nc,) + tuple(grid_shape)
+        if r is None:
+            r = _Result()
         strain = stress = None
         if device_outputs:
             import torch
@@ -309,13 +325,11 @@ class Solver:
             r.eta_history = eh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             r.mean_stress_history = mh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         r.history_capacity = cap
-        st = self.lib.fftls_solve(self.handle, ctypes.byref(p), ctypes.byref(o), ctypes.byref(r))
-        msg = self.last_error()
-        if st not in (OK, E_NOT_CONVERGED, E_DIVERGED):
-            raise FftlsError(st, msg)
-        if raise_on_error and st == E_DIVERGED:
-            raise FftlsError(st, msg)
-        del keep_p, keep_o
+        return r, (strain, stress, eh, mh, nc)
+
+    @staticmethod
+    def _collect(st, r, out, msg):
+        strain, stress, eh, mh, nc = out
         n = r.history_len
         return SolveResult(
             status=st, strain=strain, stress=stress,
@@ -323,6 +337,39 @@ class Solver:
             iterations=r.iterations, iterations_fp32=r.iterations_fp32, final_eta=r.final_eta,
             final_delta=r.final_delta, eta_history=eh[:n].copy(), mean_stress_history=mh[:n].copy(),
             message=msg)
+
+    def solve_batched(self, samples, green="R", scheme="AS", tol=1e-6, max_iter=3000, precision="fp32_refine64",
+                      stop="eta", refine_switch=0.0, concurrency=0, want_strain=False, want_stress=False,
+                      history=False, device_outputs=False, use_graphs=True, autotune=True):
+        """Solve independent problems concurrently (fftls_solve_batched in include/fftls.h).
+
+        samples: sequence of dicts with keys phase, lam, mu, eps_bar and optionally lam0, mu0,
+        green, scheme (overriding the shared arguments).  Returns (list of SolveResult, status).
+        """
+        count = len(samples)
+        probs = (_Problem * max(count, 1))()
+        results = (_Result * max(count, 1))()
+        statuses = (ctypes.c_int * max(count, 1))()
+        keeps, outs = [], []
+        for i, smp in enumerate(samples):
+            p, keep, on_dev = self._problem(smp["phase"], smp["lam"], smp["mu"], smp["eps_bar"],
+                                            smp.get("green", green), smp.get("scheme", scheme),
+                                            smp.get("lam0"), smp.get("mu0"))
+            probs[i] = p
+            keeps.append((keep, smp["phase"]))
+            _, out = self._outputs(p, smp["phase"].shape, want_strain, want_stress, history, max_iter,
+                                   device_outputs, r=results[i])
+            outs.append(out)
+        o, keep_o = self._options(tol, max_iter, precision, stop, refine_switch, None, device_outputs, None,
+                                  use_graphs, False, autotune)
+        st = self.lib.fftls_solve_batched(self.handle, probs, count, ctypes.byref(o), results, statuses,
+                                          int(concurrency))
+        msg = self.last_error()
+        if st not in (OK, E_NOT_CONVERGED, E_DIVERGED):
+            raise FftlsError(st, msg)
+        res = [self._collect(statuses[i], results[i], outs[i], "") for i in range(count)]
+        del keeps, keep_o
+        return res, st
 
     def effective_stiffness(self, phase, lam, mu, green="R", scheme="AS", lam0=None, mu0=None, tol=1e-8,
                             max_iter=1000, precision="fp64", stop="eta", refine_switch=0.0):

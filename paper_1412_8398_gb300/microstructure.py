@@ -25,6 +25,7 @@ import numpy as np
 __all__ = [
     "SplitMix64",
     "boolean_spheres",
+    "batch_recipe",
     "centered_disc",
     "square_inclusion",
     "laminate",
@@ -192,3 +193,35 @@ def binary_moduli(chi: float, dim: int):
     mu1 = 0.6
     return (np.array([lam1, chi * lam1], dtype=np.float64),
             np.array([mu1, chi * mu1], dtype=np.float64))
+
+
+BATCH_LENGTHS = (32, 48, 64, 96, 128)
+
+
+def batch_recipe(count: int, first_seed: int = 1000, lengths=BATCH_LENGTHS):
+    """Parameters of `count` independent Boolean-sphere samples of uneven sizes.
+
+    Sample s (seed first_seed + s) draws, from SplitMix64 seeded with its seed:
+    the grid length L uniformly from `lengths` (cubic grid), the sphere radius
+    uniformly in [3, 8] voxels, the target inclusion fraction uniformly in
+    [0.1, 0.4] and the stiffness contrast E_incl / E_matrix log-uniformly in
+    [10, 1000] (nu = 0.3 in both phases, E_matrix = 1).  The microstructure itself
+    is ``boolean_spheres((L, L, L), radius, fraction, seed)``.
+    Returns a list of dicts with keys seed, L, radius, fraction, contrast.
+    """
+    out = []
+    for s in range(count):
+        seed = first_seed + s
+        u = SplitMix64(seed ^ 0x5A5A5A5A).uniform(4)
+        L = int(lengths[min(int(u[0] * len(lengths)), len(lengths) - 1)])
+        out.append({"seed": seed, "L": L, "radius": 3.0 + 5.0 * float(u[1]),
+                    "fraction": 0.1 + 0.3 * float(u[2]), "contrast": float(10.0 ** (1.0 + 2.0 * u[3]))})
+    return out
+
+
+def batch_sample(spec):
+    """Phase image and (lambda, mu) of one sample of ``batch_recipe``."""
+    L = spec["L"]
+    ph, info = boolean_spheres((L, L, L), spec["radius"], spec["fraction"], spec["seed"])
+    lam, mu = young_poisson_phases([(1.0, 0.3), (spec["contrast"], 0.3)])
+    return ph, lam, mu, info
