@@ -1,0 +1,104 @@
+/* C ABI of the learned warm start of the FFT Lippmann-Schwinger solver.
+ *
+ * A small 3D convolutional network maps a phase image (indicator of phase 1)
+ * and the stiffness contrast to an initial strain field eps^0, which is handed
+ * to fftls_solve as opt->eps_init.  The solver stays the judge: the same
+ * equilibrium criterion (eq. criterion of the paper) decides convergence, so a
+ * poor prediction costs iterations, never accuracy.  The paper has no learned
+ * component: every call below is an implementation feature of this library,
+ * not a step of the paper's method.
+ *
+ * Conventions.  Activations are FP32, [batch][channel][n3][n2][n1] with n1
+ * fastest; N = n1 n2 n3.  3D convolutions have stride 1, circular (periodic)
+ * padding and odd kernel size k in {1, 3}; weights are [c_out][c_in][k][k][k]
+ * (kx fastest), biases [c_out].  All pointers are device pointers on the
+ * current CUDA device unless stated; `stream` is a cudaStream_t (NULL: default
+ * stream).  Calls are asynchronous on `stream`.  Errors: FFTLS_E_INVALID_ARG for
+ * null pointers or sizes out of range (nothing is launched),
+ * FFTLS_E_CUDA when a launch fails.  The caller owns every buffer.
+ */
+#ifndef FFTLS_NN_H
+#define FFTLS_NN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "fftls.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Largest channel count of a convolution (input or output). */
+#define FFTLS_NN_MAX_CHANNELS 128
+
+/* y = act(conv(x, w) + bias + skip): x [batch][c_in][N], y and skip (may be NULL)
+ * [batch][c_out][N], w [c_out][c_in][k^3].  act = ReLU when relu = 1, identity
+ * when 0.  y must not alias x. */
+fftls_status fftls_nn_conv3d(const float* x, const float* w, const float* bias, const float* skip, float* y,
+                             int batch, int c_in, int c_out, const int n[3], int ksize, int relu, void* stream);
+
+/* Gradient with respect to the input of fftls_nn_conv3d: dx = conv^T(dy, w)
+ * (accumulate = 0) or dx += conv^T(dy, w) (accumulate = 1); dy is the gradient
+ * with respect to the pre-activation output, [batch][c_out][N]; dx [batch][c_in][N]. */
+fftls_status fftls_nn_conv3d_backward_data(const float* dy, const float* w, float* dx, int batch, int c_in, int c_out,
+                                           const int n[3], int ksize, int accumulate, void* stream);
+
+/* Gradients with respect to the weights and bias: dw[o][i][k] = sum over batch
+ * and voxels of dy[o](v) x[i](v + offset(k)), db[o] = sum of dy[o].  Written
+ * (not accumulated).  scratch: at least fftls_nn_wgrad_scratch(...) floats of
+ * device memory for the deterministic two-stage reduction. */
+fftls_status fftls_nn_conv3d_backward_weights(const float* x, const float* dy, float* dw, float* db, int batch,
+                                              int c_in, int c_out, const int n[3], int ksize, float* scratch,
+                                              size_t scratch_floats, void* stream);
+size_t fftls_nn_wgrad_scratch(int batch, int c_in, int c_out, const int n[3], int ksize);
+
+/* dy[i] = y[i] > 0 ? dy[i] : 0 (backward of a ReLU whose output is y), count values. */
+fftls_status fftls_nn_relu_backward(float* dy, const float* y, long long count, void* stream);
+
+/* 2x2x2 mean pooling: x [planes][n3][n2][n1] -> y [planes][n3/2][n2/2][n1/2]
+ * (n even); planes = batch * channels.  Backward: dx (=|+=) dy / 8 spread over
+ * each 2x2x2 block. */
+fftls_status fftls_nn_pool2(const float* x, float* y, int planes, const int n[3], void* stream);
+fftls_status fftls_nn_pool2_backward(const float* dy, float* dx, int planes, const int n[3], int accumulate,
+                                     void* stream);
+
+/* Nearest-neighbour 2x upsampling: x [planes][nc3][nc2][nc1] -> y [planes][2nc3][2nc2][2nc1]
+ * (nc = coarse sizes).  Backward: dx = sum of dy over each 2x2x2 block (written). */
+fftls_status fftls_nn_upsample2(const float* x, float* y, int planes, const int nc[3], void* stream);
+fftls_status fftls_nn_upsample2_backward(const float* dy, float* dx, int planes, const int nc[3], void* stream);
+
+/* y += x, count values. */
+fftls_status fftls_nn_add(float* y, const float* x, long long count, void* stream);
+
+/* Mean squared error over count values: *loss (device double) = mean((y - t)^2),
+ * dy = 2 (y - t) / count. */
+fftls_status fftls_nn_mse(const float* y, const float* t, float* dy, double* loss, long long count, void* stream);
+
+/* One Adam step (Kingma and Ba 2015) on count parameters with bias-corrected
+ * moments: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps); step >= 1. */
+fftls_status fftls_nn_adam(float* p, const float* g, float* m, float* v, long long count, float lr, float beta1,
+                           float beta2, float eps, int step, void* stream);
+
+/* Network input from a phase image (uint8 ids, N voxels, device): channel 0 =
+ * indicator of phase 1, channel 1 = log_contrast everywhere; x [2][N]. */
+fftls_status fftls_nn_features(const uint8_t* phase, float* x, const int n[3], float log_contrast, void* stream);
+
+/* Initial strain from a network output y [6][N] (components 11,22,33,23,13,12 of
+ * the fluctuation for the unit load eps_bar = e1 (x) e1): eps [6][N] FP64 =
+ * eps_bar + scale * (y - <y>), so <eps> = eps_bar exactly.  scratch:
+ * FFTLS_NN_STRAIN_SCRATCH doubles of device memory (partial sums). */
+#define FFTLS_NN_STRAIN_SCRATCH 1536
+fftls_status fftls_nn_strain_init(const float* y, double* eps, const int n[3], const double eps_bar[6], double scale,
+                                  double* scratch, void* stream);
+
+/* Training target from a solved strain field: t [6][N] (FP32) = eps - eps_bar,
+ * eps [6][N] FP64 (device). */
+fftls_status fftls_nn_strain_target(const double* eps, float* t, const int n[3], const double eps_bar[6], void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTLS_NN_H */

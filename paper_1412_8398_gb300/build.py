@@ -1,7 +1,7 @@
 """Build the in-tree CUDA library ``_build/libfftls.so`` for sm_103a with nvcc.
 
-The two translation units are compiled in parallel and linked into a shared
-library exporting the C ABI of ``include/fftls.h``.  The build is skipped
+The translation units are compiled in parallel and linked into a shared
+library exporting the C ABI of ``include/fftls.h`` and ``include/fftls_nn.h``.  The build is skipped
 when the library is newer than every source and header.
 """
 from __future__ import annotations
@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfftls.so")
-SOURCES = ["fftls_kernels.cu", "fftls_solver.cu"]
+SOURCES = ["fftls_kernels.cu", "fftls_solver.cu", "fftls_nn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,7 +1,8 @@
-"""The C-ABI library builds, loads and exports every function of include/fftls.h.
+"""The C-ABI library builds, loads and exports every function of include/*.h.
 
 Runs without a GPU: only host-side entry points are called.
 """
+import ctypes
 import math
 import os
 import re
@@ -10,13 +11,16 @@ import shutil
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "fftls.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 def _declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(fftls_[a-z_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(fftls_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -41,8 +45,15 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_binding_signatures_cover_header(lib):
-    from paper_1412_8398_gb300 import fftls
-    assert set(_declared_functions()) == set(fftls._SIGNATURES)
+    from paper_1412_8398_gb300 import fftls, warmstart
+    assert set(_declared_functions()) == set(fftls._SIGNATURES) | set(warmstart._NN_SIGNATURES)
+
+
+def test_nn_host_calls(lib):
+    from paper_1412_8398_gb300 import warmstart
+    n = (ctypes.c_int * 3)(8, 8, 8)
+    assert lib.fftls_nn_wgrad_scratch(1, 2, 8, n, 3) >= 2 * 8 * 28
+    assert warmstart.parameter_count() == sum(co * ci * k ** 3 + co for _, ci, co, k, _ in warmstart.LAYERS)
 
 
 def test_host_only_calls(lib):
