@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--batched", type=int, default=0,
                     help="instead of the 512^3 workload, time COUNT batched Boolean samples of uneven sizes")
     ap.add_argument("--concurrency", type=int, default=8, help="worker streams of the batched solve")
+    ap.add_argument("--warmstart", type=int, default=0,
+                    help="instead of the 512^3 workload, train the warm-start network on COUNT solver-generated "
+                         "64^3 samples and compare warm and plain starts on 256^3 samples")
+    ap.add_argument("--warm-epochs", type=int, default=4)
+    ap.add_argument("--warm-apply", type=int, default=4, help="256^3 samples of the warm-start comparison")
     return ap.parse_args()
 
 
@@ -363,6 +368,81 @@ def run_batched(args, rank, local, world):
     solver.close()
 
 
+def run_warmstart(args, rank, local, world):
+    """Learned warm start: train on COUNT solver-generated 64^3 Boolean samples (radius 3-8,
+    fraction 0.1-0.4, contrast 10-1000, eps_bar_11 = 1, AS with G^R to eta <= 1e-6), then on
+    --warm-apply 256^3 samples of the same recipe compare, each to eta <= 1e-6 with the same
+    criterion: the ladder from eps_bar, the ladder from the network's eps^0 (inference timed in),
+    and plain FP64 from eps_bar.  Rank 0 only (a single training run)."""
+    import numpy as np
+    import torch
+    from paper_1412_8398_gb300 import build, fftls, microstructure as MS, warmstart as WS
+
+    if rank != 0:
+        return
+    build.build()
+    torch.cuda.set_device(local)
+    solver = fftls.Solver(local)
+    data, t_data = WS.make_dataset(solver, args.warmstart, 64, first_seed=20000, concurrency=args.concurrency)
+    net = WS.WarmNet(device=local, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.train(data, epochs=args.warm_epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del data
+    specs = MS.batch_recipe(args.warm_apply, first_seed=30000, lengths=(256,))
+    eb = np.diag([1.0, 0.0, 0.0])
+    kw = dict(green="R", scheme="AS", tol=1e-6, max_iter=args.max_iter, want_strain=False, want_stress=False)
+    rows = []
+    first = True
+    for spec in specs:
+        ph, lam, mu, info = MS.batch_sample(spec)
+        dph = torch.from_numpy(ph).cuda()
+        if first:   # tile schedules and buffers of 256^3 outside the timed solves
+            solver.solve(dph, lam, mu, eb, precision="fp32_refine64", **dict(kw, max_iter=3), raise_on_error=False)
+            solver.solve(dph, lam, mu, eb, precision="fp64", **dict(kw, max_iter=3), raise_on_error=False)
+            net.initial_strain(dph, spec["contrast"])
+            first = False
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            return out, time.perf_counter() - t
+
+        r0, t0_ = timed(lambda: solver.solve(dph, lam, mu, eb, precision="fp32_refine64", **kw))
+        e0, t_inf = timed(lambda: net.initial_strain(dph, spec["contrast"]))
+        r1, t1_ = timed(lambda: solver.solve(dph, lam, mu, eb, precision="fp32_refine64", eps_init=e0, **kw))
+        r64, t64 = timed(lambda: solver.solve(dph, lam, mu, eb, precision="fp64", **kw))
+        rows.append({"contrast": spec["contrast"], "fraction": info["fraction"], "radius": spec["radius"],
+                     "zero": {"iterations": r0.iterations, "time_s": t0_, "converged": r0.converged},
+                     "warm": {"iterations": r1.iterations, "time_s": t1_ + t_inf, "inference_s": t_inf,
+                              "converged": r1.converged},
+                     "fp64": {"iterations": r64.iterations, "time_s": t64, "converged": r64.converged},
+                     "warm_vs_zero_rel_mean_stress": float(np.abs(r1.mean_stress - r0.mean_stress).max()
+                                                           / np.abs(r0.mean_stress).max())})
+        del e0, dph
+    tot = lambda k, f: float(sum(r[k][f] for r in rows))
+    out = {
+        "metric": "time to eta <= 1e-6 with the learned warm start (AS, G^R, 256^3)", "unit": "s",
+        "value": tot("warm", "time_s") / len(rows), "higher_is_better": False, "n_gpus": 1, "impl": "ours",
+        "data": "synthetic", "dtype": "f32+f64",
+        "config": {"workload": f"warmstart_train_{args.warmstart}x64^3_apply_{args.warm_apply}x256^3_boolean",
+                   "train_samples": args.warmstart, "epochs": args.warm_epochs,
+                   "parameters": WS.parameter_count()},
+        "data_seconds": t_data, "train_seconds": t_train, "train_loss_per_epoch": losses,
+        "iterations": {"zero_init": tot("zero", "iterations"), "warm": tot("warm", "iterations"),
+                       "fp64_zero_init": tot("fp64", "iterations")},
+        "time_s": {"zero_init_ladder": tot("zero", "time_s"), "warm_ladder_incl_inference": tot("warm", "time_s"),
+                   "fp64_zero_init": tot("fp64", "time_s")},
+        "samples": rows,
+    }
+    print(json.dumps(out))
+    solver.close()
+
+
 def main():
     args = parse()
     rank, local, world = dist_setup()
@@ -371,6 +451,9 @@ def main():
         return
     if args.batched > 0:
         run_batched(args, rank, local, world)
+        return
+    if args.warmstart > 0:
+        run_warmstart(args, rank, local, world)
         return
     import numpy as np
     import torch
