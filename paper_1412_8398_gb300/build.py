@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfftls.so")
-SOURCES = ["fftls_kernels.cu", "fftls_solver.cu", "fftls_nn.cu"]
+SOURCES = ["fftls_kernels_x32.cu", "fftls_kernels_x64.cu", "fftls_kernels_y32.cu", "fftls_kernels_y64.cu",
+           "fftls_kernels_z32.cu", "fftls_kernels_z64.cu", "fftls_solver.cu", "fftls_nn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

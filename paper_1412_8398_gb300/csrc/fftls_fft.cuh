@@ -248,6 +248,70 @@ __device__ void tile_fft_p2(T2* buf, int nblk, int BS, int C, int ncols, const T
   }
 }
 
+// Stage S of the power-of-two plan of length L on tiles whose geometry is
+// known at compile time: C complex values per row (row stride), the first
+// NCOLS columns transformed, rows padded (PAD) or not.  Every butterfly of a
+// stage then reads and writes at compile-time offsets from one base address:
+// with rows e0 + r MR, the padded row index prow(e0 + r MR) equals
+// prow(e0) + r MR + floor(r MR / 8) for every stage of the plans above (MR is a
+// multiple of 8, or e0 mod 8 + r MR mod 8 < 8).
+template <int L, int S, int C, int NCOLS, bool PAD, bool INV, typename T2>
+__device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
+  constexpr int R = p2_radix(L, S);
+  constexpr int M = p2_msize(L, S);
+  constexpr int MR = M / R;
+  constexpr int NB = L / R;
+  constexpr int TSTR = L / M;
+  constexpr int BS = (PAD ? padded_rows(L) : L) * C;
+  const int total = nblk * NB * NCOLS;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int rest = idx / NCOLS;
+    const int c = idx - rest * NCOLS;
+    const int bf = rest & (NB - 1);
+    const int blk = rest / NB;
+    const int b = bf / MR, j = bf & (MR - 1);
+    const int e0 = b * M + j;
+    T2* base = buf + blk * BS + (PAD ? prow(e0, 1) : e0) * C + c;
+    T2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = base[(PAD ? r * MR + ((r * MR) >> 3) : r * MR) * C];
+    if (!INV) {
+      dft_fixed<R>(v, false);
+      if (MR > 1 && j) {
+        const T2* tj = tw + j * TSTR;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tj[(r - 1) * j * TSTR]);
+      }
+    } else {
+      if (MR > 1 && j) {
+        const T2* tj = tw + j * TSTR;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], tj[(r - 1) * j * TSTR]);
+      }
+      dft_fixed<R>(v, true);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[(PAD ? r * MR + ((r * MR) >> 3) : r * MR) * C] = v[r];
+  }
+  __syncthreads();
+}
+
+template <int L, int C, int NCOLS, bool PAD, typename T2>
+__device__ __forceinline__ void tile_fft_p2_ct(T2* buf, int nblk, const T2* tw, bool inv) {
+  constexpr int NST = p2_nst(L);
+  if (!inv) {
+    if constexpr (NST > 0) p2_stage_ct<L, 0, C, NCOLS, PAD, false>(buf, nblk, tw);
+    if constexpr (NST > 1) p2_stage_ct<L, 1, C, NCOLS, PAD, false>(buf, nblk, tw);
+    if constexpr (NST > 2) p2_stage_ct<L, 2, C, NCOLS, PAD, false>(buf, nblk, tw);
+    if constexpr (NST > 3) p2_stage_ct<L, 3, C, NCOLS, PAD, false>(buf, nblk, tw);
+  } else {
+    if constexpr (NST > 3) p2_stage_ct<L, 3, C, NCOLS, PAD, true>(buf, nblk, tw);
+    if constexpr (NST > 2) p2_stage_ct<L, 2, C, NCOLS, PAD, true>(buf, nblk, tw);
+    if constexpr (NST > 1) p2_stage_ct<L, 1, C, NCOLS, PAD, true>(buf, nblk, tw);
+    if constexpr (NST > 0) p2_stage_ct<L, 0, C, NCOLS, PAD, true>(buf, nblk, tw);
+  }
+}
+
 // Mixed-radix transform for any supported length (runtime plan).
 template <typename T2>
 __device__ void tile_fft_generic(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv,
@@ -297,13 +361,15 @@ __device__ void tile_fft_generic(T2* buf, int nblk, int BS, int C, int ncols, co
   }
 }
 
-// In-place transform of a tile (see the file comment).  tw[t] = e^{-2 pi i t / L}
-// (shared memory).  Power-of-two lengths up to 1024 run a compile-time plan.
-// Ends with __syncthreads() when the length has at least one stage.
-// pad = 1: row e of the tile is stored at prow(e) (x1-line tiles).
+// In-place transform of a tile (see the file comment) with a runtime tile
+// geometry, for the lengths tile_fft_ct does not specialise: the short and the
+// longest powers of two run their fixed plans, any other length the runtime
+// plan.  tw[t] = e^{-2 pi i t / L} (shared memory).  Ends with __syncthreads()
+// when the length has at least one stage.  pad = 1: row e of the tile is stored
+// at prow(e) (x1-line tiles).
 template <typename T2>
-__device__ void tile_fft(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv,
-                         int pad = 0) {
+__device__ void tile_fft_rt(T2* buf, int nblk, int BS, int C, int ncols, const AxisPlan& p, const T2* tw, bool inv,
+                            int pad) {
   switch (p.L) {
     case 1: return;
     case 2: tile_fft_p2<2>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
@@ -311,12 +377,23 @@ __device__ void tile_fft(T2* buf, int nblk, int BS, int C, int ncols, const Axis
     case 8: tile_fft_p2<8>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
     case 16: tile_fft_p2<16>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
     case 32: tile_fft_p2<32>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
-    case 64: tile_fft_p2<64>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
-    case 128: tile_fft_p2<128>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
-    case 256: tile_fft_p2<256>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
-    case 512: tile_fft_p2<512>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
     case 1024: tile_fft_p2<1024>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
     default: tile_fft_generic(buf, nblk, BS, C, ncols, p, tw, inv, pad); return;
+  }
+}
+
+// tile_fft with the tile geometry fixed at compile time (row stride C complex
+// values, first NCOLS columns transformed, padded rows when PAD): the lengths
+// 64..512 that are powers of two take the compile-time stages, any other
+// length the runtime paths.  BS is the block stride of the general path.
+template <int C, int NCOLS, bool PAD, typename T2>
+__device__ void tile_fft_ct(T2* buf, int nblk, int BS, const AxisPlan& p, const T2* tw, bool inv) {
+  switch (p.L) {
+    case 64: tile_fft_p2_ct<64, C, NCOLS, PAD>(buf, nblk, tw, inv); return;
+    case 128: tile_fft_p2_ct<128, C, NCOLS, PAD>(buf, nblk, tw, inv); return;
+    case 256: tile_fft_p2_ct<256, C, NCOLS, PAD>(buf, nblk, tw, inv); return;
+    case 512: tile_fft_p2_ct<512, C, NCOLS, PAD>(buf, nblk, tw, inv); return;
+    default: tile_fft_rt(buf, nblk, BS, C, NCOLS, p, tw, inv, PAD ? 1 : 0); return;
   }
 }
 

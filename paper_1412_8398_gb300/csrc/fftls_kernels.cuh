@@ -135,6 +135,9 @@ template <typename T> cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaSt
 template <typename T> cudaError_t launch_inv_x(const IterArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t set_kernel_attributes(const IterArgs<T>& a, size_t smax);
+// dynamic shared-memory limits of the x2 and x3 kernels (their own translation units)
+template <typename T> cudaError_t set_attrs_y(size_t smax);
+template <typename T> cudaError_t set_attrs_z(size_t smax);
 
 // Elementwise helpers.
 template <typename T> cudaError_t launch_fill_eps(T* eps, int nc, long long N, const double* eps_bar6, cudaStream_t s);

@@ -1,4 +1,9 @@
+#pragma once
 // CUDA kernels of the FFT Lippmann-Schwinger iteration (Willot 2015), sm_103a.
+// Implementation header: the kernel and launcher templates.  The translation
+// units fftls_kernels_x32/_x64.cu (x1 passes, eta, reductions, helpers),
+// _y32/_y64 (x2 pass) and _z32/_z64 (x3 + Fourier pass) each instantiate their
+// share, so the library's kernels compile in parallel.
 //
 // One iteration is five passes over the fields in HBM:
 //   K1 fwd_x     : sigma = C(x):eps (and tau = sigma - C0:eps) per voxel,
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
   const T2* tws = load_twiddles(a.tw[0], L1, &tile);
   constexpr int nout = DUAL ? 2 * NC : NC;
   constexpr int NP = (nout + 1) / 2;
-  const int CP = odd_stride(NP);
+  constexpr int CP = odd_stride(NP);
   const int BS = padded_rows(L1) * CP;
   const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
       if (lane == 0) wacc[warp][c] += (double)x;
     }
     __syncthreads();
-    tile_fft(tile, nl, BS, CP, NP, a.pl[0], tws, false, 1);
+    tile_fft_ct<CP, NP, true>(tile, nl, BS, a.pl[0], tws, false);
     for (int idx = threadIdx.x; idx < nl * H * NP; idx += blockDim.x) {
       const int rest = fdiv(idx, fNP);
       const int p = idx - rest * NP;
@@ -419,7 +424,9 @@ __global__ void __launch_bounds__(kEThreads) k_eta_stencil(IterArgs<T> a) {
 // ---------------------------------------------------------------------------
 // K2: transform along x2, in place; tiles of y_w modes x n2 rows x n_c
 // ---------------------------------------------------------------------------
-template <typename T, int NC>
+// W: modes per tile (a compile-time tile geometry; the last tile along x1 may
+// hold fewer modes, its other columns are transformed but never stored).
+template <typename T, int NC, int W>
 __global__ void __launch_bounds__(512) k_mid_y(IterArgs<T> a, int inv) {
   typedef typename Cplx<T>::type T2;
   const int st = a.ctrl->state;
@@ -428,15 +435,15 @@ __global__ void __launch_bounds__(512) k_mid_y(IterArgs<T> a, int inv) {
   const int n2 = g.n2;
   T2* tile;
   const T2* tws = load_twiddles(a.tw[1], n2, &tile);
-  const int W = a.y_w;
   const int x0 = blockIdx.x * W;
   const int nx = min(W, g.H - x0);
-  const int C = W * NC, cols = nx * NC;
+  constexpr int C = W * NC;
+  const int cols = nx * NC;
   T2* spec = blockIdx.z ? a.specB : a.specA;
   const long long base = ((long long)blockIdx.y * n2 * g.H + x0) * NC;
   const long long rstride = (long long)g.H * NC;
   tile_load(tile, C, spec + base, rstride, n2, cols);
-  tile_fft(tile, 1, 0, C, cols, a.pl[1], tws, inv != 0);
+  tile_fft_ct<C, C, false>(tile, 1, 0, a.pl[1], tws, inv != 0);
   tile_store(tile, C, spec + base, rstride, n2, cols);
 }
 
@@ -671,7 +678,7 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
   for (int c = 0; c < NC; ++c) X[c] = E[c];
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, int W>
 __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
@@ -680,21 +687,21 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   const int n3 = g.n3;
   T2* tile;
   const T2* tws = load_twiddles(a.tw[2], n3, &tile);
-  const int W = a.z_w;
   const int x0 = blockIdx.x * W;
   const int py = blockIdx.y;
   const int kind = blockIdx.z;
   const bool do_green = kind == 0;
   const bool do_eta = !a.eta_real && (a.dual ? (kind == 1) : true);
   const int nx = min(W, g.H - x0);
-  const int C = W * NC, cols = nx * NC;
+  constexpr int C = W * NC;
+  const int cols = nx * NC;
   T2* spec = kind ? a.specB : a.specA;
   const long long base = ((long long)py * g.H + x0) * NC;
   const long long zstride = (long long)g.n2 * g.H * NC;
   const FastDiv fnx = make_fastdiv(nx);
   tile_load(tile, C, spec + base, zstride, n3, cols);
   const int ym = __ldg(&a.perm[1][py]);
-  tile_fft(tile, 1, 0, C, cols, a.pl[2], tws, false);
+  tile_fft_ct<C, C, false>(tile, 1, 0, a.pl[2], tws, false);
   T eta_acc = (T)0;
   for (int idx = threadIdx.x; idx < n3 * nx; idx += blockDim.x) {
     const int pz = fdiv(idx, fnx), xc = idx - pz * nx;
@@ -711,7 +718,7 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   }
   __syncthreads();
   if (do_green) {
-    tile_fft(tile, 1, 0, C, cols, a.pl[2], tws, true);
+    tile_fft_ct<C, C, false>(tile, 1, 0, a.pl[2], tws, true);
     tile_store(tile, C, spec + base, zstride, n3, cols);
   }
   if (!a.eta_real) {  // with the real-space eta the x1 pass owns part_eta
@@ -831,7 +838,7 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
       }
     }
     __syncthreads();
-    tile_fft(tile, nl, BS, CP, NPI, a.pl[0], tws, true, 1);
+    tile_fft_ct<CP, NPI, true>(tile, nl, BS, a.pl[0], tws, true);
     for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
       const int gl = fdiv(idx, fL), x = idx - gl * L1;
       const long long vox = (l0 + gl) * (long long)L1 + x;
@@ -937,10 +944,12 @@ __global__ void k_convert(TO* out, const TI* in, long long n) {
     out[i] = (TO)in[i];
 }
 
+#ifdef FFTLS_KERNELS_MAIN
 __global__ void k_add_correction(double* out, const float* in, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] += (double)in[i];
 }
+#endif
 
 template <typename T, int DIM>
 __global__ void k_stress(const T* eps, const uint8_t* phase, const T* coef, long long N, double* stress,
@@ -969,6 +978,7 @@ __global__ void k_stress(const T* eps, const uint8_t* phase, const T* coef, long
     for (int c = 0; c < 2 * NC; ++c) part[(size_t)blockIdx.x * 2 * NC + c] = acc[c];
 }
 
+#ifdef FFTLS_KERNELS_MAIN
 __global__ void k_phase_max(const uint8_t* phase, long long N, unsigned int* out) {
   unsigned int m = 0;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x)
@@ -976,7 +986,9 @@ __global__ void k_phase_max(const uint8_t* phase, long long N, unsigned int* out
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
+#endif
 
+#ifdef FFTLS_KERNELS_MAIN
 __global__ void k_sum_parts(const double* part, int blocks, int width, double* out) {
   // one thread per output value, fixed order: deterministic
   const int c = threadIdx.x;
@@ -985,6 +997,7 @@ __global__ void k_sum_parts(const double* part, int blocks, int width, double* o
   for (int b = 0; b < blocks; ++b) s += part[(size_t)b * width + c];
   out[c] = s;
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // launchers
@@ -992,14 +1005,18 @@ __global__ void k_sum_parts(const double* part, int blocks, int width, double* o
 template <typename T>
 cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) {
 #define FFTLS_FWD(D, U, V) k_fwd_x<T, D, U, V><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a)
-#define FFTLS_FWD_VB(D, U) \
-  (a.x1_vb >= 4 ? FFTLS_FWD(D, U, 4) : a.x1_vb == 2 ? FFTLS_FWD(D, U, 2) : FFTLS_FWD(D, U, 1))
+// FP64 forward passes (the few certification passes of the ladder) load one voxel at a time
+#define FFTLS_FWD_VB(D, U)                                                                              \
+  if constexpr (sizeof(T) == 8) FFTLS_FWD(D, U, 1);                                                     \
+  else if (a.x1_vb >= 4) FFTLS_FWD(D, U, 4);                                                            \
+  else if (a.x1_vb == 2) FFTLS_FWD(D, U, 2);                                                            \
+  else FFTLS_FWD(D, U, 1)
   if (a.dim == 3) {
-    if (a.dual) FFTLS_FWD_VB(3, true);
-    else FFTLS_FWD_VB(3, false);
+    if (a.dual) { FFTLS_FWD_VB(3, true); }
+    else { FFTLS_FWD_VB(3, false); }
   } else {
-    if (a.dual) FFTLS_FWD_VB(2, true);
-    else FFTLS_FWD_VB(2, false);
+    if (a.dual) { FFTLS_FWD_VB(2, true); }
+    else { FFTLS_FWD_VB(2, false); }
   }
 #undef FFTLS_FWD_VB
 #undef FFTLS_FWD
@@ -1017,16 +1034,40 @@ template <typename T>
 cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s) {
   if (a.g.n2 == 1) return cudaSuccess;
   dim3 grid((a.g.H + a.y_w - 1) / a.y_w, a.g.n3, (!inv && a.dual && !a.eta_real) ? 2 : 1);
-  if (a.dim == 3) k_mid_y<T, 6><<<grid, a.y_threads, a.y_smem, s>>>(a, inv ? 1 : 0);
-  else k_mid_y<T, 3><<<grid, a.y_threads, a.y_smem, s>>>(a, inv ? 1 : 0);
+#define FFTLS_MIDY(NCV, WV) k_mid_y<T, NCV, WV><<<grid, a.y_threads, a.y_smem, s>>>(a, inv ? 1 : 0)
+#define FFTLS_MIDY_W(NCV)                                                                               \
+  switch (a.y_w) {                                                                                      \
+    case 1: FFTLS_MIDY(NCV, 1); break;                                                                  \
+    case 2: FFTLS_MIDY(NCV, 2); break;                                                                  \
+    case 4: FFTLS_MIDY(NCV, 4); break;                                                                  \
+    case 8: FFTLS_MIDY(NCV, 8); break;                                                                  \
+    case 16: FFTLS_MIDY(NCV, 16); break;                                                                \
+    default: return cudaErrorInvalidValue;                                                              \
+  }
+  if (a.dim == 3) { FFTLS_MIDY_W(6) }
+  else { FFTLS_MIDY_W(3) }
+#undef FFTLS_MIDY_W
+#undef FFTLS_MIDY
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s) {
   dim3 grid((a.g.H + a.z_w - 1) / a.z_w, a.g.n2, (a.dual && !a.eta_real) ? 2 : 1);
-  if (a.dim == 3) k_fourier_z<T, 3><<<grid, a.z_threads, a.z_smem, s>>>(a);
-  else k_fourier_z<T, 2><<<grid, a.z_threads, a.z_smem, s>>>(a);
+#define FFTLS_FZ(D, WV) k_fourier_z<T, D, WV><<<grid, a.z_threads, a.z_smem, s>>>(a)
+#define FFTLS_FZ_W(D)                                                                                   \
+  switch (a.z_w) {                                                                                      \
+    case 1: FFTLS_FZ(D, 1); break;                                                                      \
+    case 2: FFTLS_FZ(D, 2); break;                                                                      \
+    case 4: FFTLS_FZ(D, 4); break;                                                                      \
+    case 8: FFTLS_FZ(D, 8); break;                                                                      \
+    case 16: FFTLS_FZ(D, 16); break;                                                                    \
+    default: return cudaErrorInvalidValue;                                                              \
+  }
+  if (a.dim == 3) { FFTLS_FZ_W(3) }
+  else { FFTLS_FZ_W(2) }
+#undef FFTLS_FZ_W
+#undef FFTLS_FZ
   return cudaGetLastError();
 }
 
@@ -1053,36 +1094,70 @@ cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s) {
 }
 
 // Every kernel of the iteration may take up to smax bytes of dynamic shared
-// memory (any tile schedule the host picks stays below it).
+// memory (any tile schedule the host picks stays below it).  One function per
+// translation unit, each touching only the kernels that unit instantiates.
+#define FFTLS_ATTR(fn)                                                                                          \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+
+template <typename T>
+cudaError_t set_attrs_y(size_t smax) {
+  cudaError_t e = cudaSuccess;
+  FFTLS_ATTR((k_mid_y<T, 6, 1>));
+  FFTLS_ATTR((k_mid_y<T, 6, 2>));
+  FFTLS_ATTR((k_mid_y<T, 6, 4>));
+  FFTLS_ATTR((k_mid_y<T, 6, 8>));
+  FFTLS_ATTR((k_mid_y<T, 6, 16>));
+  FFTLS_ATTR((k_mid_y<T, 3, 1>));
+  FFTLS_ATTR((k_mid_y<T, 3, 2>));
+  FFTLS_ATTR((k_mid_y<T, 3, 4>));
+  FFTLS_ATTR((k_mid_y<T, 3, 8>));
+  FFTLS_ATTR((k_mid_y<T, 3, 16>));
+  return e;
+}
+
+template <typename T>
+cudaError_t set_attrs_z(size_t smax) {
+  cudaError_t e = cudaSuccess;
+  FFTLS_ATTR((k_fourier_z<T, 3, 1>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 2>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 4>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 8>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 16>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 1>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 2>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 4>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 8>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 16>));
+  return e;
+}
+
 template <typename T>
 cudaError_t set_kernel_attributes(const IterArgs<T>& a, size_t smax) {
   cudaError_t e = cudaSuccess;
   (void)a;
-#define FFTLS_ATTR(fn)                                                                                          \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
   FFTLS_ATTR((k_eta_stencil<T, true>));
   FFTLS_ATTR((k_eta_stencil<T, false>));
   FFTLS_ATTR((k_fwd_x<T, 3, true, 1>));
-  FFTLS_ATTR((k_fwd_x<T, 3, true, 2>));
-  FFTLS_ATTR((k_fwd_x<T, 3, true, 4>));
   FFTLS_ATTR((k_fwd_x<T, 3, false, 1>));
-  FFTLS_ATTR((k_fwd_x<T, 3, false, 2>));
-  FFTLS_ATTR((k_fwd_x<T, 3, false, 4>));
-  FFTLS_ATTR((k_inv_x<T, 3>));
-  FFTLS_ATTR((k_fourier_z<T, 3>));
-  FFTLS_ATTR((k_mid_y<T, 6>));
   FFTLS_ATTR((k_fwd_x<T, 2, true, 1>));
-  FFTLS_ATTR((k_fwd_x<T, 2, true, 2>));
-  FFTLS_ATTR((k_fwd_x<T, 2, true, 4>));
   FFTLS_ATTR((k_fwd_x<T, 2, false, 1>));
-  FFTLS_ATTR((k_fwd_x<T, 2, false, 2>));
-  FFTLS_ATTR((k_fwd_x<T, 2, false, 4>));
+  if constexpr (sizeof(T) == 4) {
+    FFTLS_ATTR((k_fwd_x<T, 3, true, 2>));
+    FFTLS_ATTR((k_fwd_x<T, 3, true, 4>));
+    FFTLS_ATTR((k_fwd_x<T, 3, false, 2>));
+    FFTLS_ATTR((k_fwd_x<T, 3, false, 4>));
+    FFTLS_ATTR((k_fwd_x<T, 2, true, 2>));
+    FFTLS_ATTR((k_fwd_x<T, 2, true, 4>));
+    FFTLS_ATTR((k_fwd_x<T, 2, false, 2>));
+    FFTLS_ATTR((k_fwd_x<T, 2, false, 4>));
+  }
+  FFTLS_ATTR((k_inv_x<T, 3>));
   FFTLS_ATTR((k_inv_x<T, 2>));
-  FFTLS_ATTR((k_fourier_z<T, 2>));
-  FFTLS_ATTR((k_mid_y<T, 3>));
-#undef FFTLS_ATTR
+  if (e == cudaSuccess) e = set_attrs_y<T>(smax);
+  if (e == cudaSuccess) e = set_attrs_z<T>(smax);
   return e;
 }
+#undef FFTLS_ATTR
 
 template <typename T>
 cudaError_t launch_fill_eps(T* eps, int nc, long long N, const double* e, cudaStream_t s) {
@@ -1098,11 +1173,13 @@ cudaError_t launch_convert(TO* out, const TI* in, long long n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+#ifdef FFTLS_KERNELS_MAIN
 cudaError_t launch_add_correction(double* out, const float* in, long long n, cudaStream_t s) {
   const int blocks = (int)min((n + 255) / 256, (long long)152 * 16);
   k_add_correction<<<blocks, 256, 0, s>>>(out, in, n);
   return cudaGetLastError();
 }
+#endif
 
 template <typename T>
 cudaError_t launch_stress(const T* eps, const uint8_t* phase, const T* coef, int dim, long long N, double* stress_out,
@@ -1112,34 +1189,22 @@ cudaError_t launch_stress(const T* eps, const uint8_t* phase, const T* coef, int
   return cudaGetLastError();
 }
 
+#ifdef FFTLS_KERNELS_MAIN
 cudaError_t launch_phase_max(const uint8_t* phase, long long N, unsigned int* out, int blocks, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   k_phase_max<<<blocks, 256, 0, s>>>(phase, N, out);
   return cudaGetLastError();
 }
+#endif
 
+#ifdef FFTLS_KERNELS_MAIN
 cudaError_t launch_sum_parts(const double* part, int blocks, int width, double* out, cudaStream_t s) {
   k_sum_parts<<<1, 32, 0, s>>>(part, blocks, width, out);
   return cudaGetLastError();
 }
+#endif
 
-#define FFTLS_INST(T)                                                                                   \
-  template cudaError_t launch_fwd_x<T>(const IterArgs<T>&, cudaStream_t);                              \
-  template cudaError_t launch_eta_stencil<T>(const IterArgs<T>&, cudaStream_t);                        \
-  template cudaError_t launch_mid_y<T>(const IterArgs<T>&, bool, cudaStream_t);                        \
-  template cudaError_t launch_fourier_z<T>(const IterArgs<T>&, cudaStream_t);                          \
-  template cudaError_t launch_reduce_eta<T>(const IterArgs<T>&, cudaStream_t);                         \
-  template cudaError_t launch_inv_x<T>(const IterArgs<T>&, cudaStream_t);                              \
-  template cudaError_t launch_reduce_delta<T>(const IterArgs<T>&, cudaStream_t);                       \
-  template cudaError_t set_kernel_attributes<T>(const IterArgs<T>&, size_t);                            \
-  template cudaError_t launch_fill_eps<T>(T*, int, long long, const double*, cudaStream_t);            \
-  template cudaError_t launch_stress<T>(const T*, const uint8_t*, const T*, int, long long, double*,   \
-                                        double*, int, cudaStream_t);
-FFTLS_INST(float)
-FFTLS_INST(double)
-template cudaError_t launch_convert<double, float>(double*, const float*, long long, cudaStream_t);
-template cudaError_t launch_convert<float, double>(float*, const double*, long long, cudaStream_t);
-template cudaError_t launch_convert<double, double>(double*, const double*, long long, cudaStream_t);
+
 
 }  // namespace fftls

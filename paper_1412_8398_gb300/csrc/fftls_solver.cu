@@ -374,7 +374,7 @@ TilePlan default_plan(const Setup& S, size_t cb, bool real_eta) {
   P.tuned = 0;
   P.x1_lines = (int)std::max<size_t>(1, (real_eta ? 32 * 1024 : 64 * 1024) / G.line1);
   P.x5_lines = (int)std::max<size_t>(1, (32 * 1024) / G.line5);
-  P.x1_vb = 4;
+  P.x1_vb = cb == 16 ? 1 : 4;  // double precision loads one voxel at a time
   auto pick_w = [&](int L) {
     int w = 16;
     while (w > 1 && strided_smem(L, w, S.nc, cb) > std::min<size_t>(G.lim, 100 * 1024)) w /= 2;
@@ -638,8 +638,9 @@ fftls_status tune_plan(fftls_ctx* c, const Setup& S, IterArgs<T>& a, bool real_e
   {
     float best = INFINITY;
     int bl = P.x1_lines, bv = P.x1_vb;
+    const std::vector<int> vbs = sizeof(T) == 8 ? std::vector<int>{1} : std::vector<int>{1, 2, 4};
     for (int lines : {1, 2, 4, 8})
-      for (int vb : {1, 2, 4}) {
+      for (int vb : vbs) {
         if (err != cudaSuccess) break;
         TilePlan Q = P;
         Q.x1_lines = lines;
