@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--precision", default="fp32_refine64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the unfused cuFFT baseline")
     ap.add_argument("--cpu-n", type=int, default=128)
     ap.add_argument("--cpu-iters", type=int, default=5)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 time-to-tolerance solve")
@@ -256,6 +257,127 @@ print(json.dumps({{"seconds": dt, "voxels": int(ph.size), "iters": {iters}}}))
     return {"value": r["voxels"] * r["iters"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{r['iters']} AS/G^R iterations of the FP64 numpy oracle on the same recipe at {n}^3 "
                       f"(radius scaled to {8.0 * n / 512:g}), single thread, {r['seconds']:.1f} s"}
+
+
+class CufftBaseline:
+    """Unfused library baseline of one AS / G^R iteration in FP32: torch elementwise
+    kernels for sigma = C(x):eps and tau = sigma - C0:eps, cuFFT (torch.fft) real-to-
+    complex transforms of sigma (for eta) and tau, G' of G^R applied per mode on the
+    half spectrum, the inverse transform and the accelerated update.  A timing baseline
+    and a cross-check of the library's fused kernels, not part of the library."""
+
+    IJ = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+    def __init__(self, phase, lam, mu, lam0, mu0, eps_bar6):
+        import numpy as np
+        import torch
+        self.t = torch
+        dev = phase.device
+        n3, n2, n1 = phase.shape
+        self.N = n1 * n2 * n3
+        lam_t = torch.tensor(np.asarray(lam, dtype=np.float32), device=dev)
+        mu_t = torch.tensor(np.asarray(mu, dtype=np.float32), device=dev)
+        ph = phase.long()
+        self.lam, self.mu = lam_t[ph], mu_t[ph]
+        kap = lam_t + 2.0 * mu_t / 3.0
+        k0 = lam0 + 2.0 * mu0 / 3.0
+        ak, am = (k0 / (kap + k0))[ph], (mu0 / (mu_t + mu0))[ph]
+        self.am2, self.av = 2.0 * am, 2.0 * (ak - am) / 3.0
+        self.lam0, self.mu0 = float(lam0), float(mu0)
+        self.eb = torch.tensor(eps_bar6, dtype=torch.float32, device=dev)
+        self.eps = self.eb.view(6, 1, 1, 1).expand(6, n3, n2, n1).contiguous()
+        q = lambda n: 2.0 * np.pi * np.fft.fftfreq(n)
+        q1 = 2.0 * np.pi * np.arange(n1 // 2 + 1) / n1
+        s1, s2, s3 = np.sin(q1 / 2), np.sin(q(n2) / 2), np.sin(q(n3) / 2)
+        c1, c2, c3 = np.cos(q1 / 2), np.cos(q(n2) / 2), np.cos(q(n3) / 2)
+        # rotated-grid direction k^R / (phase * i): 2 sin(q_i/2) prod_{m != i} cos(q_m/2)
+        k1 = 2 * s1[None, None, :] * c2[None, :, None] * c3[:, None, None]
+        k2 = 2 * c1[None, None, :] * s2[None, :, None] * c3[:, None, None]
+        k3 = 2 * c1[None, None, :] * c2[None, :, None] * s3[:, None, None]
+        kr = np.stack([k1, k2, k3])
+        kr[np.abs(kr) < 1e-12] = 0.0
+        self.kr = torch.tensor(kr, dtype=torch.float32, device=dev)
+        K2 = (self.kr ** 2).sum(0)
+        self.zero = K2 == 0
+        self.iK2 = torch.where(self.zero, torch.zeros_like(K2), 1.0 / torch.where(self.zero, torch.ones_like(K2), K2))
+        w = np.full(n1 // 2 + 1, 2.0)
+        w[0] = 1.0
+        if n1 % 2 == 0:
+            w[-1] = 1.0
+        self.w = torch.tensor(w, dtype=torch.float32, device=dev)
+
+    def stress(self, e):
+        tr = e[0] + e[1] + e[2]
+        s = 2.0 * self.mu * e
+        s[:3] += self.lam * tr
+        return s
+
+    def step(self):
+        """One iteration; returns eta of the current iterate (before the update)."""
+        t = self.t
+        e = self.eps
+        sig = self.stress(e)
+        tau = sig.clone()
+        tr = e[0] + e[1] + e[2]
+        tau -= 2.0 * self.mu0 * e
+        tau[:3] -= self.lam0 * tr
+        S = t.fft.rfftn(sig, dim=(1, 2, 3))
+        T = t.fft.rfftn(tau, dim=(1, 2, 3))
+        full = lambda X: [[X[[0, 5, 4][j] if i == 0 else ([5, 1, 3][j] if i == 1 else [4, 3, 2][j])]
+                           for j in range(3)] for i in range(3)]
+        Sm, Tm = full(S), full(T)
+        div = [sum(self.kr[i] * Sm[i][j] for i in range(3)) for j in range(3)]
+        num = sum((self.w * (d.real ** 2 + d.imag ** 2)).sum() for d in div)
+        ms = sig.mean(dim=(1, 2, 3))
+        den = float(t.sqrt((ms[:3] ** 2).sum() + 2.0 * (ms[3:] ** 2).sum())) * self.N
+        eta = float(t.sqrt(num.double())) / den if den > 0 else 0.0
+        V = [sum(self.kr[i] * Tm[i][j] for i in range(3)) for j in range(3)]
+        Ssum = sum(self.kr[j] * V[j] for j in range(3))
+        c0 = (self.lam0 + self.mu0) / (self.lam0 + 2.0 * self.mu0)
+        f = -self.iK2 / self.mu0
+        E = t.empty_like(T)
+        for c, (i, j) in enumerate(self.IJ):
+            E[c] = f * (0.5 * (self.kr[i] * V[j] + self.kr[j] * V[i]) - c0 * self.kr[i] * self.kr[j] * Ssum * self.iK2)
+        E[:, self.zero] = 0
+        E[:, 0, 0, 0] = self.eb * self.N
+        en = t.fft.irfftn(E, s=e.shape[1:], dim=(1, 2, 3))
+        d = en - e
+        trd = d[0] + d[1] + d[2]
+        upd = self.am2 * d
+        upd[:3] += self.av * trd
+        self.eps = e + upd
+        return eta
+
+
+def cufft_baseline(ph, lam, mu, iters, solver, warm=1):
+    """Voxel-iterations / s of the unfused cuFFT pipeline (device-resident inputs), and
+    its eta history over the first iterations against the library's FP32 path."""
+    import numpy as np
+    import torch
+    from paper_1412_8398_gb300 import fftls
+    l0, m0 = fftls.reference_medium(lam, mu, 3, "AS")
+    dph = torch.from_numpy(ph).cuda()
+    b = CufftBaseline(dph, lam, mu, l0, m0, [1.0, 0, 0, 0, 0, 0])
+    etas = [b.step() for _ in range(3)]
+    ours = solver.solve(dph, lam, mu, mandel_load(0), green="R", scheme="AS", tol=0.0, max_iter=3, precision="fp32",
+                        want_strain=False, want_stress=False, device_outputs=True, raise_on_error=False)
+    check = float(np.max(np.abs(np.array(etas) - ours.eta_history[:3]) / np.abs(ours.eta_history[:3])))
+    for _ in range(warm):
+        b.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        b.step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    out = {"value": ph.size / (ms / 1e3), "unit": UNIT, "ms_per_iteration": ms, "iterations_timed": iters,
+           "what": "torch elementwise + cuFFT rfftn/irfftn (sigma and tau), FP32, AS / G^R, same workload",
+           "crosscheck_eta_rel_diff_first_3_iterations": check}
+    del b
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -522,6 +644,11 @@ def main():
                                 "gbs": (kernel_bytes(k, n) / (v[0] / v[1] / 1e3) / 1e9) if kernel_bytes(k, n) else None}
                             for k, v in sorted(prof.items())}}
 
+    # the unfused library pipeline (cuFFT + elementwise kernels) on the same workload
+    cufft = None
+    if not args.no_cufft and rank == 0:
+        cufft = cufft_baseline(ph, lam, mu, 3, solver)
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -582,6 +709,7 @@ def main():
             "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "cufft_baseline": cufft,
         }
         print(json.dumps(out))
     solver.close()

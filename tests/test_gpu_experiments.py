@@ -1,0 +1,73 @@
+"""GPU: the experiment drivers reproduce the qualitative findings of the paper's Sec. 6.
+
+* N(E0) has an interior minimum for AS with G^R, and the golden-section search
+  finds an E0 at least as good as the best of a coarse sweep (Sec. 6.2);
+* iterations grow with the contrast, much faster for the direct than for the
+  accelerated scheme (Sec. 6.3: ~chi against ~sqrt(chi));
+* the apparent modulus converges within the Voigt and Reuss bounds, and the
+  full C~ from six loads is symmetric (eq. a2).
+"""
+import numpy as np
+import pytest
+
+from paper_1412_8398_gb300 import microstructure as MS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_8398_gb300 import build, experiments, fftls
+    build.build()
+    s = fftls.Solver(0)
+    yield s, experiments
+    s.close()
+
+
+def _boolean():
+    ph, _ = MS.boolean_spheres((32, 32, 32), 2.5, 0.17, seed=7)
+    return ph
+
+
+def test_reference_sweep_has_interior_minimum(env):
+    s, X = env
+    ph = _boolean()
+    lam, mu = MS.young_poisson_phases([(1.0, 0.25), (1e-3, 0.25)])   # soft inclusions, chi = 1e-3
+    E0s = [0.01, 0.03, 0.1, 0.3, 1.0]
+    sweep = X.iterations_vs_reference(s, ph, lam, mu, E0s, nu0=0.25, green="R", scheme="AS", tol=1e-6)
+    its = [n if ok else 10 ** 9 for _, n, ok in sweep]
+    k = int(np.argmin(its))
+    assert 0 < k < len(E0s) - 1, sweep
+    E0, n_best, seen = X.optimal_reference(s, ph, lam, mu, 0.01, 1.0, green="R", scheme="AS", tol=1e-6,
+                                           evaluations=10)
+    assert n_best <= min(its)
+    assert 0.01 <= E0 <= 1.0
+
+
+def test_iterations_grow_slower_with_acceleration(env):
+    s, X = env
+    ph = _boolean()
+    as_ = X.iterations_vs_contrast(s, ph, [10.0, 100.0], green="R", scheme="AS", tol=1e-6)
+    ds_ = X.iterations_vs_contrast(s, ph, [10.0, 100.0], green="R", scheme="DS", tol=1e-6)
+    assert all(ok for _, _, ok in as_ + ds_)
+    ratio_as = as_[1][1] / as_[0][1]
+    ratio_ds = ds_[1][1] / ds_[0][1]
+    assert as_[1][1] > as_[0][1] and ds_[1][1] > ds_[0][1]
+    assert ratio_ds > 2.0 * ratio_as
+
+
+def test_modulus_history_and_full_stiffness(env):
+    s, X = env
+    ph = _boolean()
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (50.0, 0.3)])
+    h = X.modulus_history(s, ph, lam, mu, iterations=60)
+    f = float(np.mean(ph == 1))
+    M = lam + 2 * mu
+    voigt = (1 - f) * M[0] + f * M[1]
+    assert h[-1] < voigt and abs(h[-1] - h[-2]) < 1e-4 * abs(h[-1])
+    C, its = X.effective_stiffness(s, ph, lam, mu, tol=1e-8)
+    assert np.allclose(C, C.T, rtol=1e-6, atol=1e-8 * np.abs(C).max())
+    assert abs(C[0, 0] - h[-1]) < 1e-4 * C[0, 0]
