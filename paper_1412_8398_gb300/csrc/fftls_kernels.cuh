@@ -111,7 +111,7 @@ struct IterArgs {
   double* eta_hist;    // [max_it]
   double* ms_hist;     // [max_it][nc]
   float* rfield;       // n_c x N defect r (written by kUpdResidual, read by corrections)
-  float2* d64;         // [modes][3]: k*.sigma_hat of the FP64 iterate (phase-free form), or with
+  float2* d64;         // [modes][3] by frequency index: k*.sigma_hat of the FP64 iterate (phase-free form), or with
                        // eta_real [3][N] floats: its real-space divergence
   // launch shapes (host-computed)
   int x1_lines, x1_blocks;  // forward x1 pass: lines per batch, blocks (grid-stride over batches)

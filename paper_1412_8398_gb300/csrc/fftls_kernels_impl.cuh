@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(512) k_mid_y(IterArgs<T> a, int inv) {
 // The divergence is accumulated in a phase-free form: V = x_hat . kr for MS/C/R
 // and b = conj(k) . x_hat for W; d64 holds that vector for the FP64 iterate.
 template <typename T, int DIM>
-__device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y, int z, long long mstore,
+__device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y, int z, long long mfreq,
                                              typename Cplx<T>::type* X, bool do_green, bool do_eta,
                                              T& eta_acc) {
   typedef typename Cplx<T>::type T2;
@@ -513,7 +513,7 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
           float2 f;
           f.x = j < DIM ? (float)V[j].x : 0.f;
           f.y = j < DIM ? (float)V[j].y : 0.f;
-          a.d64[mstore * 3 + j] = f;
+          a.d64[mfreq * 3 + j] = f;
         }
       }
       T s = (T)0;
@@ -522,7 +522,7 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
         // (the conjugate-partner term of operator G below is left out here)
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
-          const float2 f = a.d64[mstore * 3 + j];
+          const float2 f = a.d64[mfreq * 3 + j];
           const T vx = V[j].x + (T)f.x, vy = V[j].y + (T)f.y;
           s += vx * vx + vy * vy;
         }
@@ -620,7 +620,7 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
           float2 f;
           f.x = j < DIM ? (float)b[j].x : 0.f;
           f.y = j < DIM ? (float)b[j].y : 0.f;
-          a.d64[mstore * 3 + j] = f;
+          a.d64[mfreq * 3 + j] = f;
         }
       }
       T s = (T)0;
@@ -628,7 +628,7 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
       for (int j = 0; j < DIM; ++j) {
         T bx = b[j].x, by = b[j].y;
         if (a.corr) {
-          const float2 f = a.d64[mstore * 3 + j];
+          const float2 f = a.d64[mfreq * 3 + j];
           bx += (T)f.x;
           by += (T)f.y;
         }
@@ -710,8 +710,10 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
     T2 X[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) X[c] = mp[c];
-    const long long mstore = ((long long)pz * g.n2 + py) * g.H + x0 + xc;
-    fourier_mode<T, DIM>(a, x0 + xc, ym, zm, mstore, X, do_green, do_eta, eta_acc);
+    // the FP64 divergence kept for correction phases is indexed by frequency, not by
+    // storage position
+    const long long mfreq = ((long long)zm * g.n2 + ym) * g.H + x0 + xc;
+    fourier_mode<T, DIM>(a, x0 + xc, ym, zm, mfreq, X, do_green, do_eta, eta_acc);
     if (do_green)
 #pragma unroll
       for (int c = 0; c < NC; ++c) mp[c] = X[c];

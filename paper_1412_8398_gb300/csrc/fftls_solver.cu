@@ -142,6 +142,7 @@ void axis_tables(int L, double* tw, double* kt) {
 // reductions changes.
 struct TilePlan {
   int x1_lines, x5_lines, y_w, z_w, e_planes, x1_vb;
+  int y_thr, z_thr;  // threads per block of the strided passes (0: by tile size)
   int tuned;  // 1: chosen by timing candidates on the device
 };
 
@@ -375,6 +376,7 @@ TilePlan default_plan(const Setup& S, size_t cb, bool real_eta) {
   P.x1_lines = (int)std::max<size_t>(1, (real_eta ? 32 * 1024 : 64 * 1024) / G.line1);
   P.x5_lines = (int)std::max<size_t>(1, (32 * 1024) / G.line5);
   P.x1_vb = cb == 16 ? 1 : 4;  // double precision loads one voxel at a time
+  P.y_thr = P.z_thr = 0;
   auto pick_w = [&](int L) {
     int w = 16;
     while (w > 1 && strided_smem(L, w, S.nc, cb) > std::min<size_t>(G.lim, 100 * 1024)) w /= 2;
@@ -413,8 +415,8 @@ bool apply_plan(const Setup& S, IterArgs<T>& a, bool real_eta, const TilePlan& P
   if (a.y_smem > G.lim || a.z_smem > G.lim) return false;
   a.y_w = P.y_w;
   a.z_w = P.z_w;
-  a.y_threads = (long long)g.n2 * a.y_w * S.nc >= 4096 ? 512 : 256;
-  a.z_threads = (long long)g.n3 * a.z_w * S.nc >= 4096 ? 512 : 256;
+  a.y_threads = P.y_thr ? P.y_thr : ((long long)g.n2 * a.y_w * S.nc >= 4096 ? 512 : 256);
+  a.z_threads = P.z_thr ? P.z_thr : ((long long)g.n3 * a.z_w * S.nc >= 4096 ? 512 : 256);
   a.e_planes = a.e_blocks = 0;
   a.e_smem = 0;
   if (real_eta) {
@@ -662,6 +664,10 @@ fftls_status tune_plan(fftls_ctx* c, const Setup& S, IterArgs<T>& a, bool real_e
   if (S.g.n2 > 1)
     search(&TilePlan::y_w, widths, [](const IterArgs<T>& x, cudaStream_t st) { return launch_mid_y<T>(x, false, st); });
   search(&TilePlan::z_w, widths, [](const IterArgs<T>& x, cudaStream_t st) { return launch_fourier_z<T>(x, st); });
+  if (S.g.n2 > 1)
+    search(&TilePlan::y_thr, {256, 512},
+           [](const IterArgs<T>& x, cudaStream_t st) { return launch_mid_y<T>(x, false, st); });
+  search(&TilePlan::z_thr, {256, 512}, [](const IterArgs<T>& x, cudaStream_t st) { return launch_fourier_z<T>(x, st); });
   a.eps = (T*)c->specB.p;  // scratch target of the inverse pass's update
   search(&TilePlan::x5_lines, {1, 2, 4, 8}, [](const IterArgs<T>& x, cudaStream_t st) { return launch_inv_x<T>(x, st); });
   a.eps = keep.eps;
