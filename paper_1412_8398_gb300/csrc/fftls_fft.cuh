@@ -263,10 +263,22 @@ __device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
   constexpr int NB = L / R;
   constexpr int TSTR = L / M;
   constexpr int BS = (PAD ? padded_rows(L) : L) * C;
-  const int total = nblk * NB * NCOLS;
+  const int nbf = nblk * NB;
+  const int total = nbf * NCOLS;
+  // thread order: consecutive threads take consecutive columns, except in the last
+  // stage of the padded x1 tiles (few columns, rows 8 apart), where consecutive
+  // butterflies of one column keep a half-warp on distinct shared-memory banks
+  constexpr bool BF_ORDER = PAD && MR == 1;
+  const FastDiv fb = make_fastdiv(nbf);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int rest = idx / NCOLS;
-    const int c = idx - rest * NCOLS;
+    int c, rest;
+    if (BF_ORDER) {
+      c = fdiv(idx, fb);
+      rest = idx - c * nbf;
+    } else {
+      rest = idx / NCOLS;
+      c = idx - rest * NCOLS;
+    }
     const int bf = rest & (NB - 1);
     const int blk = rest / NB;
     const int b = bf / MR, j = bf & (MR - 1);
