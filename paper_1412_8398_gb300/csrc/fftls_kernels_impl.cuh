@@ -361,13 +361,33 @@ __global__ void __launch_bounds__(kEThreads) k_eta_stencil(IterArgs<T> a) {
     const int z = wrap_index(zz, n3);
     T* S = sS + ((zz - zstart) & 1) * 6 * PL;
     const long long plane = (long long)z * n2;
-    for (int e = threadIdx.x; e < HR * HC; e += kEThreads) {
-      const int r = e / HC, ci = e - r * HC;
-      const int y = wrap_index(y0 - 1 + r, n2), x = wrap_index(x0 - 1 + ci, n1);
-      T s[6];
-      sigma_of(eps, phase, coef, N, (plane + y) * n1 + x, s);
+    // sigma on the tile and its halo; a thread's (at most kEFill) elements issue
+    // all their loads before any is used
+    constexpr int kEFill = (HR * HC + kEThreads - 1) / kEThreads;
+    T ev[kEFill][6];
+    int pv[kEFill];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) S[c * PL + r * SX + ci] = s[c];
+    for (int u = 0; u < kEFill; ++u) {
+      const int e = threadIdx.x + u * kEThreads;
+      if (e < HR * HC) {
+        const int r = e / HC, ci = e - r * HC;
+        const int y = wrap_index(y0 - 1 + r, n2), x = wrap_index(x0 - 1 + ci, n1);
+        const long long v = (plane + y) * n1 + x;
+        pv[u] = phase[v];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) ev[u][c] = eps[(long long)c * N + v];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kEFill; ++u) {
+      const int e = threadIdx.x + u * kEThreads;
+      if (e < HR * HC) {
+        const int r = e / HC, ci = e - r * HC;
+        const T* cf = coef + pv[u] * kCoef;
+        const T tr = ev[u][0] + ev[u][1] + ev[u][2];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) S[c * PL + r * SX + ci] = cf[1] * ev[u][c] + (c < 3 ? cf[0] * tr : (T)0);
+      }
     }
     __syncthreads();
     const bool valid = CEN ? (zz - 1 >= z0) : (zz >= z0);
