@@ -99,6 +99,9 @@ typedef struct {
                                context, time candidate tile schedules of every kernel on the device and keep
                                the fastest (see fftls_tile_plans); 0: built-in schedule.  The schedule changes
                                no per-line or per-mode arithmetic, only the grouping of partial sums. */
+  int eta_only;             /* 0 (default): the accelerated scheme's eta test also requires
+                               |<eps> - eps_bar|_F <= tol |eps_bar|_F (its iterates need not have mean
+                               eps_bar); 1: eta <= tol alone, the paper's criterion (eq. criterion) */
 } fftls_options;
 
 typedef struct {

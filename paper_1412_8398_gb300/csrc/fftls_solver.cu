@@ -974,7 +974,7 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
   memset(&ctl, 0, sizeof(ctl));
   ctl.state = kRunning;
   ctl.max_it = o->max_iter;
-  ctl.mean_guard = direct ? 0 : 1;
+  ctl.mean_guard = (direct || o->eta_only) ? 0 : 1;
   ctl.best = INFINITY;
   ctl.stop_rule = o->stop;
   ctl.tol = o->tol;
@@ -1373,7 +1373,7 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   ctl.max_it = o->max_iter;
   ctl.stop_rule = o->stop;
   ctl.tol = o->tol;
-  ctl.mean_guard = direct ? 0 : 1;
+  ctl.mean_guard = (direct || o->eta_only) ? 0 : 1;
   ctl.best = INFINITY;
   NA_TRY(cudaMemcpyAsync(a.ctrl, &ctl, sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
   auto iteration = [&](bool dual, int update) -> cudaError_t {

@@ -16,6 +16,17 @@ periodic spheres) built by ``microstructure``.
 * ``modulus_history``: the apparent modulus <sigma_11> / eps_bar_11 after each
   iteration (Sec. 6.4, convergence of C~_1111 with the iterations).
 * ``effective_stiffness``: the full C~ from the six unit loads (eq. a2).
+* ``four_cell``: the 2D quasi-rigid square inclusion of Sec. 5.1 (chi = 1e3, eq. load2d),
+  sigma_12 around the inclusion corners.
+* ``periodic_sphere_modulus``: C~_1111 of one periodic spherical pore-like inclusion
+  (f = 20 %, chi = 1e-4) of Sec. 5.3 at grid length L.
+* ``boolean_reference_study``: N(E0) and its minimum on the 64^3 Boolean model of Sec. 6
+  (743 spheres of diameter 5, f = 17 %).
+
+The paper's phases (Sec. 2): nu = 0.25 in both phases; matrix kappa = 1, mu = 0.6
+(lambda = 0.4 in 2D, 0.6 in 3D); the inclusion's moduli are chi times the matrix's.
+``python -m paper_1412_8398_gb300.experiments`` runs the three studies and prints one JSON
+summary per study.
 """
 from __future__ import annotations
 
@@ -31,8 +42,9 @@ def lame(E: float, nu: float):
 
 
 def iterations_vs_reference(solver, phase, lam, mu, E0_values, nu0=0.25, green="R", scheme="AS", tol=1e-8,
-                            max_iter=5000, precision="fp64", eps_bar=None):
-    """[(E0, iterations, converged)] for each reference Young's modulus E0 (nu0 fixed)."""
+                            max_iter=5000, precision="fp64", eps_bar=None, eta_only=False):
+    """[(E0, iterations, converged)] for each reference Young's modulus E0 (nu0 fixed).
+    eta_only: stop on eta alone, the paper's criterion (see fftls_options.eta_only)."""
     d = phase.ndim
     eb = np.diag([1.0] + [0.0] * (d - 1)) if eps_bar is None else eps_bar
     out = []
@@ -40,20 +52,20 @@ def iterations_vs_reference(solver, phase, lam, mu, E0_values, nu0=0.25, green="
         l0, m0 = lame(float(E0), nu0)
         r = solver.solve(phase, lam, mu, eb, green, scheme, lam0=l0, mu0=m0, tol=tol, max_iter=max_iter,
                          precision=precision, want_strain=False, want_stress=False, history=False,
-                         raise_on_error=False)
+                         raise_on_error=False, eta_only=eta_only)
         out.append((float(E0), int(r.iterations), bool(r.converged)))
     return out
 
 
 def optimal_reference(solver, phase, lam, mu, E0_lo, E0_hi, nu0=0.25, green="R", scheme="AS", tol=1e-8,
-                      max_iter=5000, precision="fp64", evaluations=12):
+                      max_iter=5000, precision="fp64", evaluations=12, eta_only=False):
     """(E0*, N(E0*), evaluations) by golden-section search on log E0 in [E0_lo, E0_hi]."""
     cache = {}
 
     def N(logE):
         if logE not in cache:
             (_, its, conv), = iterations_vs_reference(solver, phase, lam, mu, [math.exp(logE)], nu0, green, scheme,
-                                                      tol, max_iter, precision)
+                                                      tol, max_iter, precision, eta_only=eta_only)
             cache[logE] = its if conv else max_iter + 1
         return cache[logE]
 
@@ -98,3 +110,85 @@ def effective_stiffness(solver, phase, lam, mu, green="R", scheme="AS", tol=1e-8
     """Mandel C~ from the six (2D: three) unit loads."""
     C, its, _ = solver.effective_stiffness(phase, lam, mu, green=green, scheme=scheme, tol=tol, precision=precision)
     return C, its
+
+
+def paper_phases(chi: float, dim: int):
+    """(lambda, mu) of the matrix and of the inclusions in the paper's convention (Sec. 2)."""
+    lam1 = 0.4 if dim == 2 else 0.6
+    return np.array([lam1, chi * lam1]), np.array([0.6, chi * 0.6])
+
+
+def four_cell(solver, L=512, green="R", chi=1e3, tol=2e-13, max_iter=100000, window=0.04, threshold=3.5):
+    """Sec. 5.1: centred square inclusion of side L/2 (the simplified four-cell), eps_bar_12 =
+    eps_bar_21 = 1/2 (eq. load2d), AS, stop when no strain or stress value moves by more than tol
+    between iterations.  Returns sigma_12 statistics in the squares of half-width `window` (in
+    cell lengths) around the four inclusion corners."""
+    ph = MS.square_inclusion(L, 2)
+    lam, mu = paper_phases(chi, 2)
+    eb = np.array([[0.0, 0.5], [0.5, 0.0]])
+    r = solver.solve(ph, lam, mu, eb, green, "AS", tol=tol, max_iter=max_iter, precision="fp64", stop="maxdelta",
+                     want_strain=False, history=False, raise_on_error=False)
+    s12 = np.asarray(r.stress[2])
+    h = int(round(window * L))
+    c_lo, c_hi = L // 4, L // 4 + L // 2
+    stats = []
+    for cy in (c_lo, c_hi):
+        for cx in (c_lo, c_hi):
+            w = s12[cy - h:cy + h, cx - h:cx + h]
+            stats.append({"corner": [cx, cy], "max": float(w.max()), "min": float(w.min()),
+                          "frac_above": float(np.mean(w > threshold))})
+    return {"L": L, "green": green, "iterations": int(r.iterations), "converged": bool(r.converged),
+            "max_sigma12_near_corners": max(q["max"] for q in stats),
+            "frac_above_threshold_near_corners": float(np.mean([q["frac_above"] for q in stats])),
+            "frac_above_threshold_whole_cell": float(np.mean(s12 > threshold)),
+            "mean_sigma12": float(s12.mean()), "corners": stats}
+
+
+def periodic_sphere_modulus(solver, L, green="R", f=0.2, chi=1e-4, tol=2e-10, max_iter=200000):
+    """Sec. 5.3: C~_1111 = <sigma_11> under eps_bar = e1 (x) e1 for one periodic sphere of volume
+    fraction f and contrast chi, AS, max-delta stop at tol (FP64)."""
+    ph = MS.periodic_sphere(L, f)
+    lam, mu = paper_phases(chi, 3)
+    r = solver.solve(ph, lam, mu, np.diag([1.0, 0.0, 0.0]), green, "AS", tol=tol, max_iter=max_iter,
+                     precision="fp64", stop="maxdelta", want_strain=False, want_stress=False, history=False,
+                     raise_on_error=False)
+    return {"L": L, "green": green, "C1111": float(r.mean_stress[0]), "iterations": int(r.iterations),
+            "converged": bool(r.converged), "fraction": float(ph.mean())}
+
+
+def boolean_reference_study(solver, chi=1e-5, green="R", scheme="AS", tol=1e-8, seed=39, eta_only=True,
+                            E0_grid=(0.02, 0.04, 0.06, 0.09, 0.13, 0.2, 0.3, 0.5)):
+    """Sec. 6: a 64^3 Boolean model of spheres of diameter 5 (seed 39: 746 spheres, f = 16.9 %, an
+    instance like the paper's 743 spheres and 17 %), N(E0) on a grid and the golden-section optimum
+    (nu0 = 0.25), iterations to eta <= tol (eta_only: the paper's criterion)."""
+    ph, info = MS.boolean_spheres((64, 64, 64), 2.5, 0.17, seed=seed)
+    lam, mu = paper_phases(chi, 3)
+    sweep = iterations_vs_reference(solver, ph, lam, mu, E0_grid, 0.25, green, scheme, tol, eta_only=eta_only)
+    E0, N, seen = optimal_reference(solver, ph, lam, mu, E0_grid[0], E0_grid[-1], 0.25, green, scheme, tol,
+                                    evaluations=14, eta_only=eta_only)
+    return {"chi": chi, "green": green, "scheme": scheme, "eta_only": eta_only, "spheres": int(info["n_centers"]),
+            "fraction": float(info["fraction"]), "sweep": sweep, "optimal_E0": E0, "optimal_iterations": N}
+
+
+def main():
+    import json
+
+    from . import fftls
+    s = fftls.Solver(0)
+    try:
+        for g in ("MS", "C", "W", "R"):
+            print(json.dumps({"study": "four_cell", **{k: v for k, v in four_cell(s, 512, g).items()
+                                                          if k != "corners"}}), flush=True)
+        for L in (64, 128, 256):
+            print(json.dumps({"study": "periodic_sphere", **periodic_sphere_modulus(s, L)}), flush=True)
+        for g in ("R", "W", "C"):
+            for eta_only in (True, False):
+                print(json.dumps({"study": "boolean_reference",
+                                  **boolean_reference_study(s, green=g, eta_only=eta_only)}), flush=True)
+    finally:
+        s.close()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -70,6 +70,7 @@ class _Options(ctypes.Structure):
         ("use_graphs", ctypes.c_int),
         ("profile", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("eta_only", ctypes.c_int),
     ]
 
 
@@ -250,7 +251,7 @@ class Solver:
         return p, keep, on_dev
 
     def _options(self, tol, max_iter, precision, stop, refine_switch, eps_init, fields_on_device, stream,
-                 use_graphs, profile, autotune=True):
+                 use_graphs, profile, autotune=True, eta_only=False):
         o = _Options()
         self.lib.fftls_default_options(ctypes.byref(o))
         o.tol = float(tol)
@@ -262,6 +263,7 @@ class Solver:
         o.use_graphs = 1 if use_graphs else 0
         o.profile = 1 if profile else 0
         o.autotune = 1 if autotune else 0
+        o.eta_only = 1 if eta_only else 0
         keep = None
         if eps_init is not None:
             if _is_torch(eps_init):
@@ -280,13 +282,13 @@ class Solver:
     def solve(self, phase, lam, mu, eps_bar, green="R", scheme="AS", lam0=None, mu0=None, tol=1e-8,
               max_iter=1000, precision="fp64", stop="eta", refine_switch=0.0, eps_init=None,
               want_strain=True, want_stress=True, history=True, device_outputs=None, stream=None,
-              use_graphs=True, profile=False, autotune=True, raise_on_error=True) -> SolveResult:
+              use_graphs=True, profile=False, autotune=True, eta_only=False, raise_on_error=True) -> SolveResult:
         """Solve one load case; see fftls_solve in include/fftls.h."""
         p, keep_p, on_dev = self._problem(phase, lam, mu, eps_bar, green, scheme, lam0, mu0)
         if device_outputs is None:
             device_outputs = on_dev
         o, keep_o = self._options(tol, max_iter, precision, stop, refine_switch, eps_init, device_outputs,
-                                  stream, use_graphs, profile, autotune)
+                                  stream, use_graphs, profile, autotune, eta_only)
         r, out = self._outputs(p, phase.shape, want_strain, want_stress, history, max_iter, device_outputs)
         st = self.lib.fftls_solve(self.handle, ctypes.byref(p), ctypes.byref(o), ctypes.byref(r))
         msg = self.last_error()
