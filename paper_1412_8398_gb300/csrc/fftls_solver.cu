@@ -1068,7 +1068,7 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
         Ctrl cc = ctl;
         cc.state = kRunning;
         cc.stop_rule = 0;
-        cc.tol = 0.25 * o->tol;
+        cc.tol = 0.5 * o->tol;  // the estimate's FP32 error stays well below tol / 2 (FP64 certifies)
         cc.switch_mode = 1;
         cc.stall_window = 32;
         cc.stall = 0;
