@@ -61,6 +61,9 @@ def parse():
                     help="instead of the 512^3 workload, train the warm-start network on COUNT solver-generated "
                          "64^3 samples and compare warm and plain starts on 256^3 samples")
     ap.add_argument("--warm-epochs", type=int, default=4)
+    ap.add_argument("--ncu-region", action="store_true",
+                    help="for ncu --profile-from-start off: tune and warm up on the workload, then bracket two "
+                         "FP32 iterations launched without graphs with the profiler start / stop calls")
     ap.add_argument("--warm-apply", type=int, default=4, help="256^3 samples of the warm-start comparison")
     return ap.parse_args()
 
@@ -565,6 +568,28 @@ def run_warmstart(args, rank, local, world):
     solver.close()
 
 
+def run_ncu_region(args, local):
+    """A profiler region of two steady-state FP32 iterations of the workload (size --n)."""
+    import torch
+    from paper_1412_8398_gb300 import build, fftls
+
+    build.build()
+    torch.cuda.set_device(local)
+    ph, lam, mu, info = workload(args.n)
+    dph = torch.from_numpy(ph).cuda()
+    s = fftls.Solver(local)
+    kw = dict(green="R", scheme="AS", tol=1e-6, precision="fp32", want_strain=False, want_stress=False,
+              history=False, device_outputs=True, raise_on_error=False)
+    s.solve(dph, lam, mu, mandel_load(0), max_iter=3, **kw)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    s.solve(dph, lam, mu, mandel_load(0), max_iter=2, use_graphs=False, **kw)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"ncu_region": "2 FP32 iterations", "n": args.n, "tile_plans": s.tile_plans()}))
+    s.close()
+
+
 def main():
     args = parse()
     rank, local, world = dist_setup()
@@ -576,6 +601,9 @@ def main():
         return
     if args.warmstart > 0:
         run_warmstart(args, rank, local, world)
+        return
+    if args.ncu_region:
+        run_ncu_region(args, local)
         return
     import numpy as np
     import torch
