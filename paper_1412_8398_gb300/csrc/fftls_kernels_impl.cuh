@@ -119,6 +119,23 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// L2 prefetch of the fields of voxels [v0, v0 + nvox) (n_c components of eps and the
+// phase ids): one prefetch per 128-byte line, spread over the block's threads, so that
+// loads issued later in the kernel hit L2 instead of waiting on DRAM.
+template <typename T>
+__device__ __forceinline__ void prefetch_voxels(const T* eps, const uint8_t* phase, long long N, int nc, long long v0,
+                                                int nvox) {
+  constexpr int PER = 128 / sizeof(T);
+  const int lines = (nvox + PER - 1) / PER + 1;  // +1: the run need not start on a line
+  for (int t = threadIdx.x; t < nc * lines; t += blockDim.x) {
+    const int c = t / lines, l = t - c * lines;
+    const long long v = min(v0 + (long long)l * PER, v0 + nvox - 1);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(eps + (long long)c * N + v));
+  }
+  for (int l = threadIdx.x; l <= nvox / 128; l += blockDim.x)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(phase + v0 + min((long long)l * 128, (long long)nvox - 1)));
+}
+
 // Copy `rows` rows of `cols` complex values between a tile (row stride C) and
 // global memory (row stride gstride, in complex values).  Rows of whole 16-byte
 // units with 16-byte aligned starts go through cp.async (loads) and 16-byte
@@ -259,6 +276,10 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
       if (lane == 0) wacc[warp][c] += (double)x;
     }
     __syncthreads();
+    {  // the next batch's eps and phase ids, while this batch is transformed
+      const long long ln = l0 + (long long)gridDim.x * G;
+      if (ln < nlines) prefetch_voxels<T>(a.eps, a.phase, g.N, NC, ln * L1, (int)min((long long)G, nlines - ln) * L1);
+    }
     tile_fft_ct<CP, NP, true>(tile, nl, BS, a.pl[0], tws, false);
     for (int idx = threadIdx.x; idx < nl * H * NP; idx += blockDim.x) {
       const int rest = fdiv(idx, fNP);
@@ -838,6 +859,8 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
   const FastDiv fL = make_fastdiv(L1), fH = make_fastdiv(H);
   for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
     const int nl = (int)min((long long)G, nlines - l0);
+    // eps and the phase ids are read after the transform: bring them towards L2 now
+    if (a.update != kUpdDirectTau) prefetch_voxels<T>(a.eps, a.phase, g.N, NC, l0 * L1, nl * L1);
     for (int idx = threadIdx.x; idx < nl * H * NPI; idx += blockDim.x) {
       const int p = idx % NPI;
       const int rest = idx / NPI;
@@ -860,6 +883,16 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
       }
     }
     __syncthreads();
+    {  // the next batch's half spectrum (its lines are consecutive, so one contiguous run)
+      const long long ln = l0 + (long long)gridDim.x * G;
+      if (ln < nlines) {
+        const int nn = (int)min((long long)G, nlines - ln);
+        const T2* base = a.specA + ln * (long long)H * NC;
+        const int bytes = nn * H * NC * (int)sizeof(T2);
+        for (int off = threadIdx.x * 128; off < bytes; off += blockDim.x * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(base) + off));
+      }
+    }
     tile_fft_ct<CP, NPI, true>(tile, nl, BS, a.pl[0], tws, true);
     for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
       const int gl = fdiv(idx, fL), x = idx - gl * L1;
