@@ -205,3 +205,23 @@ def test_not_converged_and_diverged(solver):
     assert r.status == fftls.E_DIVERGED
     ref = O.solve(ph, lam, mu, load(3), O.ROTATED, O.DIRECT, lam0=0.05, mu0=0.05, tol=1e-10, max_iter=500)
     assert not ref["converged"] and r.iterations == ref["iterations"]
+
+
+def test_eta_only_criterion_vs_mean_guard(solver):
+    """The accelerated scheme's iterates need not have mean eps_bar (reading 12): the default stop
+    also requires |<eps> - eps_bar| <= tol |eps_bar|; eta_only (the paper's criterion) stops on eta
+    alone, never later."""
+    layers = np.array([0, 0, 0, 1, 1, 0, 1, 1, 1, 0], dtype=np.uint8)     # odd layer widths
+    ph = MS.laminate((layers.size, 4), layers)
+    lam, mu = MS.binary_moduli(25.0, 2)
+    eb = np.array([[0.7, 0.2], [0.2, -0.3]])
+    tol = 1e-12
+    for green in ("W", "R"):
+        g = solver.solve(ph, lam, mu, eb, green, "AS", tol=tol, max_iter=2000)
+        e = solver.solve(ph, lam, mu, eb, green, "AS", tol=tol, max_iter=2000, eta_only=True)
+        assert g.converged and e.converged
+        assert e.iterations <= g.iterations
+        ebv = np.array([0.7, -0.3, 0.2])
+        w = np.array([1.0, 1.0, 2.0])
+        err = np.sqrt(np.sum(w * (g.mean_strain - ebv) ** 2) / np.sum(w * ebv ** 2))
+        assert err <= tol * 1.0001
