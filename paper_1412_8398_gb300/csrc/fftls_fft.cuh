@@ -181,6 +181,31 @@ __host__ __device__ constexpr int p2_radix(int L, int s) {
 }
 __host__ __device__ constexpr int p2_msize(int L, int s) { return s == 0 ? L : p2_msize(L, s - 1) / p2_radix(L, s - 1); }
 
+// Lengths whose transforms run the compile-time stages (tile_fft_ct).
+__host__ __device__ constexpr bool ct_length(int L) { return L == 64 || L == 128 || L == 256 || L == 512; }
+// Twiddle table of a compile-time length, laid out by stage (read by the
+// padded x1 tiles): stage s with MR = M / R > 1 (M = msize, R = radix) holds MR
+// rows of R complex values, row j = {w^(j T), w^(2 j T), ..., w^((R-1) j T),
+// unused} with w = e^{-2 pi i / L} and T = L / M, so a butterfly reads its R - 1
+// twiddles as one contiguous 16-byte-aligned row.  stage_tw_offset(L, s) is the
+// first entry of stage s; the stages without twiddles (MR = 1) take no rows.
+__host__ __device__ constexpr int stage_tw_offset(int L, int s) {
+  return s == 0 ? 0 : stage_tw_offset(L, s - 1) + (p2_msize(L, s - 1) > p2_radix(L, s - 1) ? p2_msize(L, s - 1) : 0);
+}
+// Complex entries of an axis's shared-memory twiddle table (even, so that the
+// tile after it starts 16-byte aligned): the stage layout for the compile-time
+// lengths when staged, else the plain table tw[t] = w^t, t < L.  Written out as
+// constants (checked below) so that a kernel pays no run-time recursion for it.
+__host__ __device__ constexpr int tw_count(int L, bool staged) {
+  return !staged ? ((L + 1) & ~1)
+       : L == 64 ? 64 : L == 128 ? 160 : L == 256 ? 320 : L == 512 ? 576 : ((L + 1) & ~1);
+}
+static_assert(tw_count(64, true) == stage_tw_offset(64, p2_nst(64)) &&
+                  tw_count(128, true) == stage_tw_offset(128, p2_nst(128)) &&
+                  tw_count(256, true) == stage_tw_offset(256, p2_nst(256)) &&
+                  tw_count(512, true) == stage_tw_offset(512, p2_nst(512)),
+              "stage twiddle counts");
+
 template <int R, typename T2>
 __device__ __forceinline__ void dft_fixed(T2* v, bool inv) {
   if (R == 2) dft2(v);
@@ -255,6 +280,39 @@ __device__ void tile_fft_p2(T2* buf, int nblk, int BS, int C, int ncols, const T
 // with rows e0 + r MR, the padded row index prow(e0 + r MR) equals
 // prow(e0) + r MR + floor(r MR / 8) for every stage of the plans above (MR is a
 // multiple of 8, or e0 mod 8 + r MR mod 8 < 8).
+// One twiddle row of the stage layout (R complex values, 16-byte aligned) into
+// registers: 16-byte loads for FP32, one load per value for FP64.
+template <int R>
+__device__ __forceinline__ void load_tw_row(const float2* p, float2* w) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < R / 2; ++i) {
+    const float4 t = q[i];
+    w[2 * i] = make_float2(t.x, t.y);
+    w[2 * i + 1] = make_float2(t.z, t.w);
+  }
+}
+template <int R>
+__device__ __forceinline__ void load_tw_row(const double2* p, double2* w) {
+#pragma unroll
+  for (int i = 0; i < R - 1; ++i) w[i] = p[i];
+}
+
+// The R - 1 twiddles w^(r j L / M), r = 1..R-1, of butterfly j of stage S:
+// one row of the stage layout (STAGED), else gathered from the plain table.
+template <int L, int S, bool STAGED, typename T2>
+__device__ __forceinline__ void stage_twiddles(const T2* tw, int j, T2* w) {
+  constexpr int R = p2_radix(L, S);
+  constexpr int TSTR = L / p2_msize(L, S);
+  if (STAGED) {
+    load_tw_row<R>(tw + stage_tw_offset(L, S) + j * R, w);
+  } else {
+    const T2* tj = tw + j * TSTR;
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r - 1] = tj[(r - 1) * j * TSTR];
+  }
+}
+
 template <int L, int S, int C, int NCOLS, bool PAD, bool INV, typename T2>
 __device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
   constexpr int R = p2_radix(L, S);
@@ -290,15 +348,17 @@ __device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
     if (!INV) {
       dft_fixed<R>(v, false);
       if (MR > 1 && j) {
-        const T2* tj = tw + j * TSTR;
+        T2 w[R];
+        stage_twiddles<L, S, PAD>(tw, j, w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tj[(r - 1) * j * TSTR]);
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r - 1]);
       }
     } else {
       if (MR > 1 && j) {
-        const T2* tj = tw + j * TSTR;
+        T2 w[R];
+        stage_twiddles<L, S, PAD>(tw, j, w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], tj[(r - 1) * j * TSTR]);
+        for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], w[r - 1]);
       }
       dft_fixed<R>(v, true);
     }
@@ -397,9 +457,12 @@ __device__ void tile_fft_rt(T2* buf, int nblk, int BS, int C, int ncols, const A
 // tile_fft with the tile geometry fixed at compile time (row stride C complex
 // values, first NCOLS columns transformed, padded rows when PAD): the lengths
 // 64..512 that are powers of two take the compile-time stages, any other
-// length the runtime paths.  BS is the block stride of the general path.
+// length the runtime paths.  BS is the block stride of the general path.  tw
+// holds tw_count(L, PAD) entries: the padded (x1) tiles of the compile-time
+// lengths read the stage layout, every other transform the plain table.
 template <int C, int NCOLS, bool PAD, typename T2>
 __device__ void tile_fft_ct(T2* buf, int nblk, int BS, const AxisPlan& p, const T2* tw, bool inv) {
+  static_assert(ct_length(64) && ct_length(128) && ct_length(256) && ct_length(512), "compile-time lengths");
   switch (p.L) {
     case 64: tile_fft_p2_ct<64, C, NCOLS, PAD>(buf, nblk, tw, inv); return;
     case 128: tile_fft_p2_ct<128, C, NCOLS, PAD>(buf, nblk, tw, inv); return;

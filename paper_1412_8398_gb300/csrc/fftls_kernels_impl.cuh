@@ -98,13 +98,15 @@ __device__ void block_max(double (&v)[W]) {
   __syncthreads();
 }
 
-// Dynamic shared memory: twiddles of the transformed axis, then the tile.
+// Dynamic shared memory: twiddles of the transformed axis (tw_count(L, staged)
+// entries, see tile_fft_ct), then the tile.
 template <typename T2>
-__device__ __forceinline__ T2* load_twiddles(const T2* __restrict__ tw, int L, T2** tile) {
+__device__ __forceinline__ T2* load_twiddles(const T2* __restrict__ tw, int L, bool staged, T2** tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* tws = reinterpret_cast<T2*>(smem_raw);
-  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = tw[t];
-  *tile = tws + ((L + 1) & ~1);
+  const int n = tw_count(L, staged);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) tws[t] = tw[t];
+  *tile = tws + n;
   __syncthreads();
   return tws;
 }
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
   const Geom g = a.g;
   const int L1 = g.n1, H = g.H;
   T2* tile;
-  const T2* tws = load_twiddles(a.tw[0], L1, &tile);
+  const T2* tws = load_twiddles(a.tw[0], L1, true, &tile);
   constexpr int nout = DUAL ? 2 * NC : NC;
   constexpr int NP = (nout + 1) / 2;
   constexpr int CP = odd_stride(NP);
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(512) k_mid_y(IterArgs<T> a, int inv) {
   const Geom g = a.g;
   const int n2 = g.n2;
   T2* tile;
-  const T2* tws = load_twiddles(a.tw[1], n2, &tile);
+  const T2* tws = load_twiddles(a.tw[1], n2, false, &tile);
   const int x0 = blockIdx.x * W;
   const int nx = min(W, g.H - x0);
   constexpr int C = W * NC;
@@ -727,7 +729,7 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   const Geom g = a.g;
   const int n3 = g.n3;
   T2* tile;
-  const T2* tws = load_twiddles(a.tw[2], n3, &tile);
+  const T2* tws = load_twiddles(a.tw[2], n3, false, &tile);
   const int x0 = blockIdx.x * W;
   const int py = blockIdx.y;
   const int kind = blockIdx.z;
@@ -850,7 +852,7 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
   const Geom g = a.g;
   const int L1 = g.n1, H = g.H;
   T2* tile;
-  const T2* tws = load_twiddles(a.tw[0], L1, &tile);
+  const T2* tws = load_twiddles(a.tw[0], L1, true, &tile);
   const int BS = padded_rows(L1) * CP;
   const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;

@@ -101,9 +101,13 @@ void plan_permutation(const AxisPlan& p, int* perm, int* pos) {
   }
 }
 
-// Twiddles e^{-2 pi i t / L} (exact at multiples of pi/2) and the wave-vector
-// table {q, sin q, cos q - 1, sin q/2, cos q/2, nyquist} by frequency index.
-void axis_tables(int L, double* tw, double* kt) {
+// Twiddles w^t = e^{-2 pi i t / L} (exact at multiples of pi/2) in the layout
+// tile_fft_ct reads (tw_count(L, staged) complex values: rows per stage for the
+// compile-time lengths when staged, else w^t by t) and the wave-vector table
+// {q, sin q, cos q - 1, sin q/2, cos q/2, nyquist} by frequency index.
+void axis_tables(int L, bool staged, double* tw, double* kt) {
+  static_assert(fftls::tw_count(512, true) <= kMaxL + 2, "stage twiddle rows fit the plain table's bound");
+  double plain[2 * kMaxL];
   for (int t = 0; t < L; ++t) {
     const double ang = -2.0 * M_PI * (double)t / (double)L;
     double cs = cos(ang), sn = sin(ang);
@@ -113,8 +117,23 @@ void axis_tables(int L, double* tw, double* kt) {
       cs = cq[qd % 4];
       sn = sq[qd % 4];
     }
-    tw[2 * t] = cs;
-    tw[2 * t + 1] = sn;
+    plain[2 * t] = cs;
+    plain[2 * t + 1] = sn;
+  }
+  const int ntw = fftls::tw_count(L, staged);
+  for (int t = 0; t < 2 * ntw; ++t) tw[t] = t < 2 * L ? plain[t] : 0.0;
+  if (staged && fftls::ct_length(L)) {
+    for (int t = 0; t < 2 * ntw; ++t) tw[t] = 0.0;
+    for (int st = 0; st < fftls::p2_nst(L); ++st) {
+      const int R = fftls::p2_radix(L, st), M = fftls::p2_msize(L, st), MR = M / R, T = L / M;
+      if (MR == 1) continue;
+      double* rows = tw + 2 * (size_t)fftls::stage_tw_offset(L, st);
+      for (int j = 0; j < MR; ++j)
+        for (int r = 1; r < R; ++r) {
+          rows[2 * (j * R + r - 1)] = plain[2 * (r * j * T)];
+          rows[2 * (j * R + r - 1) + 1] = plain[2 * (r * j * T) + 1];
+        }
+    }
   }
   for (int m = 0; m < L; ++m) {
     const int s = m <= L / 2 ? m : m - L;
@@ -195,7 +214,6 @@ fftls_status set_err(fftls_ctx* c, fftls_status s, const char* fmt, ...) {
   } while (0)
 
 int ncomp(int dim) { return dim == 3 ? 6 : 3; }
-int even_up(int n) { return (n + 1) & ~1; }
 int odd_up(int n) { return (n & 1) ? n : n + 1; }
 
 bool default_medium(const fftls_problem* p, double* l0, double* m0) {
@@ -322,13 +340,16 @@ void coef_table(const Setup& S, const fftls_problem* p, double* cf) {
   }
 }
 
-// Table block per precision: per axis twiddles (L complex) then k tables (L x 6).
+// Table block per precision: per axis twiddles (tw_count(L, ax == 0) complex: the x1
+// axis in the stage layout) then k tables (L x 6).
 size_t table_offset_tw(const Setup& S, int ax) {
   size_t off = 0;
-  for (int a = 0; a < ax; ++a) off += 2 * (size_t)even_up(S.pl[a].L) + 6 * (size_t)S.pl[a].L;
+  for (int a = 0; a < ax; ++a) off += 2 * (size_t)fftls::tw_count(S.pl[a].L, a == 0) + 6 * (size_t)S.pl[a].L;
   return off;
 }
-size_t table_offset_kt(const Setup& S, int ax) { return table_offset_tw(S, ax) + 2 * (size_t)even_up(S.pl[ax].L); }
+size_t table_offset_kt(const Setup& S, int ax) {
+  return table_offset_tw(S, ax) + 2 * (size_t)fftls::tw_count(S.pl[ax].L, ax == 0);
+}
 size_t table_count(const Setup& S) { return table_offset_tw(S, 3); }
 
 void build_tables(const Setup& S, std::vector<double>& tab, std::vector<int>& perms) {
@@ -336,7 +357,7 @@ void build_tables(const Setup& S, std::vector<double>& tab, std::vector<int>& pe
   perms.assign(2 * (size_t)(S.pl[0].L + S.pl[1].L + S.pl[2].L), 0);
   size_t po = 0;
   for (int ax = 0; ax < 3; ++ax) {
-    axis_tables(S.pl[ax].L, &tab[table_offset_tw(S, ax)], &tab[table_offset_kt(S, ax)]);
+    axis_tables(S.pl[ax].L, ax == 0, &tab[table_offset_tw(S, ax)], &tab[table_offset_kt(S, ax)]);
     plan_permutation(S.pl[ax], &perms[po], &perms[po + S.pl[ax].L]);
     po += 2 * (size_t)S.pl[ax].L;
   }
@@ -356,7 +377,7 @@ PlanGeom plan_geom(const Setup& S, size_t cb, bool real_eta) {
   const int nc = S.nc;
   G.cb = cb;
   G.lim = (size_t)S.smem_optin - 4096;  // static reduction arrays
-  G.twx = (size_t)even_up(S.g.n1) * cb;
+  G.twx = (size_t)fftls::tw_count(S.g.n1, true) * cb;
   G.line1 = (size_t)padded_rows(S.g.n1) * odd_up(real_eta ? (nc + 1) / 2 : nc) * cb;
   G.line5 = (size_t)padded_rows(S.g.n1) * odd_up((nc + 1) / 2) * cb;
   G.nlines = (long long)S.g.n2 * S.g.n3;
@@ -364,7 +385,7 @@ PlanGeom plan_geom(const Setup& S, size_t cb, bool real_eta) {
   return G;
 }
 
-size_t strided_smem(int L, int w, int nc, size_t cb) { return (size_t)even_up(L) * cb + (size_t)L * w * nc * cb; }
+size_t strided_smem(int L, int w, int nc, size_t cb) { return (size_t)fftls::tw_count(L, false) * cb + (size_t)L * w * nc * cb; }
 
 // Built-in schedule: x1 tiles of about 32 KB (64 KB for the two-field forward
 // tile), x2/x3 tiles of at most 16 modes and about 100 KB, eta slabs of up to 32
@@ -1340,7 +1361,7 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   NA_TRY(cudaMemcpyAsync(base + o_coef, g_na_coef, sizeof(g_na_coef), cudaMemcpyHostToDevice, S.s));
   size_t po = 0;
   for (int ax = 0; ax < 3; ++ax) {
-    axis_tables(S.pl[ax].L, &g_na_tab[table_offset_tw(S, ax)], &g_na_tab[table_offset_kt(S, ax)]);
+    axis_tables(S.pl[ax].L, ax == 0, &g_na_tab[table_offset_tw(S, ax)], &g_na_tab[table_offset_kt(S, ax)]);
     plan_permutation(S.pl[ax], &g_na_perm[po], &g_na_perm[po + S.pl[ax].L]);
     po += 2 * (size_t)S.pl[ax].L;
   }
