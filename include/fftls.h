@@ -201,10 +201,11 @@ fftls_status fftls_solve_batched(fftls_ctx* ctx, const fftls_problem* probs, int
  * lines per batch of the forward x1 pass, voxels per thread it loads together,
  * lines per batch of the inverse x1 pass, modes per tile of the x2 pass, of the
  * x3 pass, x3-planes per block of the real-space eta kernel (0: not used),
- * 1 if tuned on the device else 0}.  Copies min(*count, held) rows into
+ * 1 if tuned on the device else 0, threads per block of the x2 pass and of
+ * the x3 pass (0: chosen from the tile size)}.  Copies min(*count, held) rows into
  * `rows` (may be NULL when *count is 0) and returns the number held in *count.
  * The paper has no counterpart (an implementation detail of the GPU path). */
-#define FFTLS_PLAN_FIELDS 12
+#define FFTLS_PLAN_FIELDS 14
 fftls_status fftls_tile_plans(const fftls_ctx* ctx, int* rows, int* count);
 
 /* Kernels launched on this context since creation (nodes of CUDA graphs

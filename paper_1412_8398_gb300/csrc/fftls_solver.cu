@@ -699,13 +699,36 @@ fftls_status tune_plan(fftls_ctx* c, const Setup& S, IterArgs<T>& a, bool real_e
     P.x1_vb = bv;
     apply_plan<T>(S, a, real_eta, P);
   }
+  // strided passes: tile width and block size searched jointly (a narrow tile with
+  // small blocks puts more independent blocks on an SM)
+  auto search_wt = [&](int TilePlan::*wf, int TilePlan::*tf, LaunchFn fn) {
+    float best = INFINITY;
+    int bw = P.*wf, bt = P.*tf;
+    for (int w : widths)
+      for (int thr : {256, 512}) {
+        if (err != cudaSuccess) return;
+        TilePlan Q = P;
+        Q.*wf = w;
+        Q.*tf = thr;
+        if (!apply_plan<T>(S, a, real_eta, Q)) continue;
+        float ms = 0.f;
+        err = timed(fn, &ms);
+        c->launches += 1 + kReps;
+        if (ms < best) {
+          best = ms;
+          bw = w;
+          bt = thr;
+        }
+      }
+    P.*wf = bw;
+    P.*tf = bt;
+    apply_plan<T>(S, a, real_eta, P);
+  };
   if (S.g.n2 > 1)
-    search(&TilePlan::y_w, widths, [](const IterArgs<T>& x, cudaStream_t st) { return launch_mid_y<T>(x, false, st); });
-  search(&TilePlan::z_w, widths, [](const IterArgs<T>& x, cudaStream_t st) { return launch_fourier_z<T>(x, st); });
-  if (S.g.n2 > 1)
-    search(&TilePlan::y_thr, {256, 512},
-           [](const IterArgs<T>& x, cudaStream_t st) { return launch_mid_y<T>(x, false, st); });
-  search(&TilePlan::z_thr, {256, 512}, [](const IterArgs<T>& x, cudaStream_t st) { return launch_fourier_z<T>(x, st); });
+    search_wt(&TilePlan::y_w, &TilePlan::y_thr,
+              [](const IterArgs<T>& x, cudaStream_t st) { return launch_mid_y<T>(x, false, st); });
+  search_wt(&TilePlan::z_w, &TilePlan::z_thr,
+            [](const IterArgs<T>& x, cudaStream_t st) { return launch_fourier_z<T>(x, st); });
   a.eps = (T*)c->specB.p;  // scratch target of the inverse pass's update
   search(&TilePlan::x5_lines, {1, 2, 4, 8}, [](const IterArgs<T>& x, cudaStream_t st) { return launch_inv_x<T>(x, st); });
   a.eps = keep.eps;
@@ -821,7 +844,8 @@ fftls_status fftls_tile_plans(const fftls_ctx* c, int* rows, int* count) {
     const PlanKey& k = c->plans[i].first;
     const TilePlan& P = c->plans[i].second;
     const int row[FFTLS_PLAN_FIELDS] = {k.prec,     k.n1,  k.n2,  k.n3, k.green, P.x1_lines, P.x1_vb,
-                                        P.x5_lines, P.y_w, P.z_w, k.real_eta ? P.e_planes : 0, P.tuned};
+                                        P.x5_lines, P.y_w, P.z_w, k.real_eta ? P.e_planes : 0, P.tuned,
+                                        P.y_thr,    P.z_thr};
     memcpy(rows + (size_t)i * FFTLS_PLAN_FIELDS, row, sizeof(row));
   }
   *count = held;

@@ -400,7 +400,7 @@ class Solver:
         n = ctypes.c_int(0)
         self.lib.fftls_tile_plans(self.handle, None, ctypes.byref(n))
         keys = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x1_vb", "x5_lines", "y_w", "z_w", "e_planes",
-                "tuned")
+                "tuned", "y_threads", "z_threads")
         w = len(keys)
         rows = (ctypes.c_int * (w * max(n.value, 1)))()
         self.lib.fftls_tile_plans(self.handle, rows, ctypes.byref(n))
