@@ -327,12 +327,17 @@ __device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
   // stage of the padded x1 tiles (few columns, rows 8 apart), where consecutive
   // butterflies of one column keep a half-warp on distinct shared-memory banks
   constexpr bool BF_ORDER = PAD && MR == 1;
-  const FastDiv fb = make_fastdiv(nbf);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int c, rest;
-    if (BF_ORDER) {
-      c = fdiv(idx, fb);
-      rest = idx - c * nbf;
+    if (BF_ORDER) {  // c = idx / nbf by at most NCOLS - 1 subtractions (NCOLS is small)
+      c = 0;
+      rest = idx;
+#pragma unroll
+      for (int k = 1; k < NCOLS; ++k)
+        if (rest >= nbf) {
+          rest -= nbf;
+          ++c;
+        }
     } else {
       rest = idx / NCOLS;
       c = idx - rest * NCOLS;

@@ -138,20 +138,25 @@ __device__ __forceinline__ void prefetch_voxels(const T* eps, const uint8_t* pha
     asm volatile("prefetch.global.L2 [%0];" ::"l"(phase + v0 + min((long long)l * 128, (long long)nvox - 1)));
 }
 
-// Copy `rows` rows of `cols` complex values between a tile (row stride C) and
-// global memory (row stride gstride, in complex values).  Rows of whole 16-byte
-// units with 16-byte aligned starts go through cp.async (loads) and 16-byte
-// vector accesses; anything else element by element.
-template <typename T2>
-__device__ __forceinline__ void tile_load(T2* tile, int C, const T2* g, long long gstride, int rows, int cols) {
-  const bool vec = ((cols * sizeof(T2)) % 16 == 0) && ((C * sizeof(T2)) % 16 == 0) &&
-                   ((gstride * sizeof(T2)) % 16 == 0) && (((size_t)g & 15) == 0);
+// Copy `rows` rows of `cols` complex values between a tile (row stride C, a
+// compile-time width) and global memory (row stride gstride, in complex values).
+// Rows of whole 16-byte units with 16-byte aligned starts go through cp.async
+// (loads) and 16-byte vector accesses; anything else element by element.  Full
+// rows (cols == C) split the work with compile-time divisions; only a partial
+// tile builds a run-time divider (a 64-bit division per thread).
+template <int C, typename T2>
+__device__ __forceinline__ void tile_load(T2* tile, const T2* g, long long gstride, int rows, int cols) {
+  constexpr int PER = 16 / sizeof(T2);
+  const bool vec = (C % PER == 0) && (cols % PER == 0) && ((gstride * sizeof(T2)) % 16 == 0) &&
+                   (((size_t)g & 15) == 0);
   if (vec) {
-    constexpr int PER = 16 / sizeof(T2);
+    constexpr int UC = C / PER;
+    const bool full = cols == C;
     const int U = cols / PER;
-    const FastDiv fu = make_fastdiv(U);
+    FastDiv fu = {0u, 0u, 1};
+    if (!full) fu = make_fastdiv(U);
     for (int idx = threadIdx.x; idx < rows * U; idx += blockDim.x) {
-      const int r = fdiv(idx, fu), u = idx - r * U;
+      const int r = full ? (int)((unsigned)idx / UC) : fdiv(idx, fu), u = idx - r * U;
       cp_async16(tile + r * C + u * PER, g + r * gstride + u * PER);
     }
     cp_async_wait_all();
@@ -165,16 +170,19 @@ __device__ __forceinline__ void tile_load(T2* tile, int C, const T2* g, long lon
   __syncthreads();
 }
 
-template <typename T2>
-__device__ __forceinline__ void tile_store(const T2* tile, int C, T2* g, long long gstride, int rows, int cols) {
-  const bool vec = ((cols * sizeof(T2)) % 16 == 0) && ((C * sizeof(T2)) % 16 == 0) &&
-                   ((gstride * sizeof(T2)) % 16 == 0) && (((size_t)g & 15) == 0);
+template <int C, typename T2>
+__device__ __forceinline__ void tile_store(const T2* tile, T2* g, long long gstride, int rows, int cols) {
+  constexpr int PER = 16 / sizeof(T2);
+  const bool vec = (C % PER == 0) && (cols % PER == 0) && ((gstride * sizeof(T2)) % 16 == 0) &&
+                   (((size_t)g & 15) == 0);
   if (vec) {
-    constexpr int PER = 16 / sizeof(T2);
+    constexpr int UC = C / PER;
+    const bool full = cols == C;
     const int U = cols / PER;
-    const FastDiv fu = make_fastdiv(U);
+    FastDiv fu = {0u, 0u, 1};
+    if (!full) fu = make_fastdiv(U);
     for (int idx = threadIdx.x; idx < rows * U; idx += blockDim.x) {
-      const int r = fdiv(idx, fu), u = idx - r * U;
+      const int r = full ? (int)((unsigned)idx / UC) : fdiv(idx, fu), u = idx - r * U;
       *reinterpret_cast<float4*>(g + r * gstride + u * PER) = *reinterpret_cast<const float4*>(tile + r * C + u * PER);
     }
   } else {
@@ -485,9 +493,9 @@ __global__ void __launch_bounds__(512) k_mid_y(IterArgs<T> a, int inv) {
   T2* spec = blockIdx.z ? a.specB : a.specA;
   const long long base = ((long long)blockIdx.y * n2 * g.H + x0) * NC;
   const long long rstride = (long long)g.H * NC;
-  tile_load(tile, C, spec + base, rstride, n2, cols);
+  tile_load<C>(tile, spec + base, rstride, n2, cols);
   tile_fft_ct<C, C, false>(tile, 1, 0, a.pl[1], tws, inv != 0);
-  tile_store(tile, C, spec + base, rstride, n2, cols);
+  tile_store<C>(tile, spec + base, rstride, n2, cols);
 }
 
 // ---------------------------------------------------------------------------
@@ -741,13 +749,14 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   T2* spec = kind ? a.specB : a.specA;
   const long long base = ((long long)py * g.H + x0) * NC;
   const long long zstride = (long long)g.n2 * g.H * NC;
-  const FastDiv fnx = make_fastdiv(nx);
-  tile_load(tile, C, spec + base, zstride, n3, cols);
+  FastDiv fnx = {0u, 0u, 1};  // full tiles (nx == W) divide by the compile-time width
+  if (nx != W) fnx = make_fastdiv(nx);
+  tile_load<C>(tile, spec + base, zstride, n3, cols);
   const int ym = __ldg(&a.perm[1][py]);
   tile_fft_ct<C, C, false>(tile, 1, 0, a.pl[2], tws, false);
   T eta_acc = (T)0;
   for (int idx = threadIdx.x; idx < n3 * nx; idx += blockDim.x) {
-    const int pz = fdiv(idx, fnx), xc = idx - pz * nx;
+    const int pz = nx == W ? (int)((unsigned)idx / W) : fdiv(idx, fnx), xc = idx - pz * nx;
     const int zm = __ldg(&a.perm[2][pz]);
     T2* mp = tile + pz * C + xc * NC;
     T2 X[NC];
@@ -764,7 +773,7 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   __syncthreads();
   if (do_green) {
     tile_fft_ct<C, C, false>(tile, 1, 0, a.pl[2], tws, true);
-    tile_store(tile, C, spec + base, zstride, n3, cols);
+    tile_store<C>(tile, spec + base, zstride, n3, cols);
   }
   if (!a.eta_real) {  // with the real-space eta the x1 pass owns part_eta
     double e1[1] = {(double)eta_acc};
