@@ -22,11 +22,15 @@ periodic spheres) built by ``microstructure``.
   (f = 20 %, chi = 1e-4) of Sec. 5.3 at grid length L.
 * ``boolean_reference_study``: N(E0) and its minimum on the 64^3 Boolean model of Sec. 6
   (743 spheres of diameter 5, f = 17 %).
+* ``eight_cube``: the 3D analogue of the four-cell (Sec. 5.2): a centred cube inclusion of side
+  L/2 (f = 12.5 %, chi = 1e3) under eps_bar_12 = eps_bar_21 = 1/2, sigma_12 on the section
+  x3 = -0.2461 close to the inclusion's face: mirror asymmetry, corner peaks, ripple inside the
+  inclusion, and the fraction of voxels above 8.5.
 
 The paper's phases (Sec. 2): nu = 0.25 in both phases; matrix kappa = 1, mu = 0.6
 (lambda = 0.4 in 2D, 0.6 in 3D); the inclusion's moduli are chi times the matrix's.
-``python -m paper_1412_8398_gb300.experiments`` runs the three studies and prints one JSON
-summary per study.
+``python -m paper_1412_8398_gb300.experiments [--study NAME ...]`` runs the studies (all four by
+default) and prints one JSON summary per case.
 """
 from __future__ import annotations
 
@@ -170,21 +174,81 @@ def boolean_reference_study(solver, chi=1e-5, green="R", scheme="AS", tol=1e-8, 
             "fraction": float(info["fraction"]), "sweep": sweep, "optimal_E0": E0, "optimal_iterations": N}
 
 
-def main():
+def section_index(L: int, x3: float = -0.2461) -> int:
+    """Voxel plane nearest to the section x3 (cell [-1/2, 1/2)^3, voxel i at x = -1/2 + i / L;
+    x3 = -0.2461 is the second voxel plane of the inclusion at L = 256, 512, 1024)."""
+    return int(round((0.5 + x3) * L))
+
+
+def mirror_asymmetry(s12):
+    """max |sigma_12 - M sigma_12| / max |sigma_12| over the cube's mirrors x_i -> -x_i and the
+    swap x1 <-> x2 (index i -> L - 1 - i about the cube's centre); sigma_12 is invariant under
+    each for the load eps_bar_12 (a reflection flips the sign of eps_bar_12 and of sigma_12)."""
+    m = np.abs(s12).max()
+    maps = [s12[:, :, ::-1], s12[:, ::-1, :], s12[::-1, :, :], np.swapaxes(s12, 1, 2)] if s12.ndim == 3 else \
+        [s12[:, ::-1], s12[::-1, :], s12.T]
+    return max(float(np.abs(s12 - t).max()) for t in maps) / m
+
+
+def eight_cube(solver, L=128, green="R", chi=1e3, tol=1e-12, max_iter=100000, x3=-0.2461, threshold=8.5,
+               window=0.04, precision="fp64"):
+    """Sec. 5.2: the centred cube inclusion of side L/2, eps_bar_12 = eps_bar_21 = 1/2, AS, iterated
+    until no strain or stress value moves by more than tol (FP64: round-off).  Returns statistics of
+    sigma_12: on the section plane (its maximum, its mirror asymmetry, the peaks in squares of
+    half-width `window` around the four corners of the inclusion's cross-section and their spread,
+    the ripple inside the inclusion = mean |second difference along x1| / mean |sigma_12| away from
+    the interface) and over the volume (mirror asymmetry, fraction of voxels above `threshold`)."""
+    ph = MS.square_inclusion(L, 3)
+    lam, mu = paper_phases(chi, 3)
+    eb = np.zeros((3, 3))
+    eb[0, 1] = eb[1, 0] = 0.5
+    r = solver.solve(ph, lam, mu, eb, green, "AS", tol=tol, max_iter=max_iter, precision=precision,
+                     stop="maxdelta", want_strain=False, history=False, raise_on_error=False)
+    s12 = np.asarray(r.stress[5])  # [x3][x2][x1]
+    z = section_index(L, x3)
+    sec = s12[z]
+    lo, hi = L // 4, L // 4 + L // 2
+    h = max(1, int(round(window * L)))
+    peaks = [float(sec[cy - h:cy + h, cx - h:cx + h].max()) for cy in (lo, hi) for cx in (lo, hi)]
+    inner = sec[lo + 2:hi - 2, lo + 2:hi - 2]
+    ripple = float(np.abs(np.diff(inner, 2, axis=1)).mean() / np.abs(inner).mean())
+    return {"L": L, "green": green, "iterations": int(r.iterations), "converged": bool(r.converged),
+            "section_plane": z, "max_sigma12_section": float(sec.max()),
+            "mirror_asymmetry_section": mirror_asymmetry(sec), "mirror_asymmetry_volume": mirror_asymmetry(s12),
+            "corner_peaks": peaks, "corner_spread": (max(peaks) - min(peaks)) / max(peaks),
+            "ripple_inside": ripple, "frac_above_threshold": float(np.mean(s12 > threshold)),
+            "mean_sigma12": float(s12.mean())}
+
+
+def main(argv=None):
+    import argparse
     import json
 
     from . import fftls
+    ap = argparse.ArgumentParser(description="the paper's studies on the GPU path, one JSON line per case")
+    ap.add_argument("--study", action="append", choices=["four_cell", "periodic_sphere", "eight_cube", "boolean_reference"],
+                    help="run only these studies (repeatable; default: all)")
+    ap.add_argument("--cube-sizes", default="128,256", help="grid lengths of the eight-cube study")
+    args = ap.parse_args(argv)
+    studies = args.study or ["four_cell", "periodic_sphere", "eight_cube", "boolean_reference"]
     s = fftls.Solver(0)
     try:
-        for g in ("MS", "C", "W", "R"):
-            print(json.dumps({"study": "four_cell", **{k: v for k, v in four_cell(s, 512, g).items()
-                                                          if k != "corners"}}), flush=True)
-        for L in (64, 128, 256):
-            print(json.dumps({"study": "periodic_sphere", **periodic_sphere_modulus(s, L)}), flush=True)
-        for g in ("R", "W", "C"):
-            for eta_only in (True, False):
-                print(json.dumps({"study": "boolean_reference",
-                                  **boolean_reference_study(s, green=g, eta_only=eta_only)}), flush=True)
+        if "four_cell" in studies:
+            for g in ("MS", "C", "W", "R"):
+                print(json.dumps({"study": "four_cell", **{k: v for k, v in four_cell(s, 512, g).items()
+                                                              if k != "corners"}}), flush=True)
+        if "periodic_sphere" in studies:
+            for L in (64, 128, 256):
+                print(json.dumps({"study": "periodic_sphere", **periodic_sphere_modulus(s, L)}), flush=True)
+        if "eight_cube" in studies:
+            for L in (int(v) for v in args.cube_sizes.split(",")):
+                for g in ("MS", "C", "W", "R"):
+                    print(json.dumps({"study": "eight_cube", **eight_cube(s, L, g)}), flush=True)
+        if "boolean_reference" in studies:
+            for g in ("R", "W", "C"):
+                for eta_only in (True, False):
+                    print(json.dumps({"study": "boolean_reference",
+                                      **boolean_reference_study(s, green=g, eta_only=eta_only)}), flush=True)
     finally:
         s.close()
     return 0

@@ -5,7 +5,9 @@
 * iterations grow with the contrast, much faster for the direct than for the
   accelerated scheme (Sec. 6.3: ~chi against ~sqrt(chi));
 * the apparent modulus converges within the Voigt and Reuss bounds, and the
-  full C~ from six loads is symmetric (eq. a2).
+  full C~ from six loads is symmetric (eq. a2);
+* on the eight-cube cell (Sec. 5.2) G, G^C and G^R keep the cube's mirror symmetries in
+  sigma_12 and G^W does not.
 """
 import numpy as np
 import pytest
@@ -71,3 +73,21 @@ def test_modulus_history_and_full_stiffness(env):
     C, its = X.effective_stiffness(s, ph, lam, mu, tol=1e-8)
     assert np.allclose(C, C.T, rtol=1e-6, atol=1e-8 * np.abs(C).max())
     assert abs(C[0, 0] - h[-1]) < 1e-4 * C[0, 0]
+
+
+def test_eight_cube_symmetry(env):
+    s, X = env
+    out = {g: X.eight_cube(s, 32, g, tol=1e-10) for g in ("MS", "C", "W", "R")}
+    # <sigma_12> = mu_eff (eps_bar_12 = 1/2) lies between the Reuss and Voigt means of mu, f = 1/8
+    mu_m, mu_i = 0.6, 600.0
+    reuss, voigt = 1.0 / (7 / 8 / mu_m + 1 / 8 / mu_i), 7 / 8 * mu_m + 1 / 8 * mu_i
+    for g, o in out.items():
+        assert o["converged"], (g, o["iterations"])
+        assert o["section_plane"] == 8
+        assert reuss < o["mean_sigma12"] < voigt, (g, o["mean_sigma12"])
+    for g in ("MS", "C", "R"):
+        assert out[g]["mirror_asymmetry_volume"] < 1e-6, (g, out[g]["mirror_asymmetry_volume"])
+    assert out["W"]["mirror_asymmetry_volume"] > 1e-3
+    # the same cell, the same load: the operators agree on the mean stress to a few percent
+    means = [o["mean_sigma12"] for o in out.values()]
+    assert (max(means) - min(means)) < 0.05 * max(means)

@@ -193,6 +193,26 @@ def test_centered_disc_symmetry():
             assert asym < 1e-10
 
 
+def test_eight_cube_symmetry():
+    """The centred cube (the 3D four-cell of Sec. 5.2) under eps_bar_12: sigma_12 is invariant
+    under the mirrors x_i -> -x_i and the swap x1 <-> x2 for G, G^C, G^R and not for G^W."""
+    n = 8
+    ph = MS.square_inclusion(n, 3)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.25), (1000.0, 0.25)])
+    eb = np.zeros((3, 3))
+    eb[0, 1] = eb[1, 0] = 0.5
+    for green in GREENS:
+        r = O.solve(ph, lam, mu, eb, green, O.ACCELERATED, tol=1e-12, max_iter=5000)
+        assert r["converged"]
+        s12 = r["stress"][0, 1]
+        maps = [s12[:, :, ::-1], s12[:, ::-1, :], s12[::-1, :, :], np.swapaxes(s12, 1, 2)]
+        asym = max(np.abs(s12 - t).max() for t in maps) / np.abs(s12).max()
+        if green == O.WILLOT:
+            assert asym > 1e-3
+        else:
+            assert asym < 1e-10
+
+
 def test_porous_periodic_sphere_ordering():
     """Sec. 5.3: every operator under-estimates C~_1111 at finite L; G^R is closest, G farthest."""
     g = _golden("periodic_sphere.txt")
