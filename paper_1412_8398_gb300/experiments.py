@@ -22,6 +22,9 @@ periodic spheres) built by ``microstructure``.
   (f = 20 %, chi = 1e-4) of Sec. 5.3 at grid length L.
 * ``boolean_reference_study``: N(E0) and its minimum on the 64^3 Boolean model of Sec. 6
   (743 spheres of diameter 5, f = 17 %).
+* ``modulus_rate_study``: Sec. 6.4, the apparent C~_1111 after each iteration of AS with each
+  operator (each at its optimal E0 on the 64^3 model) on the Sec. 6 Boolean model refined to
+  L^3, and the iterations after which it stays within 1 % of its converged value.
 * ``eight_cube``: the 3D analogue of the four-cell (Sec. 5.2): a centred cube inclusion of side
   L/2 (f = 12.5 %, chi = 1e3) under eps_bar_12 = eps_bar_21 = 1/2, sigma_12 on the section
   x3 = -0.2461 close to the inclusion's face: mirror asymmetry, corner peaks, ripple inside the
@@ -29,7 +32,7 @@ periodic spheres) built by ``microstructure``.
 
 The paper's phases (Sec. 2): nu = 0.25 in both phases; matrix kappa = 1, mu = 0.6
 (lambda = 0.4 in 2D, 0.6 in 3D); the inclusion's moduli are chi times the matrix's.
-``python -m paper_1412_8398_gb300.experiments [--study NAME ...]`` runs the studies (all four by
+``python -m paper_1412_8398_gb300.experiments [--study NAME ...]`` runs the studies (all five by
 default) and prints one JSON summary per case.
 """
 from __future__ import annotations
@@ -174,6 +177,52 @@ def boolean_reference_study(solver, chi=1e-5, green="R", scheme="AS", tol=1e-8, 
             "fraction": float(info["fraction"]), "sweep": sweep, "optimal_E0": E0, "optimal_iterations": N}
 
 
+def boolean_model(L: int, seed: int = 39):
+    """The Sec. 6 Boolean model (spheres of diameter 5 on 64^3, f = 17 %) at L^3: the generator draws
+    the same number of centres at the same relative positions for any L when the radius scales with
+    L (seed 39: 746 spheres), so L = 256 and 512 are refinements of the same microstructure."""
+    return MS.boolean_spheres((L, L, L), 2.5 * L / 64.0, 0.17, seed=seed)
+
+
+def settle_iteration(history, final, rel=1e-2):
+    """First iteration k after which every estimate stays within rel of `final` (len(history) if none)."""
+    bad = np.nonzero(np.abs(np.asarray(history) - final) > rel * abs(final))[0]
+    return int(bad[-1]) + 1 if bad.size else 0
+
+
+def modulus_rate_study(solver, L, chi, greens=("MS", "C", "W", "R"), nu0=0.25, tol=1e-6, max_iter=20000,
+                       E0=None, search_evaluations=12, rel=1e-2):
+    """Sec. 6.4: C~_1111 = <sigma_11> after each iteration for eps_bar = e1 (x) e1, AS, on the Boolean
+    model at L^3.  The reference Young's modulus of each operator is its golden-section optimum on the
+    64^3 model at the same contrast (eta <= 1e-8, eta alone), unless E0 = {green: E0} is given; the
+    search brackets are the matrix's and the inclusions' moduli.  Each run iterates to eta <= tol
+    (FP32 bulk, FP64 certification) and reports the iterations after which the estimate stays within
+    rel of its converged value, and the largest relative deviation after iteration 5."""
+    lam, mu = paper_phases(chi, 3)
+    E = [9 * (l + 2 * m / 3) * m / (3 * (l + 2 * m / 3) + m) for l, m in zip(lam, mu)]
+    lo, hi = min(E), max(E)
+    ph, info = boolean_model(L)
+    out = {"L": L, "chi": chi, "fraction": float(info["fraction"]), "spheres": int(info["n_centers"]), "schemes": {}}
+    ph64 = boolean_model(64)[0] if E0 is None else None
+    for g in greens:
+        if E0 is not None and g in E0:
+            e0 = float(E0[g])
+        else:
+            e0, _, _ = optimal_reference(solver, ph64, lam, mu, lo, hi, nu0, g, "AS", 1e-8,
+                                         evaluations=search_evaluations, eta_only=True)
+        l0, m0 = lame(e0, nu0)
+        r = solver.solve(ph, lam, mu, np.diag([1.0, 0.0, 0.0]), g, "AS", lam0=l0, mu0=m0, tol=tol,
+                         max_iter=max_iter, precision="fp32_refine64", want_strain=False, want_stress=False,
+                         history=True, raise_on_error=False)
+        h = r.mean_stress_history[:, 0]
+        final = float(r.mean_stress[0])
+        dev = np.abs(h[5:] - final) / abs(final) if h.size > 5 else np.zeros(1)
+        out["schemes"][g] = {"E0": e0, "iterations": int(r.iterations), "converged": bool(r.converged),
+                             "C1111": final, "settle_1pct": settle_iteration(h, final, rel),
+                             "max_dev_after_5": float(dev.max()), "first_10": [float(v) for v in h[:10]]}
+    return out
+
+
 def section_index(L: int, x3: float = -0.2461) -> int:
     """Voxel plane nearest to the section x3 (cell [-1/2, 1/2)^3, voxel i at x = -1/2 + i / L;
     x3 = -0.2461 is the second voxel plane of the inclusion at L = 256, 512, 1024)."""
@@ -226,11 +275,12 @@ def main(argv=None):
 
     from . import fftls
     ap = argparse.ArgumentParser(description="the paper's studies on the GPU path, one JSON line per case")
-    ap.add_argument("--study", action="append", choices=["four_cell", "periodic_sphere", "eight_cube", "boolean_reference"],
+    ap.add_argument("--study", action="append",
+                    choices=["four_cell", "periodic_sphere", "eight_cube", "boolean_reference", "modulus_rate"],
                     help="run only these studies (repeatable; default: all)")
     ap.add_argument("--cube-sizes", default="128,256", help="grid lengths of the eight-cube study")
     args = ap.parse_args(argv)
-    studies = args.study or ["four_cell", "periodic_sphere", "eight_cube", "boolean_reference"]
+    studies = args.study or ["four_cell", "periodic_sphere", "eight_cube", "boolean_reference", "modulus_rate"]
     s = fftls.Solver(0)
     try:
         if "four_cell" in studies:
@@ -244,6 +294,9 @@ def main(argv=None):
             for L in (int(v) for v in args.cube_sizes.split(",")):
                 for g in ("MS", "C", "W", "R"):
                     print(json.dumps({"study": "eight_cube", **eight_cube(s, L, g)}), flush=True)
+        if "modulus_rate" in studies:  # quasi-porous at 512^3, quasi-rigid at 256^3 (Figs. itPorous, itRigid)
+            for L, chi in ((512, 1e-4), (256, 1e4)):
+                print(json.dumps({"study": "modulus_rate", **modulus_rate_study(s, L, chi)}), flush=True)
         if "boolean_reference" in studies:
             for g in ("R", "W", "C"):
                 for eta_only in (True, False):

@@ -91,3 +91,16 @@ def test_eight_cube_symmetry(env):
     # the same cell, the same load: the operators agree on the mean stress to a few percent
     means = [o["mean_sigma12"] for o in out.values()]
     assert (max(means) - min(means)) < 0.05 * max(means)
+
+
+def test_modulus_settles_slower_for_rigid_inclusions(env):
+    """Sec. 6.4: C~_1111 settles within 1 % of its converged value in far fewer iterations for
+    quasi-porous spheres than for quasi-rigid ones (the reference moduli are the optima measured
+    on the 64^3 model at each contrast)."""
+    s, X = env
+    porous = X.modulus_rate_study(s, 64, 1e-4, greens=("R",), E0={"R": 0.061})["schemes"]["R"]
+    rigid = X.modulus_rate_study(s, 64, 1e4, greens=("R",), E0={"R": 64.45})["schemes"]["R"]
+    assert porous["converged"] and rigid["converged"]
+    assert porous["settle_1pct"] < 30 and rigid["settle_1pct"] > 3 * porous["settle_1pct"], (porous, rigid)
+    # quasi-porous spheres (f ~ 17 %) soften the matrix's C_1111 = 1.8, quasi-rigid ones stiffen it
+    assert porous["C1111"] < 1.8 < rigid["C1111"]
