@@ -51,7 +51,7 @@ typedef struct fftls_ctx fftls_ctx;
 typedef enum {
   FFTLS_OK = 0,
   FFTLS_E_INVALID_ARG = 1,      /* bad dimension, size, moduli, enum or pointer */
-  FFTLS_E_UNSUPPORTED_SIZE = 2, /* a grid length with a prime factor other than 2, 3, 5, or > 1024 */
+  FFTLS_E_UNSUPPORTED_SIZE = 2, /* a length with a prime factor other than 2, 3, 5, or > 2048; tiles too large */
   FFTLS_E_OOM = 3,              /* device allocation failed */
   FFTLS_E_CUDA = 4,             /* a CUDA runtime call failed (message in fftls_last_error) */
   FFTLS_E_NOT_CONVERGED = 5,    /* max_iter reached; outputs hold the last iterate */
@@ -71,7 +71,10 @@ enum { FFTLS_STOP_ETA = 0, FFTLS_STOP_MAXDELTA = 1 };
 
 typedef struct {
   int dim;                  /* 2 or 3 */
-  int n[3];                 /* n1 (x1, fastest), n2, n3; n3 = 1 when dim == 2; each in 1..1024, factors 2,3,5 */
+  int n[3];                 /* n1 (x1, fastest), n2, n3; n3 = 1 when dim == 2; each in 1..2048, factors 2,3,5.
+                               The tiles must also fit in shared memory: in FP64 (and the ladder's FP64
+                               passes) a 3D grid needs n2, n3 <= 2000 and, for G, n1 <= 1600 (so 2048 fits
+                               in 2D and along x1 of 3D G^C/W/R only); else FFTLS_E_UNSUPPORTED_SIZE */
   const uint8_t* phase;     /* N phase ids in 0..n_phases-1, x1 fastest */
   int phase_on_device;      /* 1: `phase` is a device pointer on the context's device */
   int n_phases;             /* 1..256 */

@@ -19,7 +19,7 @@ using namespace fftls;
 
 namespace {
 
-constexpr int kMaxL = 1024;
+constexpr int kMaxL = 2048;
 constexpr int kNumKinds = 8;
 const char* const kKindNames[2][kNumKinds] = {
     {"fwd_x_f32", "mid_y_fwd_f32", "fourier_z_f32", "reduce_eta_f32", "mid_y_inv_f32", "inv_x_f32",

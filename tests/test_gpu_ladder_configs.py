@@ -169,9 +169,13 @@ def test_full_size_512_properties(solver):
     assert spread < 1e-7 * np.abs(exact).max()
 
 
-@pytest.mark.parametrize("shape_np", [(1, 1, 1), (1, 1), (1, 2, 1024), (3, 1, 1)])
+@pytest.mark.parametrize("shape_np", [(1, 1, 1), (1, 1), (1, 2, 1024), (3, 1, 1), (2, 2048), (2048, 2),
+                                      (1, 2, 2048), (2048, 1, 2)])
 def test_degenerate_and_maximum_lengths(solver, shape_np):
-    """Single voxel, single-pixel 2D grid, the longest supported axis, unit axes."""
+    """Single voxel, single-pixel 2D grid, the longest supported axes (2048: in 3D FP64 refused along
+    x2 / x3, whose tiles of six complex doubles per mode do not fit shared memory, and for G along
+    x1, whose tau and sigma lines share one tile), unit axes."""
+    from paper_1412_8398_gb300 import fftls
     rng = np.random.default_rng(0)
     ph = (rng.random(shape_np) < 0.5).astype(np.uint8)
     d = ph.ndim
@@ -179,6 +183,11 @@ def test_degenerate_and_maximum_lengths(solver, shape_np):
     eb = np.eye(d) * 0.5
     eb[0, d - 1] = eb[d - 1, 0] = 0.25
     for g in range(4):
+        if d == 3 and (max(ph.shape[:2]) > 2000 or (g == O.MS and ph.shape[-1] > 1600)):
+            with pytest.raises(fftls.FftlsError) as e:
+                solver.solve(ph, lam, mu, eb, GREENS[g], "AS", tol=0.0, max_iter=3)
+            assert e.value.status == fftls.E_UNSUPPORTED_SIZE
+            continue
         ref = O.solve(ph, lam, mu, eb, g, O.ACCELERATED, tol=0.0, max_iter=3)
         got = solver.solve(ph, lam, mu, eb, GREENS[g], "AS", tol=0.0, max_iter=3)
         assert np.abs(got.strain - comps(ref["strain"])).max() < FIELD_TOL

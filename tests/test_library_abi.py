@@ -60,7 +60,8 @@ def test_host_only_calls(lib):
     from paper_1412_8398_gb300 import fftls
     assert fftls.supported_length(512) and fftls.supported_length(96) and fftls.supported_length(1)
     assert fftls.supported_length(48) and fftls.supported_length(5) and fftls.supported_length(1000)
-    assert not fftls.supported_length(7) and not fftls.supported_length(2048) and not fftls.supported_length(0)
+    assert fftls.supported_length(2048) and fftls.supported_length(1536)
+    assert not fftls.supported_length(7) and not fftls.supported_length(4096) and not fftls.supported_length(0)
     l0, m0 = fftls.reference_medium([0.6, 600.0], [0.6, 600.0], 3, "AS")
     assert abs(m0 - math.sqrt(0.6 * 600.0)) < 1e-12 and abs(l0 + 2 * m0 / 3 - math.sqrt(1000.0)) < 1e-12
     l0, m0 = fftls.reference_medium([0.4, 4.0], [0.6, 6.0], 2, "DS")
