@@ -387,19 +387,30 @@ def cufft_baseline(ph, lam, mu, iters, solver, warm=1):
     return out
 
 
+def bench_config(n, precision, fraction, world):
+    """The `config` of the workload line (shared by both arms)."""
+    return {"workload": f"boolean_spheres_{n}^3_R{8.0 * n / 512:g}_f0.25_chi1000_AS_R_{precision}_eta1e-6",
+            "grid": [n, n, n], "realised_fraction": fraction, "load_cases": "Mandel unit loads, cycled",
+            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only), on the workload's
+    config; each step is one oracle iteration on the cpu_n^3 sample of the same recipe."""
     if rank != 0:
         return
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"  # one core, as the cpu_baseline subprocess (numpy is not imported yet)
     import numpy as np
     from oracle import fftls_oracle as O
+    config = bench_config(args.n, args.precision, workload(args.n)[3]["fraction"], world)
     n = args.cpu_n
     ph, lam, mu, info = workload(n)
     times, iters = [], 0
     for i in range(args.warmup + args.steps):
         eb = O.from_mandel(mandel_load(i % 6), 3)
         t = time.perf_counter()
-        r = O.solve(ph, lam, mu, eb, O.ROTATED, O.ACCELERATED, tol=0.0, max_iter=1)
+        r = O.solve(ph, lam, mu, eb, O.ROTATED, O.ACCELERATED, tol=0.0, max_iter=args.cpu_iters)
         dt = time.perf_counter() - t
         if i >= args.warmup:
             times.append(dt)
@@ -412,9 +423,10 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"boolean_spheres_{n}^3_sample_of_512^3_recipe", "green": "R", "scheme": "AS"},
+        "config": config,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"one oracle iteration per step on the {n}^3 sample of the recipe"},
+                         "sample": f"{args.cpu_iters} FP64 AS/G^R oracle iterations per step on the {n}^3 sample of "
+                                   f"the recipe (radius scaled to {8.0 * n / 512:g}), single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -729,9 +741,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32_refine64" else args.precision,
             "data": "synthetic",
-            "config": {"workload": f"boolean_spheres_{n}^3_R{8.0 * n / 512:g}_f0.25_chi1000_AS_R_{args.precision}_eta1e-6",
-                       "grid": [n, n, n], "realised_fraction": info["fraction"], "load_cases": "Mandel unit loads, cycled",
-                       "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": bench_config(n, args.precision, info["fraction"], world),
             "iterations_per_step": iters / args.steps, "fp32_iterations_per_step": its32 / args.steps,
             "time_to_tol_s": ms_max / 1e3 / args.steps,
             "vs_fp64": fp64,
