@@ -139,10 +139,17 @@ __device__ __forceinline__ void dft_r(T2* v, int R, bool inv) {
   }
 }
 
-// Tiles of x1-lines (few columns) pad one row every 8 rows so that the strided
-// butterflies of the late stages spread over the shared-memory banks.
-__host__ __device__ constexpr int padded_rows(int n) { return n + ((n + 7) >> 3); }
-__device__ __forceinline__ int prow(int e, int pad) { return pad ? e + (e >> 3) : e; }
+// Tiles of x1-lines (few columns, an odd row stride) pad one row every 16 rows,
+// so that the butterflies of the stages with rows 8 or 64 apart, the rows of
+// voxels staged in order, and the digit-reversed partners of the real-to-complex
+// untangling spread over the shared-memory banks (the period was chosen by
+// replaying each phase's addresses per half-warp: at L = 512 one pad row per 8
+// rows needs 42 % more wavefronts than conflict-free accesses would, one per 16
+// rows 21 %, one per 32 rows 49 %).
+constexpr int kPadShift = 4;
+__host__ __device__ constexpr int pad_row(int e) { return e + (e >> kPadShift); }
+__host__ __device__ constexpr int padded_rows(int n) { return n + ((n + (1 << kPadShift) - 1) >> kPadShift); }
+__device__ __forceinline__ int prow(int e, int pad) { return pad ? pad_row(e) : e; }
 
 // Division by a runtime divisor 1 <= d < 2^31 through a multiply-high and a
 // shift (Granlund and Montgomery 1994), exact for 0 <= n < 2^31.
@@ -273,13 +280,6 @@ __device__ void tile_fft_p2(T2* buf, int nblk, int BS, int C, int ncols, const T
   }
 }
 
-// Stage S of the power-of-two plan of length L on tiles whose geometry is
-// known at compile time: C complex values per row (row stride), the first
-// NCOLS columns transformed, rows padded (PAD) or not.  Every butterfly of a
-// stage then reads and writes at compile-time offsets from one base address:
-// with rows e0 + r MR, the padded row index prow(e0 + r MR) equals
-// prow(e0) + r MR + floor(r MR / 8) for every stage of the plans above (MR is a
-// multiple of 8, or e0 mod 8 + r MR mod 8 < 8).
 // One twiddle row of the stage layout (R complex values, 16-byte aligned) into
 // registers: 16-byte loads for FP32, one load per value for FP64.
 template <int R>
@@ -313,6 +313,29 @@ __device__ __forceinline__ void stage_twiddles(const T2* tw, int j, T2* w) {
   }
 }
 
+// pad_row(e0 + r MR) == pad_row(e0) + r MR + (r MR >> kPadShift) for every butterfly
+// (base row e0, leg r) of every stage of the plan of length L.
+__host__ __device__ constexpr bool pad_offsets_hold(int L) {
+  for (int s = 0; s < p2_nst(L); ++s) {
+    const int R = p2_radix(L, s), M = p2_msize(L, s), MR = M / R;
+    for (int bf = 0; bf < L / R; ++bf) {
+      const int e0 = (bf / MR) * M + bf % MR;
+      for (int r = 0; r < R; ++r)
+        if (pad_row(e0 + r * MR) != pad_row(e0) + r * MR + ((r * MR) >> kPadShift)) return false;
+    }
+  }
+  return true;
+}
+static_assert(pad_offsets_hold(64) && pad_offsets_hold(128) && pad_offsets_hold(256) && pad_offsets_hold(512),
+              "padded butterfly offsets are compile-time constants");
+
+// Stage S of the power-of-two plan of length L on tiles whose geometry is
+// known at compile time: C complex values per row (row stride), the first
+// NCOLS columns transformed, rows padded (PAD) or not.  Every butterfly of a
+// stage then reads and writes at compile-time offsets from one base address:
+// with rows e0 + r MR, the padded row index pad_row(e0 + r MR) equals
+// pad_row(e0) + r MR + floor(r MR / 16) for every stage of the compile-time
+// lengths (checked below: pad_offsets_hold).
 template <int L, int S, int C, int NCOLS, bool PAD, bool INV, typename T2>
 __device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
   constexpr int R = p2_radix(L, S);
@@ -324,7 +347,7 @@ __device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
   const int nbf = nblk * NB;
   const int total = nbf * NCOLS;
   // thread order: consecutive threads take consecutive columns, except in the last
-  // stage of the padded x1 tiles (few columns, rows 8 apart), where consecutive
+  // stage of the padded x1 tiles (few columns, legs 1 row apart), where consecutive
   // butterflies of one column keep a half-warp on distinct shared-memory banks
   constexpr bool BF_ORDER = PAD && MR == 1;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -349,7 +372,7 @@ __device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
     T2* base = buf + blk * BS + (PAD ? prow(e0, 1) : e0) * C + c;
     T2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = base[(PAD ? r * MR + ((r * MR) >> 3) : r * MR) * C];
+    for (int r = 0; r < R; ++r) v[r] = base[(PAD ? r * MR + ((r * MR) >> kPadShift) : r * MR) * C];
     if (!INV) {
       dft_fixed<R>(v, false);
       if (MR > 1 && j) {
@@ -368,7 +391,7 @@ __device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
       dft_fixed<R>(v, true);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) base[(PAD ? r * MR + ((r * MR) >> 3) : r * MR) * C] = v[r];
+    for (int r = 0; r < R; ++r) base[(PAD ? r * MR + ((r * MR) >> kPadShift) : r * MR) * C] = v[r];
   }
   __syncthreads();
 }
