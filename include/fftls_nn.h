@@ -2,7 +2,7 @@
  *
  * A small 3D convolutional network maps a phase image (indicator of phase 1)
  * and the stiffness contrast to an initial strain field eps^0, which is handed
- * to fftls_solve as opt->eps_init.  The solver stays the judge: the same
+ * to fftls_solve as opt->eps_init.  The solver still decides: the same
  * equilibrium criterion (eq. criterion of the paper) decides convergence, so a
  * poor prediction costs iterations, never accuracy.  The paper has no learned
  * component: every call below is an implementation feature of this library,

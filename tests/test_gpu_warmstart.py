@@ -6,7 +6,7 @@ and what the trained network gains over the solver started from eps_bar.
 * the whole network: output and every parameter gradient against the oracle's
   analytic backward (itself pinned by finite differences);
 * a short training on solver-generated fields cuts the iterations to
-  eta <= 1e-6 on held-out samples, with the solver as judge.
+  eta <= 1e-6 on held-out samples, the solver deciding convergence.
 """
 import ctypes
 
@@ -183,7 +183,7 @@ def test_network_forward_and_gradients_match_oracle(env):
 def test_trained_network_gain_over_plain_start(env):
     """What a short training buys on held-out samples: the initial field's error
     against the converged solution drops well below that of eps_bar, the solver
-    (the judge) reaches the same moduli from it, and the iteration count to
+    (which decides convergence) reaches the same moduli from it, and the iteration count to
     eta <= 1e-6 is not worse.  The accelerated scheme's iteration count depends
     only logarithmically on the starting error (scaling the exact fluctuation by
     0.5 saves about 5 % of the iterations), so the iteration gain itself is small."""
