@@ -145,11 +145,12 @@ fftls_status fftls_effective_stiffness(fftls_ctx* ctx, const fftls_problem* prob
                                        double* C_eff, int* iterations);
 
 /* Allocation-free solve.  The paper has no counterpart: this entry point is
- * for callers that must not allocate device memory, for example code that runs
- * while a CUDA stream is being captured into a graph (cudaMalloc is not allowed
- * there) or a host application whose device memory is owned by its own
- * allocator and handed out in fixed pools.  It makes no cudaMalloc / cudaFree
- * call, creates no context, stream, event or graph, and needs no fftls_ctx.
+ * for callers that must not allocate device memory, typically an application
+ * that reserves its GPU memory once at start-up and hands it out from its own
+ * fixed pools (a long-running service with a hard memory budget, or a host
+ * framework whose plug-ins may not call cudaMalloc behind its allocator's
+ * back).  It makes no cudaMalloc / cudaFree call, creates no context, stream,
+ * event or graph, and needs no fftls_ctx.
  *  - Scratch (spectrum, partial sums, control block, tables, histories and a
  *    copy of a host phase image) lives in one file-scope device array of
  *    16 MiB, which every GPU that loads the library holds until the process
@@ -158,15 +159,21 @@ fftls_status fftls_effective_stiffness(fftls_ctx* ctx, const fftls_problem* prob
  *    FFTLS_E_UNSUPPORTED_SIZE before anything runs.
  *  - Runs on the caller's current device and on opt->stream (NULL: the legacy
  *    default stream).  The first call on a device looks up the array's device
- *    address; make that first call before any stream capture starts.
- *  - FP64 only (opt->precision must be FFTLS_FP64); no graphs, no profiling.
+ *    address (cudaGetSymbolAddress) with that device current.
+ *  - The call blocks the host: it copies a host phase image and the tables in
+ *    with cudaMemcpyAsync, synchronises opt->stream after every chunk of
+ *    iterations to read the solver's control block back, and copies the mean
+ *    fields and the histories to the host before it returns.
+ *  - FP64 only (opt->precision must be FFTLS_FP64); no profiling.
  *  - opt->fields_on_device must be 1 and res->strain a device buffer of
  *    n_c x N doubles: the iterate lives there.  res->stress (device) and the
  *    host histories are optional.
- *  - Every call shares the one array and leaves its contents behind; calls
- *    that overlap on the GPU (two host threads, or two streams) race and give
- *    wrong results.  Returns the statuses of fftls_solve; no error message is
- *    kept (there is no context). */
+ *  - Every call on a device shares that device's array and leaves its
+ *    contents behind; calls that overlap on one GPU (two host threads, or two
+ *    streams) race and give wrong results.  Calls on different GPUs use
+ *    different arrays; the host-side staging of their tables is serialised by
+ *    a lock, so they may run from different host threads.  Returns the
+ *    statuses of fftls_solve; no error message is kept (there is no context). */
 fftls_status fftls_solve_noalloc(const fftls_problem* prob, const fftls_options* opt, fftls_result* res);
 
 /* Default reference medium (lambda0, mu0) for prob->scheme: eq. refAcc for the

@@ -304,7 +304,7 @@ def mean_strain_error(eps, eps_bar):
 
 def solve(phase, lam, mu, eps_bar, green, scheme, lam0=None, mu0=None,
           tol=1e-8, max_iter=1000, stop=STOP_ETA, eps_init=None, beta=0.5,
-          check_real=True):
+          check_real=True, omega=2.0):
     """Run the direct (eq. ds) or accelerated (eq. as) scheme with operator `green`.
 
     phase: uint8 image, numpy order (n3, n2, n1) or (n2, n1).
@@ -324,6 +324,9 @@ def solve(phase, lam, mu, eps_bar, green, scheme, lam0=None, mu0=None,
     the field returned is then eps^{k+1} and `iterations` = k + 1.
     The iteration is declared diverged (and stops, no update) when eta_k is
     not finite or exceeds 1e4 eta_0.
+    omega is the factor 2 of eq. (as); the tests pass other values only to
+    plant a wrong relaxation and check that the pins of the accelerated step
+    catch it.
     """
     phase = np.asarray(phase)
     d = phase.ndim
@@ -382,7 +385,7 @@ def solve(phase, lam, mu, eps_bar, green, scheme, lam0=None, mu0=None,
         if scheme == DIRECT:
             new = e
         else:
-            new = eps + 2.0 * _contract(Ms, phase, e - eps)
+            new = eps + omega * _contract(Ms, phase, e - eps)
         new_sig = _contract(Cs, phase, new)
         if stop == STOP_MAXDELTA:
             delta = max(float(np.abs(new - eps).max()), float(np.abs(new_sig - sig).max()))

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -1308,9 +1309,9 @@ fftls_status fftls_effective_stiffness(fftls_ctx* c, const fftls_problem* p, con
 
 // ---------------------------------------------------------------------------
 // Allocation-free solve (fftls_solve_noalloc).  The paper has no counterpart:
-// this serves callers that cannot call cudaMalloc (for example code running
-// inside stream capture, or hosts whose device memory is handed out by
-// another allocator).  All scratch lives in one file-scope device array.
+// this serves callers that cannot call cudaMalloc (applications whose device
+// memory is reserved up front and handed out by their own allocator).  All
+// scratch lives in one file-scope device array.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1319,7 +1320,11 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 constexpr int kNoAllocMaxDevices = 64;
 void* g_noalloc_base[kNoAllocMaxDevices];  // device address of g_noalloc_scratch per device (set up on first call)
 
-// host staging for the tables (fixed size: no heap allocation)
+// host staging for the tables (fixed size: no heap allocation), shared by every
+// device: g_na_lock serialises building them and issuing their copies (a
+// cudaMemcpyAsync from pageable memory returns once the source has been staged,
+// so the arrays are free again when the lock is released)
+std::mutex g_na_lock;
 double g_na_coef[256 * kCoef];
 double g_na_tab[3 * (2 * (kMaxL + 2) + 6 * kMaxL)];
 int g_na_perm[6 * kMaxL];
@@ -1339,12 +1344,16 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   int dev = 0;
   NA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices) return FFTLS_E_CUDA;
-  if (!g_noalloc_base[dev]) {  // set-up, once per device, with that device current
-    void* base = nullptr;
-    NA_TRY(cudaGetSymbolAddress(&base, g_noalloc_scratch));
-    g_noalloc_base[dev] = base;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_na_lock);
+    if (!g_noalloc_base[dev]) {  // set-up, once per device, with that device current
+      void* b = nullptr;
+      NA_TRY(cudaGetSymbolAddress(&b, g_noalloc_scratch));
+      g_noalloc_base[dev] = b;
+    }
+    base = (unsigned char*)g_noalloc_base[dev];
   }
-  unsigned char* base = (unsigned char*)g_noalloc_base[dev];
   Setup S;
   memset(&S, 0, sizeof(S));
   setup_geometry(S, p);
@@ -1380,17 +1389,20 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   const size_t o_perm = take(nperm * sizeof(int));
   const size_t o_phase = p->phase_on_device ? 0 : take((size_t)N);
   if (off > kNoAllocScratchBytes) return FFTLS_E_UNSUPPORTED_SIZE;  // grid too large for the fixed scratch
-  // tables (host staging arrays, no heap)
-  coef_table(S, p, g_na_coef);
-  NA_TRY(cudaMemcpyAsync(base + o_coef, g_na_coef, sizeof(g_na_coef), cudaMemcpyHostToDevice, S.s));
+  // tables (host staging arrays, no heap), built and copied under the staging lock
   size_t po = 0;
-  for (int ax = 0; ax < 3; ++ax) {
-    axis_tables(S.pl[ax].L, ax == 0, &g_na_tab[table_offset_tw(S, ax)], &g_na_tab[table_offset_kt(S, ax)]);
-    plan_permutation(S.pl[ax], &g_na_perm[po], &g_na_perm[po + S.pl[ax].L]);
-    po += 2 * (size_t)S.pl[ax].L;
+  {
+    std::lock_guard<std::mutex> lk(g_na_lock);
+    coef_table(S, p, g_na_coef);
+    NA_TRY(cudaMemcpyAsync(base + o_coef, g_na_coef, sizeof(g_na_coef), cudaMemcpyHostToDevice, S.s));
+    for (int ax = 0; ax < 3; ++ax) {
+      axis_tables(S.pl[ax].L, ax == 0, &g_na_tab[table_offset_tw(S, ax)], &g_na_tab[table_offset_kt(S, ax)]);
+      plan_permutation(S.pl[ax], &g_na_perm[po], &g_na_perm[po + S.pl[ax].L]);
+      po += 2 * (size_t)S.pl[ax].L;
+    }
+    NA_TRY(cudaMemcpyAsync(base + o_tab, g_na_tab, ntab * 8, cudaMemcpyHostToDevice, S.s));
+    NA_TRY(cudaMemcpyAsync(base + o_perm, g_na_perm, nperm * sizeof(int), cudaMemcpyHostToDevice, S.s));
   }
-  NA_TRY(cudaMemcpyAsync(base + o_tab, g_na_tab, ntab * 8, cudaMemcpyHostToDevice, S.s));
-  NA_TRY(cudaMemcpyAsync(base + o_perm, g_na_perm, nperm * sizeof(int), cudaMemcpyHostToDevice, S.s));
   // phase image (copied into the scratch when it is on the host) and its id check
   const uint8_t* d_phase = p->phase;
   if (!p->phase_on_device) {

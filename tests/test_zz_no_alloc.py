@@ -1,11 +1,13 @@
 """fftls_solve_noalloc, the allocation-free entry point, against fftls_solve.
 
-Some callers cannot allocate device memory (code running during CUDA stream
-capture, or applications whose device memory comes from their own fixed
-pools), so the library offers a solve whose scratch sits in a fixed
-file-scope device array.  This test calls it through the C ABI twice in a
-row and checks each result against the regular entry point.  The file is
-named so that pytest collects it last.
+Some callers cannot allocate device memory: applications that reserve their
+GPU memory once and hand it out from their own fixed pools must not have a
+library call cudaMalloc behind their allocator's back.  For them the library
+offers a solve whose scratch sits in a fixed file-scope device array.  This
+test calls it through the C ABI twice in a row and checks each result against
+the regular entry point, then covers the two inputs that only this path copies
+into its scratch: a phase image held on the host and a host warm start under
+the direct scheme.  The file is named so that pytest collects it last.
 """
 import ctypes
 import math
@@ -19,15 +21,20 @@ pytestmark = pytest.mark.gpu
 FIELD_TOL = 1e-9
 
 
-def _noalloc(lib, fftls, torch, ph, lam, mu, eb, green, scheme, tol, max_iter):
+def _noalloc(lib, fftls, torch, ph, lam, mu, eb, green, scheme, tol, max_iter, phase_on_device=True, eps_init=None):
     dim = ph.ndim
     nc = 6 if dim == 3 else 3
     p = fftls._Problem()
     p.dim = dim
     p.n[:] = list(reversed(ph.shape)) + [1] * (3 - dim)
-    dph = torch.from_numpy(ph).cuda()
-    p.phase = dph.data_ptr()
-    p.phase_on_device = 1
+    if phase_on_device:
+        dph = torch.from_numpy(ph).cuda()
+        p.phase = dph.data_ptr()
+        p.phase_on_device = 1
+    else:
+        hph = np.ascontiguousarray(ph, dtype=np.uint8)
+        p.phase = hph.ctypes.data
+        p.phase_on_device = 0
     lam = np.ascontiguousarray(lam, dtype=np.float64)
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     p.n_phases = lam.size
@@ -44,6 +51,10 @@ def _noalloc(lib, fftls, torch, ph, lam, mu, eb, green, scheme, tol, max_iter):
     o.tol = tol
     o.max_iter = max_iter
     o.fields_on_device = 1
+    if eps_init is not None:
+        e0 = np.ascontiguousarray(eps_init, dtype=np.float64)
+        o.eps_init = e0.ctypes.data
+        o.eps_init_on_device = 0
     strain = torch.empty((nc,) + ph.shape, dtype=torch.float64, device="cuda")
     stress = torch.empty((nc,) + ph.shape, dtype=torch.float64, device="cuda")
     r = fftls._Result()
@@ -94,4 +105,45 @@ def test_noalloc_matches_solve_twice():
     big = np.zeros((64, 64, 64), dtype=np.uint8)
     st = _noalloc(lib, fftls, torch, big, [1.0], [1.0], np.eye(3), "R", "AS", 1e-6, 10)[0]
     assert st == fftls.E_UNSUPPORTED_SIZE
+    solver.close()
+
+
+def test_noalloc_host_phase_and_warm_start():
+    """A phase image on the host (copied into the scratch array) and a host warm start under the
+    direct scheme (copied into the caller's strain buffer, then one tau-form step) give the
+    regular entry point's results for the same inputs."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_8398_gb300 import build, fftls
+    build.build()
+    lib = fftls.load_library()
+    solver = fftls.Solver(0)
+    cases = [
+        (MS.boolean_spheres((16, 18, 20), 2.5, 0.3, seed=8)[0], "R", "AS", False, False),
+        (MS.centered_disc(48, 0.25), "W", "DS", False, True),
+        (MS.boolean_spheres((12, 16, 18), 2.0, 0.25, seed=9)[0], "C", "DS", True, True),
+    ]
+    for ph, green, scheme, on_device, warm in cases:
+        d = ph.ndim
+        lam, mu = MS.young_poisson_phases([(1.0, 0.3), (50.0, 0.25)])
+        eb = np.zeros((d, d))
+        eb[0, 0] = 1.0
+        eb[0, 1] = eb[1, 0] = 0.2
+        e0 = None
+        if warm:
+            # the converged field of a lower contrast: mean eps_bar, far from the new solution
+            l2, m2 = MS.young_poisson_phases([(1.0, 0.3), (20.0, 0.25)])
+            e0 = solver.solve(ph, l2, m2, eb, green, scheme, tol=1e-9, max_iter=800).strain.copy()
+        ref = solver.solve(ph, lam, mu, eb, green, scheme, tol=1e-9, max_iter=800, eps_init=e0)
+        assert ref.converged
+        st, strain, stress, ms, its, eh = _noalloc(lib, fftls, torch, ph, lam, mu, eb, green, scheme, 1e-9, 800,
+                                                   phase_on_device=on_device, eps_init=e0)
+        assert st == fftls.OK
+        assert abs(its - ref.iterations) <= 1
+        assert np.abs(strain - ref.strain).max() < FIELD_TOL
+        assert np.abs(stress - ref.stress).max() < FIELD_TOL * 100
+        assert np.abs(ms - ref.mean_stress).max() < 1e-10 * np.abs(ref.mean_stress).max()
+        n = min(its, ref.iterations)
+        np.testing.assert_allclose(eh[:n], ref.eta_history[:n], rtol=1e-6, atol=1e-12 * ref.eta_history[0])
     solver.close()
