@@ -199,19 +199,40 @@ __host__ __device__ constexpr bool ct_length(int L) { return L == 64 || L == 128
 __host__ __device__ constexpr int stage_tw_offset(int L, int s) {
   return s == 0 ? 0 : stage_tw_offset(L, s - 1) + (p2_msize(L, s - 1) > p2_radix(L, s - 1) ? p2_msize(L, s - 1) : 0);
 }
-// Complex entries of an axis's shared-memory twiddle table (even, so that the
-// tile after it starts 16-byte aligned): the stage layout for the compile-time
-// lengths when staged, else the plain table tw[t] = w^t, t < L.  Written out as
-// constants (checked below) so that a kernel pays no run-time recursion for it.
-__host__ __device__ constexpr int tw_count(int L, bool staged) {
-  return !staged ? ((L + 1) & ~1)
-       : L == 64 ? 64 : L == 128 ? 160 : L == 256 ? 320 : L == 512 ? 576 : ((L + 1) & ~1);
+// Twiddle-table layouts of an axis (shared memory): kTwPlain, tw[t] = w^t for
+// t < L; kTwX1, the stage rows above (the padded x1 tiles of the compile-time
+// lengths); kTwStrided, the same rows padded to srow(R) complex values (ten for
+// radix 8), read by the x2 / x3 tiles, whose warps touch up to six consecutive
+// rows of a stage at once: 80-byte rows put those on distinct banks (64-byte rows
+// would place rows j and j + 2 on the same banks).
+enum TwLayout : int { kTwPlain = 0, kTwX1 = 1, kTwStrided = 2 };
+__host__ __device__ constexpr int srow(int R) { return R == 8 ? 10 : R; }
+__host__ __device__ constexpr int strided_tw_offset(int L, int s) {
+  return s == 0 ? 0
+                : strided_tw_offset(L, s - 1) +
+                      (p2_msize(L, s - 1) > p2_radix(L, s - 1)
+                           ? (p2_msize(L, s - 1) / p2_radix(L, s - 1)) * srow(p2_radix(L, s - 1))
+                           : 0);
 }
-static_assert(tw_count(64, true) == stage_tw_offset(64, p2_nst(64)) &&
-                  tw_count(128, true) == stage_tw_offset(128, p2_nst(128)) &&
-                  tw_count(256, true) == stage_tw_offset(256, p2_nst(256)) &&
-                  tw_count(512, true) == stage_tw_offset(512, p2_nst(512)),
+// Complex entries of an axis's shared-memory twiddle table (even, so that the
+// tile after it starts 16-byte aligned): the stage layouts for the compile-time
+// lengths, else the plain table.  Written out as constants (checked below) so
+// that a kernel pays no run-time recursion for it.
+__host__ __device__ constexpr int tw_count(int L, int layout) {
+  return layout == kTwX1 ? (L == 64 ? 64 : L == 128 ? 160 : L == 256 ? 320 : L == 512 ? 576 : ((L + 1) & ~1))
+       : layout == kTwStrided ? (L == 64 ? 80 : L == 128 ? 160 : L == 256 ? 336 : L == 512 ? 720 : ((L + 1) & ~1))
+       : ((L + 1) & ~1);
+}
+static_assert(tw_count(64, kTwX1) == stage_tw_offset(64, p2_nst(64)) &&
+                  tw_count(128, kTwX1) == stage_tw_offset(128, p2_nst(128)) &&
+                  tw_count(256, kTwX1) == stage_tw_offset(256, p2_nst(256)) &&
+                  tw_count(512, kTwX1) == stage_tw_offset(512, p2_nst(512)),
               "stage twiddle counts");
+static_assert(tw_count(64, kTwStrided) == strided_tw_offset(64, p2_nst(64)) &&
+                  tw_count(128, kTwStrided) == strided_tw_offset(128, p2_nst(128)) &&
+                  tw_count(256, kTwStrided) == strided_tw_offset(256, p2_nst(256)) &&
+                  tw_count(512, kTwStrided) == strided_tw_offset(512, p2_nst(512)),
+              "strided twiddle counts");
 
 template <int R, typename T2>
 __device__ __forceinline__ void dft_fixed(T2* v, bool inv) {
@@ -342,7 +363,6 @@ __device__ __forceinline__ void p2_stage_ct(T2* buf, int nblk, const T2* tw) {
   constexpr int M = p2_msize(L, S);
   constexpr int MR = M / R;
   constexpr int NB = L / R;
-  constexpr int TSTR = L / M;
   constexpr int BS = (PAD ? padded_rows(L) : L) * C;
   const int nbf = nblk * NB;
   const int total = nbf * NCOLS;
@@ -480,6 +500,91 @@ __device__ void tile_fft_rt(T2* buf, int nblk, int BS, int C, int ncols, const A
     case 1024: tile_fft_p2<1024>(buf, nblk, BS, C, ncols, tw, inv, pad); return;
     default: tile_fft_generic(buf, nblk, BS, C, ncols, p, tw, inv, pad); return;
   }
+}
+
+// Stage S of the length-L transform on a strided tile (x2 / x3 passes): one
+// block of L rows of C columns, row stride C, NT threads.  Item it = tid + k NT
+// is butterfly it / C of column it % C; consecutive threads take consecutive
+// columns, so a warp's loads and stores cover contiguous shared memory.  The
+// trip count is a compile-time constant, and the butterfly j = 0 multiplies by
+// the unit twiddles of its row instead of branching.
+template <int L, int S, int C, int NT, bool INV, typename T2>
+__device__ __forceinline__ void strided_stage(T2* __restrict__ buf, const T2* __restrict__ tw) {
+  constexpr int R = p2_radix(L, S);
+  constexpr int M = p2_msize(L, S);
+  constexpr int MR = M / R;
+  constexpr int NB = L / R;
+  constexpr int ITEMS = NB * C;
+  constexpr int K = (ITEMS + NT - 1) / NT;
+  constexpr int TWO = strided_tw_offset(L, S);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int it = (int)threadIdx.x + k * NT;
+    if ((ITEMS % NT) != 0 && it >= ITEMS) break;
+    const int bf = it / C;
+    const int c = it - bf * C;
+    const int j = bf & (MR - 1);
+    T2* base = buf + ((bf / MR) * M + j) * C + c;
+    T2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = base[r * MR * C];
+    if (!INV) {
+      dft_fixed<R>(v, false);
+      if (MR > 1) {
+        T2 w[R];
+        load_tw_row<R>(tw + TWO + j * srow(R), w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r - 1]);
+      }
+    } else {
+      if (MR > 1) {
+        T2 w[R];
+        load_tw_row<R>(tw + TWO + j * srow(R), w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], w[r - 1]);
+      }
+      dft_fixed<R>(v, true);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[r * MR * C] = v[r];
+  }
+  __syncthreads();
+}
+
+template <int L, int C, int NT, bool INV, typename T2>
+__device__ __forceinline__ void strided_fft(T2* buf, const T2* tw) {
+  constexpr int NST = p2_nst(L);
+  if (!INV) {
+    if constexpr (NST > 0) strided_stage<L, 0, C, NT, false>(buf, tw);
+    if constexpr (NST > 1) strided_stage<L, 1, C, NT, false>(buf, tw);
+    if constexpr (NST > 2) strided_stage<L, 2, C, NT, false>(buf, tw);
+    if constexpr (NST > 3) strided_stage<L, 3, C, NT, false>(buf, tw);
+  } else {
+    if constexpr (NST > 3) strided_stage<L, 3, C, NT, true>(buf, tw);
+    if constexpr (NST > 2) strided_stage<L, 2, C, NT, true>(buf, tw);
+    if constexpr (NST > 1) strided_stage<L, 1, C, NT, true>(buf, tw);
+    if constexpr (NST > 0) strided_stage<L, 0, C, NT, true>(buf, tw);
+  }
+}
+
+// In-place transform of a strided tile (x2 / x3 passes): the compile-time
+// lengths run strided_fft (twiddles in the kTwStrided layout), any other length
+// the run-time paths (plain table).  All C columns are transformed.
+// A tile of L rows of C columns fits the 227 KB of shared memory of a block (the
+// compile-time stages are generated only for tiles that can run).
+template <typename T2>
+__host__ __device__ constexpr bool strided_fits(int L, int C) { return (long long)L * C * (long long)sizeof(T2) <= 232448; }
+
+template <int C, int NT, bool INV, typename T2>
+__device__ void tile_fft_strided(T2* buf, const AxisPlan& p, const T2* tw) {
+  switch (p.L) {
+    case 64: if constexpr (strided_fits<T2>(64, C)) { strided_fft<64, C, NT, INV>(buf, tw); return; } break;
+    case 128: if constexpr (strided_fits<T2>(128, C)) { strided_fft<128, C, NT, INV>(buf, tw); return; } break;
+    case 256: if constexpr (strided_fits<T2>(256, C)) { strided_fft<256, C, NT, INV>(buf, tw); return; } break;
+    case 512: if constexpr (strided_fits<T2>(512, C)) { strided_fft<512, C, NT, INV>(buf, tw); return; } break;
+    default: break;
+  }
+  tile_fft_rt(buf, 1, 0, C, C, p, tw, INV, 0);
 }
 
 // tile_fft with the tile geometry fixed at compile time (row stride C complex

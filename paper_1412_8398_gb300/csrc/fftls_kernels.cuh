@@ -99,6 +99,8 @@ struct IterArgs {
   T2* specB;         // AoS [modes][n_c]: sigma_hat (dual)
   const T2* tw[3];   // per axis: e^{-2 pi i t / L}
   const KTab<T>* kt[3];
+  const T2* rd[3];     // per axis, by storage position: {a, b} with kr_i = a_i prod_{m != i} b_m
+                       // (G^R: a = 2 sin(q/2), b = cos(q/2); G^C: a = sin q, b = 1; G: a = q, b = 1)
   const int* perm[3];  // per axis: storage position -> frequency index
   const int* pos[3];   // per axis: frequency index -> storage position
   AxisPlan pl[3];
@@ -123,6 +125,11 @@ struct IterArgs {
   int e_planes, e_blocks;  // real-space eta: x3-planes per block, blocks (tiles x slabs)
   size_t e_smem;
 };
+
+// Threads per block of the strided (x2 / x3) passes with W modes per tile: a
+// compile-time count, so that every stage of the tile transforms has a fixed
+// trip count.
+__host__ __device__ constexpr int strided_threads(int W) { return W == 1 ? 128 : 256; }
 
 // Launchers (fftls_kernels.cu).  All return cudaGetLastError().
 template <typename T> cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s);

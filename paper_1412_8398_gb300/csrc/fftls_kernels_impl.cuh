@@ -98,13 +98,13 @@ __device__ void block_max(double (&v)[W]) {
   __syncthreads();
 }
 
-// Dynamic shared memory: twiddles of the transformed axis (tw_count(L, staged)
-// entries, see tile_fft_ct), then the tile.
+// Dynamic shared memory: twiddles of the transformed axis (tw_count(L, layout)
+// entries: kTwX1 for the x1 tiles, kTwStrided for the x2 / x3 tiles), then the tile.
 template <typename T2>
-__device__ __forceinline__ T2* load_twiddles(const T2* __restrict__ tw, int L, bool staged, T2** tile) {
+__device__ __forceinline__ T2* load_twiddles(const T2* __restrict__ tw, int L, int layout, T2** tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* tws = reinterpret_cast<T2*>(smem_raw);
-  const int n = tw_count(L, staged);
+  const int n = tw_count(L, layout);
   for (int t = threadIdx.x; t < n; t += blockDim.x) tws[t] = tw[t];
   *tile = tws + n;
   __syncthreads();
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
   const Geom g = a.g;
   const int L1 = g.n1, H = g.H;
   T2* tile;
-  const T2* tws = load_twiddles(a.tw[0], L1, true, &tile);
+  const T2* tws = load_twiddles(a.tw[0], L1, kTwX1, &tile);
   constexpr int nout = DUAL ? 2 * NC : NC;
   constexpr int NP = (nout + 1) / 2;
   constexpr int CP = odd_stride(NP);
@@ -477,15 +477,18 @@ __global__ void __launch_bounds__(kEThreads) k_eta_stencil(IterArgs<T> a) {
 // ---------------------------------------------------------------------------
 // W: modes per tile (a compile-time tile geometry; the last tile along x1 may
 // hold fewer modes, its other columns are transformed but never stored).
+// Blocks of strided_threads(W) threads (a compile-time count for the stages).
+
 template <typename T, int NC, int W>
-__global__ void __launch_bounds__(512) k_mid_y(IterArgs<T> a, int inv) {
+__global__ void __launch_bounds__(strided_threads(W)) k_mid_y(IterArgs<T> a, int inv) {
   typedef typename Cplx<T>::type T2;
+  constexpr int NT = strided_threads(W);
   const int st = a.ctrl->state;
   if (inv ? (st != kRunning && st != kLast) : (st != kRunning)) return;
   const Geom g = a.g;
   const int n2 = g.n2;
   T2* tile;
-  const T2* tws = load_twiddles(a.tw[1], n2, false, &tile);
+  const T2* tws = load_twiddles(a.tw[1], n2, kTwStrided, &tile);
   const int x0 = blockIdx.x * W;
   const int nx = min(W, g.H - x0);
   constexpr int C = W * NC;
@@ -494,7 +497,8 @@ __global__ void __launch_bounds__(512) k_mid_y(IterArgs<T> a, int inv) {
   const long long base = ((long long)blockIdx.y * n2 * g.H + x0) * NC;
   const long long rstride = (long long)g.H * NC;
   tile_load<C>(tile, spec + base, rstride, n2, cols);
-  tile_fft_ct<C, C, false>(tile, 1, 0, a.pl[1], tws, inv != 0);
+  if (inv) tile_fft_strided<C, NT, true>(tile, a.pl[1], tws);
+  else tile_fft_strided<C, NT, false>(tile, a.pl[1], tws);
   tile_store<C>(tile, spec + base, rstride, n2, cols);
 }
 
@@ -729,15 +733,94 @@ __device__ __forceinline__ void fourier_mode(const IterArgs<T>& a, int x, int y,
   for (int c = 0; c < NC; ++c) X[c] = E[c];
 }
 
-template <typename T, int DIM, int W>
-__global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
+// Reciprocal of a positive scalar: correctly rounded in float (__frcp_rn), a
+// plain division in double.
+__device__ __forceinline__ float recip_pos(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_pos(double x) { return 1.0 / x; }
+
+// e_hat = -G'(k) : tau_hat / N at one mode of the real-direction operators
+// G^C / G^R (3D), k = phase * i * kr with kr real (the phase cancels, eq. green0b
+// at direction kr): with V_j = tau_ij kr_i, S = kr . V, K2 = |kr|^2,
+// U_i = V_i - kr_i c0 S / K2 and f = -1 / (N mu0 K2),
+//   e_ij = f (kr_i U_j + kr_j U_i) / 2,      c0 = (lambda0 + mu0) / (lambda0 + 2 mu0),
+// and 0 where K2 = 0 (the modes of eq. mulfix and of the rule G^R = 0 where two
+// q_i = pi; q = 0 is set by the caller).
+template <typename T, typename T2>
+__device__ __forceinline__ void green_rd_mode(T2 (&X)[6], T k0, T k1, T k2, T cf, T c0) {
+  const T K2 = k0 * k0 + k1 * k1 + k2 * k2;
+  const T iK2 = K2 > (T)0 ? recip_pos(K2) : (T)0;
+  T2 V[3];
+  V[0].x = X[0].x * k0 + X[5].x * k1 + X[4].x * k2;
+  V[0].y = X[0].y * k0 + X[5].y * k1 + X[4].y * k2;
+  V[1].x = X[5].x * k0 + X[1].x * k1 + X[3].x * k2;
+  V[1].y = X[5].y * k0 + X[1].y * k1 + X[3].y * k2;
+  V[2].x = X[4].x * k0 + X[3].x * k1 + X[2].x * k2;
+  V[2].y = X[4].y * k0 + X[3].y * k1 + X[2].y * k2;
+  const T hs = c0 * iK2;
+  const T Sx = (k0 * V[0].x + k1 * V[1].x + k2 * V[2].x) * hs;
+  const T Sy = (k0 * V[0].y + k1 * V[1].y + k2 * V[2].y) * hs;
+  const T kr[3] = {k0, k1, k2};
+  T2 U[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    U[i].x = V[i].x - kr[i] * Sx;
+    U[i].y = V[i].y - kr[i] * Sy;
+  }
+  const T f = cf * iK2;
+  const T fk[3] = {f * k0, f * k1, f * k2};
+  const T h = (T)0.5;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    X[i].x = fk[i] * U[i].x;
+    X[i].y = fk[i] * U[i].y;
+  }
+  X[3].x = h * (fk[1] * U[2].x + fk[2] * U[1].x);
+  X[3].y = h * (fk[1] * U[2].y + fk[2] * U[1].y);
+  X[4].x = h * (fk[0] * U[2].x + fk[2] * U[0].x);
+  X[4].y = h * (fk[0] * U[2].y + fk[2] * U[0].y);
+  X[5].x = h * (fk[0] * U[1].x + fk[1] * U[0].x);
+  X[5].y = h * (fk[0] * U[1].y + fk[1] * U[0].y);
+}
+
+// Six complex values of one mode between registers and the tile (16-byte accesses;
+// a mode starts on a 48-byte (float) or 96-byte (double) boundary).
+__device__ __forceinline__ void load_mode6(const float2* p, float2 (&X)[6]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float4 t = q[i];
+    X[2 * i] = make_float2(t.x, t.y);
+    X[2 * i + 1] = make_float2(t.z, t.w);
+  }
+}
+__device__ __forceinline__ void store_mode6(float2* p, const float2 (&X)[6]) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) q[i] = make_float4(X[2 * i].x, X[2 * i].y, X[2 * i + 1].x, X[2 * i + 1].y);
+}
+__device__ __forceinline__ void load_mode6(const double2* p, double2 (&X)[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) X[i] = p[i];
+}
+__device__ __forceinline__ void store_mode6(double2* p, const double2 (&X)[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) p[i] = X[i];
+}
+
+// FAST: 3D G^C / G^R with eta from the real-space stencil (only tau is
+// transformed, no eta here): the modes take green_rd_mode with the per-axis
+// factors of rd (by storage position), kr_1 = a_1 b_2 b_3, kr_2 = b_1 a_2 b_3,
+// kr_3 = b_1 b_2 a_3.  Otherwise the general fourier_mode.
+template <typename T, int DIM, int W, bool FAST>
+__global__ void __launch_bounds__(strided_threads(W)) k_fourier_z(IterArgs<T> a) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
+  constexpr int NT = strided_threads(W);
   if (a.ctrl->state != kRunning) return;
   const Geom g = a.g;
   const int n3 = g.n3;
   T2* tile;
-  const T2* tws = load_twiddles(a.tw[2], n3, false, &tile);
+  const T2* tws = load_twiddles(a.tw[2], n3, kTwStrided, &tile);
   const int x0 = blockIdx.x * W;
   const int py = blockIdx.y;
   const int kind = blockIdx.z;
@@ -749,30 +832,54 @@ __global__ void __launch_bounds__(512) k_fourier_z(IterArgs<T> a) {
   T2* spec = kind ? a.specB : a.specA;
   const long long base = ((long long)py * g.H + x0) * NC;
   const long long zstride = (long long)g.n2 * g.H * NC;
-  FastDiv fnx = {0u, 0u, 1};  // full tiles (nx == W) divide by the compile-time width
-  if (nx != W) fnx = make_fastdiv(nx);
   tile_load<C>(tile, spec + base, zstride, n3, cols);
-  const int ym = __ldg(&a.perm[1][py]);
-  tile_fft_ct<C, C, false>(tile, 1, 0, a.pl[2], tws, false);
+  tile_fft_strided<C, NT, false>(tile, a.pl[2], tws);
   T eta_acc = (T)0;
-  for (int idx = threadIdx.x; idx < n3 * nx; idx += blockDim.x) {
-    const int pz = nx == W ? (int)((unsigned)idx / W) : fdiv(idx, fnx), xc = idx - pz * nx;
-    const int zm = __ldg(&a.perm[2][pz]);
-    T2* mp = tile + pz * C + xc * NC;
-    T2 X[NC];
+  if constexpr (FAST) {
+    static_assert(DIM == 3 && NT % W == 0, "fast Fourier pass: 3D, whole modes per thread");
+    const int xc = (int)threadIdx.x % W;
+    if (xc < nx) {
+      const T2 rx = a.rd[0][x0 + xc], ry = a.rd[1][py];
+      const T cf = (T)(-1.0 / ((double)g.N * a.mu0));
+      const T c0 = (T)((a.lam0 + a.mu0) / (a.lam0 + 2.0 * a.mu0));
+      const T bxy = rx.y * ry.y, axy = rx.x * ry.y, bxay = rx.y * ry.x;
+      const bool line0 = (x0 + xc == 0) && (py == 0);
+      for (int pz = (int)threadIdx.x / W; pz < n3; pz += NT / W) {
+        const T2 rz = __ldg(&a.rd[2][pz]);
+        T2* mp = tile + pz * C + xc * NC;
+        T2 X[6];
+        load_mode6(mp, X);
+        green_rd_mode<T>(X, axy * rz.y, bxay * rz.y, bxy * rz.x, cf, c0);
+        if (line0 && pz == 0) {
 #pragma unroll
-    for (int c = 0; c < NC; ++c) X[c] = mp[c];
-    // the FP64 divergence kept for correction phases is indexed by frequency, not by
-    // storage position
-    const long long mfreq = ((long long)zm * g.n2 + ym) * g.H + x0 + xc;
-    fourier_mode<T, DIM>(a, x0 + xc, ym, zm, mfreq, X, do_green, do_eta, eta_acc);
-    if (do_green)
+          for (int c = 0; c < 6; ++c) { X[c].x = a.corr ? (T)0 : (T)a.eps_bar[c]; X[c].y = (T)0; }
+        }
+        store_mode6(mp, X);
+      }
+    }
+  } else {
+    FastDiv fnx = {0u, 0u, 1};  // full tiles (nx == W) divide by the compile-time width
+    if (nx != W) fnx = make_fastdiv(nx);
+    const int ym = __ldg(&a.perm[1][py]);
+    for (int idx = threadIdx.x; idx < n3 * nx; idx += blockDim.x) {
+      const int pz = nx == W ? (int)((unsigned)idx / W) : fdiv(idx, fnx), xc = idx - pz * nx;
+      const int zm = __ldg(&a.perm[2][pz]);
+      T2* mp = tile + pz * C + xc * NC;
+      T2 X[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) mp[c] = X[c];
+      for (int c = 0; c < NC; ++c) X[c] = mp[c];
+      // the FP64 divergence kept for correction phases is indexed by frequency, not by
+      // storage position
+      const long long mfreq = ((long long)zm * g.n2 + ym) * g.H + x0 + xc;
+      fourier_mode<T, DIM>(a, x0 + xc, ym, zm, mfreq, X, do_green, do_eta, eta_acc);
+      if (do_green)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) mp[c] = X[c];
+    }
   }
   __syncthreads();
   if (do_green) {
-    tile_fft_ct<C, C, false>(tile, 1, 0, a.pl[2], tws, true);
+    tile_fft_strided<C, NT, true>(tile, a.pl[2], tws);
     tile_store<C>(tile, spec + base, zstride, n3, cols);
   }
   if (!a.eta_real) {  // with the real-space eta the x1 pass owns part_eta
@@ -861,7 +968,7 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
   const Geom g = a.g;
   const int L1 = g.n1, H = g.H;
   T2* tile;
-  const T2* tws = load_twiddles(a.tw[0], L1, true, &tile);
+  const T2* tws = load_twiddles(a.tw[0], L1, kTwX1, &tile);
   const int BS = padded_rows(L1) * CP;
   const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
@@ -1100,7 +1207,7 @@ template <typename T>
 cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s) {
   if (a.g.n2 == 1) return cudaSuccess;
   dim3 grid((a.g.H + a.y_w - 1) / a.y_w, a.g.n3, (!inv && a.dual && !a.eta_real) ? 2 : 1);
-#define FFTLS_MIDY(NCV, WV) k_mid_y<T, NCV, WV><<<grid, a.y_threads, a.y_smem, s>>>(a, inv ? 1 : 0)
+#define FFTLS_MIDY(NCV, WV) k_mid_y<T, NCV, WV><<<grid, strided_threads(WV), a.y_smem, s>>>(a, inv ? 1 : 0)
 #define FFTLS_MIDY_W(NCV)                                                                               \
   switch (a.y_w) {                                                                                      \
     case 1: FFTLS_MIDY(NCV, 1); break;                                                                  \
@@ -1117,21 +1224,31 @@ cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The fast Fourier pass serves 3D G^C / G^R when eta comes from the real-space stencil.
+template <typename T>
+bool fourier_fast(const IterArgs<T>& a) {
+  return a.dim == 3 && a.eta_real && (a.green == kCentered || a.green == kRotated);
+}
+
 template <typename T>
 cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s) {
   dim3 grid((a.g.H + a.z_w - 1) / a.z_w, a.g.n2, (a.dual && !a.eta_real) ? 2 : 1);
-#define FFTLS_FZ(D, WV) k_fourier_z<T, D, WV><<<grid, a.z_threads, a.z_smem, s>>>(a)
-#define FFTLS_FZ_W(D)                                                                                   \
+#define FFTLS_FZ(D, WV, F) k_fourier_z<T, D, WV, F><<<grid, strided_threads(WV), a.z_smem, s>>>(a)
+#define FFTLS_FZ_W(D, F)                                                                                \
   switch (a.z_w) {                                                                                      \
-    case 1: FFTLS_FZ(D, 1); break;                                                                      \
-    case 2: FFTLS_FZ(D, 2); break;                                                                      \
-    case 4: FFTLS_FZ(D, 4); break;                                                                      \
-    case 8: FFTLS_FZ(D, 8); break;                                                                      \
-    case 16: FFTLS_FZ(D, 16); break;                                                                    \
+    case 1: FFTLS_FZ(D, 1, F); break;                                                                   \
+    case 2: FFTLS_FZ(D, 2, F); break;                                                                   \
+    case 4: FFTLS_FZ(D, 4, F); break;                                                                   \
+    case 8: FFTLS_FZ(D, 8, F); break;                                                                   \
+    case 16: FFTLS_FZ(D, 16, F); break;                                                                 \
     default: return cudaErrorInvalidValue;                                                              \
   }
-  if (a.dim == 3) { FFTLS_FZ_W(3) }
-  else { FFTLS_FZ_W(2) }
+  if (a.dim == 3) {
+    if (fourier_fast(a)) { FFTLS_FZ_W(3, true) }
+    else { FFTLS_FZ_W(3, false) }
+  } else {
+    FFTLS_FZ_W(2, false)
+  }
 #undef FFTLS_FZ_W
 #undef FFTLS_FZ
   return cudaGetLastError();
@@ -1184,16 +1301,21 @@ cudaError_t set_attrs_y(size_t smax) {
 template <typename T>
 cudaError_t set_attrs_z(size_t smax) {
   cudaError_t e = cudaSuccess;
-  FFTLS_ATTR((k_fourier_z<T, 3, 1>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 2>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 4>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 8>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 16>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 1>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 2>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 4>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 8>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 16>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 1, false>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 2, false>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 4, false>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 8, false>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 16, false>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 1, true>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 2, true>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 4, true>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 8, true>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 16, true>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 1, false>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 2, false>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 4, false>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 8, false>));
+  FFTLS_ATTR((k_fourier_z<T, 2, 16, false>));
   return e;
 }
 

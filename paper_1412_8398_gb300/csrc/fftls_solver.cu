@@ -103,11 +103,15 @@ void plan_permutation(const AxisPlan& p, int* perm, int* pos) {
 }
 
 // Twiddles w^t = e^{-2 pi i t / L} (exact at multiples of pi/2) in the layout
-// tile_fft_ct reads (tw_count(L, staged) complex values: rows per stage for the
-// compile-time lengths when staged, else w^t by t) and the wave-vector table
-// {q, sin q, cos q - 1, sin q/2, cos q/2, nyquist} by frequency index.
-void axis_tables(int L, bool staged, double* tw, double* kt) {
-  static_assert(fftls::tw_count(512, true) <= kMaxL + 2, "stage twiddle rows fit the plain table's bound");
+// the tile transforms read (tw_count(L, layout) complex values: the plain table
+// w^t by t, or rows per stage for the compile-time lengths, kTwX1 for the x1
+// tiles and kTwStrided, with padded rows, for the x2 / x3 tiles), the
+// wave-vector table {q, sin q, cos q - 1, sin q/2, cos q/2, nyquist} by frequency
+// index, and the real-direction factors {a, b} of operator `green` by storage
+// position p (frequency perm[p]; perm = NULL: natural order): kr_i = a_i prod_{m != i} b_m, with
+// G^R: a = 2 sin(q/2), b = cos(q/2);  G^C: a = sin q, b = 1;  G: a = q, b = 1.
+void axis_tables(int L, int layout, int green, const int* perm, double* tw, double* kt, double* rd) {
+  static_assert(fftls::tw_count(512, fftls::kTwStrided) <= kMaxL + 2, "stage twiddle rows fit the plain table's bound");
   double plain[2 * kMaxL];
   for (int t = 0; t < L; ++t) {
     const double ang = -2.0 * M_PI * (double)t / (double)L;
@@ -121,18 +125,21 @@ void axis_tables(int L, bool staged, double* tw, double* kt) {
     plain[2 * t] = cs;
     plain[2 * t + 1] = sn;
   }
-  const int ntw = fftls::tw_count(L, staged);
+  const int ntw = fftls::tw_count(L, layout);
   for (int t = 0; t < 2 * ntw; ++t) tw[t] = t < 2 * L ? plain[t] : 0.0;
-  if (staged && fftls::ct_length(L)) {
+  if (layout != fftls::kTwPlain && fftls::ct_length(L)) {
     for (int t = 0; t < 2 * ntw; ++t) tw[t] = 0.0;
     for (int st = 0; st < fftls::p2_nst(L); ++st) {
       const int R = fftls::p2_radix(L, st), M = fftls::p2_msize(L, st), MR = M / R, T = L / M;
       if (MR == 1) continue;
-      double* rows = tw + 2 * (size_t)fftls::stage_tw_offset(L, st);
+      const int row = layout == fftls::kTwX1 ? R : fftls::srow(R);
+      const size_t off = layout == fftls::kTwX1 ? (size_t)fftls::stage_tw_offset(L, st)
+                                                : (size_t)fftls::strided_tw_offset(L, st);
+      double* rows = tw + 2 * off;
       for (int j = 0; j < MR; ++j)
         for (int r = 1; r < R; ++r) {
-          rows[2 * (j * R + r - 1)] = plain[2 * (r * j * T)];
-          rows[2 * (j * R + r - 1) + 1] = plain[2 * (r * j * T) + 1];
+          rows[2 * (j * row + r - 1)] = plain[2 * (r * j * T)];
+          rows[2 * (j * row + r - 1) + 1] = plain[2 * (r * j * T) + 1];
         }
     }
   }
@@ -152,6 +159,15 @@ void axis_tables(int L, bool staged, double* tw, double* kt) {
     e[3] = sh;
     e[4] = ch;
     e[5] = (L % 2 == 0 && 2 * m == L) ? 1.0 : 0.0;
+  }
+  for (int p = 0; p < L; ++p) {
+    const double* e = kt + 6 * (size_t)(perm ? perm[p] : p);
+    double av = 0.0, bv = 1.0;
+    if (green == FFTLS_GREEN_R) { av = 2.0 * e[3]; bv = e[4]; }
+    else if (green == FFTLS_GREEN_C) av = e[1];
+    else if (green == FFTLS_GREEN_MS) av = e[0];
+    rd[2 * (size_t)p] = av;
+    rd[2 * (size_t)p + 1] = bv;
   }
 }
 
@@ -341,27 +357,40 @@ void coef_table(const Setup& S, const fftls_problem* p, double* cf) {
   }
 }
 
-// Table block per precision: per axis twiddles (tw_count(L, ax == 0) complex: the x1
-// axis in the stage layout) then k tables (L x 6).
+// Table block per precision: per axis twiddles (tw_count(L, tw_layout(ax))
+// complex), the k table (L x 6) and the real-direction factors (L x 2).
+int tw_layout(int ax) { return ax == 0 ? fftls::kTwX1 : fftls::kTwStrided; }
+size_t axis_table_count(int L, int ax) { return 2 * (size_t)fftls::tw_count(L, tw_layout(ax)) + 8 * (size_t)L; }
 size_t table_offset_tw(const Setup& S, int ax) {
   size_t off = 0;
-  for (int a = 0; a < ax; ++a) off += 2 * (size_t)fftls::tw_count(S.pl[a].L, a == 0) + 6 * (size_t)S.pl[a].L;
+  for (int a = 0; a < ax; ++a) off += axis_table_count(S.pl[a].L, a);
   return off;
 }
 size_t table_offset_kt(const Setup& S, int ax) {
-  return table_offset_tw(S, ax) + 2 * (size_t)fftls::tw_count(S.pl[ax].L, ax == 0);
+  return table_offset_tw(S, ax) + 2 * (size_t)fftls::tw_count(S.pl[ax].L, tw_layout(ax));
 }
+size_t table_offset_rd(const Setup& S, int ax) { return table_offset_kt(S, ax) + 6 * (size_t)S.pl[ax].L; }
 size_t table_count(const Setup& S) { return table_offset_tw(S, 3); }
+
+// Fill the table block (tab) and the per-axis permutations (perms: storage position ->
+// frequency, then frequency -> position, per axis).  No heap allocation (the
+// allocation-free entry point stages its tables through here).
+void fill_tables(const Setup& S, double* tab, int* perms) {
+  size_t po = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const int L = S.pl[ax].L;
+    plan_permutation(S.pl[ax], &perms[po], &perms[po + L]);
+    // x1: the half spectrum is stored in natural order (the rd table is by frequency)
+    axis_tables(L, tw_layout(ax), S.green, ax == 0 ? nullptr : &perms[po], &tab[table_offset_tw(S, ax)],
+                &tab[table_offset_kt(S, ax)], &tab[table_offset_rd(S, ax)]);
+    po += 2 * (size_t)L;
+  }
+}
 
 void build_tables(const Setup& S, std::vector<double>& tab, std::vector<int>& perms) {
   tab.assign(table_count(S), 0.0);
   perms.assign(2 * (size_t)(S.pl[0].L + S.pl[1].L + S.pl[2].L), 0);
-  size_t po = 0;
-  for (int ax = 0; ax < 3; ++ax) {
-    axis_tables(S.pl[ax].L, ax == 0, &tab[table_offset_tw(S, ax)], &tab[table_offset_kt(S, ax)]);
-    plan_permutation(S.pl[ax], &perms[po], &perms[po + S.pl[ax].L]);
-    po += 2 * (size_t)S.pl[ax].L;
-  }
+  fill_tables(S, tab.data(), perms.data());
 }
 
 // Launch shapes for precision T; false if a size does not fit in shared memory.
@@ -378,7 +407,7 @@ PlanGeom plan_geom(const Setup& S, size_t cb, bool real_eta) {
   const int nc = S.nc;
   G.cb = cb;
   G.lim = (size_t)S.smem_optin - 4096;  // static reduction arrays
-  G.twx = (size_t)fftls::tw_count(S.g.n1, true) * cb;
+  G.twx = (size_t)fftls::tw_count(S.g.n1, fftls::kTwX1) * cb;
   G.line1 = (size_t)padded_rows(S.g.n1) * odd_up(real_eta ? (nc + 1) / 2 : nc) * cb;
   G.line5 = (size_t)padded_rows(S.g.n1) * odd_up((nc + 1) / 2) * cb;
   G.nlines = (long long)S.g.n2 * S.g.n3;
@@ -386,7 +415,9 @@ PlanGeom plan_geom(const Setup& S, size_t cb, bool real_eta) {
   return G;
 }
 
-size_t strided_smem(int L, int w, int nc, size_t cb) { return (size_t)fftls::tw_count(L, false) * cb + (size_t)L * w * nc * cb; }
+size_t strided_smem(int L, int w, int nc, size_t cb) {
+  return (size_t)fftls::tw_count(L, fftls::kTwStrided) * cb + (size_t)L * w * nc * cb;
+}
 
 // Built-in schedule: x1 tiles of about 32 KB (64 KB for the two-field forward
 // tile), x2/x3 tiles of at most 16 modes and about 100 KB, eta slabs of up to 32
@@ -437,8 +468,8 @@ bool apply_plan(const Setup& S, IterArgs<T>& a, bool real_eta, const TilePlan& P
   if (a.y_smem > G.lim || a.z_smem > G.lim) return false;
   a.y_w = P.y_w;
   a.z_w = P.z_w;
-  a.y_threads = P.y_thr ? P.y_thr : ((long long)g.n2 * a.y_w * S.nc >= 4096 ? 512 : 256);
-  a.z_threads = P.z_thr ? P.z_thr : ((long long)g.n3 * a.z_w * S.nc >= 4096 ? 512 : 256);
+  a.y_threads = fftls::strided_threads(a.y_w);
+  a.z_threads = fftls::strided_threads(a.z_w);
   a.e_planes = a.e_blocks = 0;
   a.e_smem = 0;
   if (real_eta) {
@@ -700,13 +731,12 @@ fftls_status tune_plan(fftls_ctx* c, const Setup& S, IterArgs<T>& a, bool real_e
     P.x1_vb = bv;
     apply_plan<T>(S, a, real_eta, P);
   }
-  // strided passes: tile width and block size searched jointly (a narrow tile with
-  // small blocks puts more independent blocks on an SM)
+  // strided passes: tile width (the block size follows from it, strided_threads)
   auto search_wt = [&](int TilePlan::*wf, int TilePlan::*tf, LaunchFn fn) {
     float best = INFINITY;
     int bw = P.*wf, bt = P.*tf;
     for (int w : widths)
-      for (int thr : {256, 512}) {
+      for (int thr : {fftls::strided_threads(w)}) {
         if (err != cudaSuccess) return;
         TilePlan Q = P;
         Q.*wf = w;
@@ -782,6 +812,7 @@ fftls_status prepare(fftls_ctx* c, const Setup& S, const fftls_problem* p, const
   for (int ax = 0; ax < 3; ++ax) {
     a.tw[ax] = (const T2*)((const T*)tb.p + table_offset_tw(S, ax));
     a.kt[ax] = (const KTab<T>*)((const T*)tb.p + table_offset_kt(S, ax));
+    a.rd[ax] = (const T2*)((const T*)tb.p + table_offset_rd(S, ax));
     a.perm[ax] = d_perms + po;
     a.pos[ax] = d_perms + po + S.pl[ax].L;
     po += 2 * (size_t)S.pl[ax].L;
@@ -1326,7 +1357,7 @@ void* g_noalloc_base[kNoAllocMaxDevices];  // device address of g_noalloc_scratc
 // so the arrays are free again when the lock is released)
 std::mutex g_na_lock;
 double g_na_coef[256 * kCoef];
-double g_na_tab[3 * (2 * (kMaxL + 2) + 6 * kMaxL)];
+double g_na_tab[3 * (2 * (kMaxL + 2) + 8 * kMaxL)];
 int g_na_perm[6 * kMaxL];
 
 size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1395,11 +1426,7 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
     std::lock_guard<std::mutex> lk(g_na_lock);
     coef_table(S, p, g_na_coef);
     NA_TRY(cudaMemcpyAsync(base + o_coef, g_na_coef, sizeof(g_na_coef), cudaMemcpyHostToDevice, S.s));
-    for (int ax = 0; ax < 3; ++ax) {
-      axis_tables(S.pl[ax].L, ax == 0, &g_na_tab[table_offset_tw(S, ax)], &g_na_tab[table_offset_kt(S, ax)]);
-      plan_permutation(S.pl[ax], &g_na_perm[po], &g_na_perm[po + S.pl[ax].L]);
-      po += 2 * (size_t)S.pl[ax].L;
-    }
+    fill_tables(S, g_na_tab, g_na_perm);
     NA_TRY(cudaMemcpyAsync(base + o_tab, g_na_tab, ntab * 8, cudaMemcpyHostToDevice, S.s));
     NA_TRY(cudaMemcpyAsync(base + o_perm, g_na_perm, nperm * sizeof(int), cudaMemcpyHostToDevice, S.s));
   }
@@ -1438,6 +1465,7 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   for (int ax = 0; ax < 3; ++ax) {
     a.tw[ax] = (const double2*)((const double*)(base + o_tab) + table_offset_tw(S, ax));
     a.kt[ax] = (const KTab<double>*)((const double*)(base + o_tab) + table_offset_kt(S, ax));
+    a.rd[ax] = (const double2*)((const double*)(base + o_tab) + table_offset_rd(S, ax));
     a.perm[ax] = (const int*)(base + o_perm) + po;
     a.pos[ax] = (const int*)(base + o_perm) + po + S.pl[ax].L;
     po += 2 * (size_t)S.pl[ax].L;

@@ -3,8 +3,13 @@ full-size properties, against the FP64 oracle or against what holds exactly.
 
 * Ladder: the returned field's eta is recomputed by the oracle (FP64, from the
   field alone) and must be <= tol; moduli agree with the FP64 solve to 1e-6.
-* 2D 128^2 centred disc and 3D 128^3 Boolean spheres (three contrasts): parity
-  with the oracle (fields 1e-9 max-abs, <sigma> 1e-10 relative).
+* 2D 128^2 centred disc: parity with the oracle (fields 1e-9 max-abs, <sigma>
+  1e-10 relative).
+* 3D 128^3 Boolean spheres at three contrasts: every operator under both
+  schemes for two FP64 iterations against the oracle (fields 1e-9 max-abs, eta
+  1e-9 relative), and every operator under the ladder (oracle eta of the
+  returned field <= tol, <sigma> within 1e-6 of FP64); operator G's two-field
+  x1 tile at 64^3.
 * 512^3, the benchmark's launch configuration: a homogeneous medium converges
   in one iteration to eps_bar exactly; a laminate reproduces the exact
   piecewise-constant solution (G^R and G^W are exact for any layer widths).
@@ -13,6 +18,7 @@ import numpy as np
 import pytest
 
 from oracle import fftls_oracle as O
+import _oracle_jobs as _jobs
 from paper_1412_8398_gb300 import microstructure as MS
 
 pytestmark = pytest.mark.gpu
@@ -112,18 +118,73 @@ def test_config_2d_disc(solver):
         assert (asym < 1e-6) if sym else (asym > 1e-3)
 
 
-@pytest.mark.parametrize("contrast", [0.01, 10.0, 1000.0])
-def test_config_128_boolean_parity(solver, contrast):
-    """128^3 Boolean spheres (radius 6, f = 0.3): two iterations of every discretisation agree with the oracle."""
+C2_CHIS = [0.01, 10.0, 1000.0]
+C2_CASES = [(128, 6.0, 0.3, 1, chi, g, sch, 2) for chi in C2_CHIS for g in range(4) for sch in (O.DIRECT, O.ACCELERATED)]
+# operator G with the accelerated scheme at a second compile-time length: its x1 pass carries tau and sigma
+C2_CASES.append((64, 3.0, 0.3, 2, 1000.0, O.MS, O.ACCELERATED, 2))
+
+
+@pytest.fixture(scope="module")
+def c2_oracle():
+    """The oracle on every case of the 128^3 matrix, in spawned worker processes (the parent has a CUDA
+    context; spawn starts clean interpreters)."""
+    import multiprocessing as mp
+    import os
+    workers = max(1, min(8, (os.cpu_count() or 2) - 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        out = {case: (comp, eta) for case, comp, eta in pool.imap_unordered(_jobs.boolean_case, C2_CASES)}
+    return out
+
+
+@pytest.mark.parametrize("contrast", C2_CHIS)
+def test_config_128_boolean_parity(solver, c2_oracle, contrast):
+    """128^3 Boolean spheres (radius 6, f = 0.3, seed 1), contrast chi: two FP64 iterations of every
+    operator under both schemes agree with the oracle element by element (fields 1e-9 max-abs,
+    eta histories 1e-9 relative)."""
     ph, _ = MS.boolean_spheres((128, 128, 128), 6.0, 0.3, seed=1)
     lam, mu = MS.young_poisson_phases([(1.0, 0.3), (contrast, 0.3)])
     eb = np.diag([1.0, 0.0, 0.0])
-    green, scheme = {0.01: (O.ROTATED, O.ACCELERATED), 10.0: (O.WILLOT, O.DIRECT),
-                     1000.0: (O.ROTATED, O.ACCELERATED)}[contrast]
-    ref = O.solve(ph, lam, mu, eb, green, scheme, tol=0.0, max_iter=2)
-    got = solver.solve(ph, lam, mu, eb, GREENS[green], ["DS", "AS"][scheme], tol=0.0, max_iter=2)
-    assert np.abs(got.strain - comps(ref["strain"])).max() < FIELD_TOL
-    np.testing.assert_allclose(got.eta_history, ref["eta_history"], rtol=1e-9)
+    for case in C2_CASES:
+        n, _, _, _, chi, green, scheme, iters = case
+        if n != 128 or chi != contrast:
+            continue
+        comp, eta = c2_oracle[case]
+        got = solver.solve(ph, lam, mu, eb, GREENS[green], ["DS", "AS"][scheme], tol=0.0, max_iter=iters)
+        assert np.abs(got.strain - comp).max() < FIELD_TOL, (GREENS[green], scheme)
+        np.testing.assert_allclose(got.eta_history, eta, rtol=1e-9)
+
+
+def test_config_64_ms_accelerated_parity(solver, c2_oracle):
+    """Operator G under the accelerated scheme at 64^3: the x1 pass transforms tau and sigma together
+    (eta in Fourier space) on the compile-time tile of length 64."""
+    case = C2_CASES[-1]
+    n, radius, fraction, seed, chi, green, scheme, iters = case
+    ph, _ = MS.boolean_spheres((n, n, n), radius, fraction, seed=seed)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (chi, 0.3)])
+    comp, eta = c2_oracle[case]
+    got = solver.solve(ph, lam, mu, np.diag([1.0, 0.0, 0.0]), "MS", "AS", tol=0.0, max_iter=iters)
+    assert np.abs(got.strain - comp).max() < FIELD_TOL
+    np.testing.assert_allclose(got.eta_history, eta, rtol=1e-9)
+
+
+@pytest.mark.parametrize("contrast", C2_CHIS)
+def test_config_128_boolean_ladder(solver, contrast):
+    """128^3 Boolean spheres, every operator with the accelerated scheme under the FP32 -> FP64 ladder
+    to eta <= 1e-6: the oracle recomputes eta from the returned FP64 field (<= tol) and <sigma> agrees
+    with the plain FP64 solve to 1e-6 relative."""
+    ph, _ = MS.boolean_spheres((128, 128, 128), 6.0, 0.3, seed=1)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (contrast, 0.3)])
+    eb = np.diag([1.0, 0.0, 0.0])
+    tol = 1e-6
+    for green in range(4):
+        mix = solver.solve(ph, lam, mu, eb, GREENS[green], "AS", tol=tol, max_iter=5000, precision="fp32_refine64",
+                           want_stress=False)
+        f64 = solver.solve(ph, lam, mu, eb, GREENS[green], "AS", tol=tol, max_iter=5000, precision="fp64",
+                           want_strain=False, want_stress=False, history=False)
+        assert mix.converged and f64.converged
+        assert oracle_eta(ph, lam, mu, mix.strain, green) <= tol * 1.0001
+        rel = np.abs(mix.mean_stress - f64.mean_stress).max() / np.abs(f64.mean_stress).max()
+        assert rel < 1e-6, (GREENS[green], rel)
 
 
 def _laminate_exact(layers, lam, mu, eb):
