@@ -193,16 +193,23 @@ fftls_status fftls_profile(const fftls_ctx* ctx, const char** names, double* tot
 /* Solves `count` independent problems (any mix of supported grid sizes, each
  * with its own phases, moduli, reference medium, operator, scheme and eps_bar)
  * under the shared options `opt`.  opt->eps_init must be NULL; opt->stream, if
- * set, is synchronised before the work starts.  The samples run concurrently on
+ * set, is synchronised before the work starts.  3D samples that share a grid,
+ * an operator and a scheme are solved together: every kernel of the iteration
+ * runs as one grouped launch over them (a sample's blocks read its own control
+ * block, so each stops, switches precision and diverges on its own), in groups
+ * of at most 256 samples and about 24 GB of device memory; every other sample
+ * runs as fftls_solve.  The groups and single samples are spread over
  * `concurrency` worker contexts (0 selects 8, at most 64), each with its own
- * stream, device buffers, CUDA graphs and tile schedules, largest grid first;
- * every sample takes the same path as fftls_solve, so results[i] (caller-owned
- * buffers as in fftls_solve) and statuses[i] (may be NULL) are what fftls_solve
- * would give (bit for bit with opt->autotune = 0).  Returns FFTLS_OK when every
- * sample converged, else the first failing status in sample order, with the
- * sample named in fftls_last_error.  Blocks until all samples are done.  The
- * paper solves one problem at a time; batching serves many-sample studies
- * (its Boolean-model statistics). */
+ * stream, device buffers, CUDA graphs and tile schedules, largest task first.
+ * results[i] (caller-owned buffers as in fftls_solve) and statuses[i] (may be
+ * NULL) are what fftls_solve would give: the same status, iteration counts and
+ * fields (bit for bit with opt->autotune = 0), the eta and <sigma> histories to
+ * within one unit in the last place.  Invalid samples are reported with their
+ * own status and never run.  Returns FFTLS_OK when every sample converged, else
+ * the first failing status in sample order, with the sample named in
+ * fftls_last_error.  Blocks until all samples are done.  The paper solves one
+ * problem at a time; batching serves many-sample studies (its Boolean-model
+ * statistics). */
 fftls_status fftls_solve_batched(fftls_ctx* ctx, const fftls_problem* probs, int count, const fftls_options* opt,
                                  fftls_result* results, fftls_status* statuses, int concurrency);
 

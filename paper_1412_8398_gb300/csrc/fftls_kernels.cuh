@@ -115,6 +115,13 @@ struct IterArgs {
   float* rfield;       // n_c x N defect r (written by kUpdResidual, read by corrections)
   float2* d64;         // [modes][3] by frequency index: k*.sigma_hat of the FP64 iterate (phase-free form), or with
                        // eta_real [3][N] floats: its real-space divergence
+  // grouped launches (fftls_solve_batched): nsmp samples of one 3D geometry share a
+  // launch; sample s finds its fields at these element offsets times s (null fields:
+  // offset 0) and its lambda0, mu0, eps_bar[6] at smp_par[8 s ..] (device memory).
+  // Single solves have nsmp = 1 and use the values above.
+  int nsmp;
+  long long st_field, st_phase, st_spec, st_coef, st_pmean, st_peta, st_pdelta, st_hist, st_d64;
+  const double* smp_par;
   // launch shapes (host-computed)
   int x1_lines, x1_blocks;  // forward x1 pass: lines per batch, blocks (grid-stride over batches)
   int x1_vb;                // forward x1 pass: voxels per thread loaded together (1, 2 or 4)
@@ -130,6 +137,20 @@ struct IterArgs {
 // compile-time count, so that every stage of the tile transforms has a fixed
 // trip count.
 __host__ __device__ constexpr int strided_threads(int W) { return W == 1 ? 128 : 256; }
+
+// Grouped launches (GRP variants, fftls_kernels_{x,y,z}{32,64}g.cu): the same
+// kernels over a.nsmp samples of one 3D geometry; 2D grids are not grouped.
+template <typename T> cudaError_t launch_fwd_x_grp(const IterArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_eta_stencil_grp(const IterArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_mid_y_grp(const IterArgs<T>& a, bool inv, cudaStream_t s);
+template <typename T> cudaError_t launch_fourier_z_grp(const IterArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_reduce_eta_grp(const IterArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_inv_x_grp(const IterArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_reduce_delta_grp(const IterArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t set_attrs_grp(size_t smax);
+template <typename T> cudaError_t set_attrs_xgrp(size_t smax);
+template <typename T> cudaError_t set_attrs_ygrp(size_t smax);
+template <typename T> cudaError_t set_attrs_zgrp(size_t smax);
 
 // Launchers (fftls_kernels.cu).  All return cudaGetLastError().
 template <typename T> cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s);

@@ -31,6 +31,29 @@ namespace fftls {
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
+// The view of sample s of a grouped launch: its fields and parameters.
+template <typename T>
+__device__ __forceinline__ void at_sample(IterArgs<T>& a, int s) {
+  a.eps += s * a.st_field;
+  a.phase += s * a.st_phase;
+  a.coef += s * a.st_coef;
+  a.specA += s * a.st_spec;
+  a.specB += s * a.st_spec;
+  a.ctrl += s;
+  a.part_mean += s * a.st_pmean;
+  a.part_eta += s * a.st_peta;
+  a.part_delta += s * a.st_pdelta;
+  a.eta_hist += s * a.st_hist;
+  a.ms_hist += s * a.st_hist * 6;
+  a.rfield += s * a.st_field;
+  a.d64 += s * a.st_d64;
+  const double* p = a.smp_par + 8 * s;
+  a.lam0 = p[0];
+  a.mu0 = p[1];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) a.eps_bar[i] = p[2 + i];
+}
+
 template <int DIM> struct Comp;
 template <> struct Comp<3> {
   static constexpr int NC = 6;
@@ -200,7 +223,7 @@ __device__ __forceinline__ void tile_store(const T2* tile, T2* g, long long gstr
 // VB: voxels per thread whose loads are issued together (a tuned trade of
 // registers against loads in flight).
 template <typename T, int DIM, bool DUAL, int VB>
-__global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
+__device__ __forceinline__ void k_fwd_x_body(const IterArgs<T>& a, const AxisPlan* pl) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
   if (a.ctrl->state != kRunning) return;
@@ -290,7 +313,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
       const long long ln = l0 + (long long)gridDim.x * G;
       if (ln < nlines) prefetch_voxels<T>(a.eps, a.phase, g.N, NC, ln * L1, (int)min((long long)G, nlines - ln) * L1);
     }
-    tile_fft_ct<CP, NP, true>(tile, nl, BS, a.pl[0], tws, false);
+    tile_fft_ct<CP, NP, true>(tile, nl, BS, pl[0], tws, false);
     for (int idx = threadIdx.x; idx < nl * H * NP; idx += blockDim.x) {
       const int rest = fdiv(idx, fNP);
       const int p = idx - rest * NP;
@@ -314,6 +337,18 @@ __global__ void __launch_bounds__(256) k_fwd_x(IterArgs<T> a) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wacc[w][threadIdx.x];
     a.part_mean[(size_t)blockIdx.x * 2 * NC + threadIdx.x] = t;
+  }
+}
+
+// GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
+template <typename T, int DIM, bool DUAL, int VB, bool GRP>
+__global__ void __launch_bounds__(256) k_fwd_x(const __grid_constant__ IterArgs<T> a_) {
+  if constexpr (GRP) {
+    IterArgs<T> a = a_;
+    at_sample(a, blockIdx.y);
+    k_fwd_x_body<T, DIM, DUAL, VB>(a, a_.pl);
+  } else {
+    k_fwd_x_body<T, DIM, DUAL, VB>(a_, a_.pl);
   }
 }
 
@@ -358,7 +393,7 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 }
 
 template <typename T, bool CEN>
-__global__ void __launch_bounds__(kEThreads) k_eta_stencil(IterArgs<T> a) {
+__device__ __forceinline__ void k_eta_stencil_body(const IterArgs<T>& a, const AxisPlan* pl) {
   if (a.ctrl->state != kRunning) return;
   const Geom g = a.g;
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
@@ -472,6 +507,18 @@ __global__ void __launch_bounds__(kEThreads) k_eta_stencil(IterArgs<T> a) {
   if (threadIdx.x == 0) a.part_eta[blockIdx.x] = e1[0];
 }
 
+// GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
+template <typename T, bool CEN, bool GRP>
+__global__ void __launch_bounds__(kEThreads) k_eta_stencil(const __grid_constant__ IterArgs<T> a_) {
+  if constexpr (GRP) {
+    IterArgs<T> a = a_;
+    at_sample(a, blockIdx.y);
+    k_eta_stencil_body<T, CEN>(a, a_.pl);
+  } else {
+    k_eta_stencil_body<T, CEN>(a_, a_.pl);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K2: transform along x2, in place; tiles of y_w modes x n2 rows x n_c
 // ---------------------------------------------------------------------------
@@ -480,7 +527,7 @@ __global__ void __launch_bounds__(kEThreads) k_eta_stencil(IterArgs<T> a) {
 // Blocks of strided_threads(W) threads (a compile-time count for the stages).
 
 template <typename T, int NC, int W>
-__global__ void __launch_bounds__(strided_threads(W)) k_mid_y(IterArgs<T> a, int inv) {
+__device__ __forceinline__ void k_mid_y_body(const IterArgs<T>& a, const AxisPlan* pl, int inv, int kind) {
   typedef typename Cplx<T>::type T2;
   constexpr int NT = strided_threads(W);
   const int st = a.ctrl->state;
@@ -493,13 +540,26 @@ __global__ void __launch_bounds__(strided_threads(W)) k_mid_y(IterArgs<T> a, int
   const int nx = min(W, g.H - x0);
   constexpr int C = W * NC;
   const int cols = nx * NC;
-  T2* spec = blockIdx.z ? a.specB : a.specA;
+  T2* spec = kind ? a.specB : a.specA;
   const long long base = ((long long)blockIdx.y * n2 * g.H + x0) * NC;
   const long long rstride = (long long)g.H * NC;
   tile_load<C>(tile, spec + base, rstride, n2, cols);
-  if (inv) tile_fft_strided<C, NT, true>(tile, a.pl[1], tws);
-  else tile_fft_strided<C, NT, false>(tile, a.pl[1], tws);
+  if (inv) tile_fft_strided<C, NT, true>(tile, pl[1], tws);
+  else tile_fft_strided<C, NT, false>(tile, pl[1], tws);
   tile_store<C>(tile, spec + base, rstride, n2, cols);
+}
+
+// GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
+template <typename T, int NC, int W, bool GRP>
+__global__ void __launch_bounds__(strided_threads(W)) k_mid_y(const __grid_constant__ IterArgs<T> a_, int inv) {
+  if constexpr (GRP) {
+    const int kinds = gridDim.z / a_.nsmp;
+    IterArgs<T> a = a_;
+    at_sample(a, blockIdx.z / kinds);
+    k_mid_y_body<T, NC, W>(a, a_.pl, inv, (int)(blockIdx.z % kinds));
+  } else {
+    k_mid_y_body<T, NC, W>(a_, a_.pl, inv, (int)blockIdx.z);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -812,7 +872,7 @@ __device__ __forceinline__ void store_mode6(double2* p, const double2 (&X)[6]) {
 // factors of rd (by storage position), kr_1 = a_1 b_2 b_3, kr_2 = b_1 a_2 b_3,
 // kr_3 = b_1 b_2 a_3.  Otherwise the general fourier_mode.
 template <typename T, int DIM, int W, bool FAST>
-__global__ void __launch_bounds__(strided_threads(W)) k_fourier_z(IterArgs<T> a) {
+__device__ __forceinline__ void k_fourier_z_body(const IterArgs<T>& a, const AxisPlan* pl, int kind) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
   constexpr int NT = strided_threads(W);
@@ -823,7 +883,6 @@ __global__ void __launch_bounds__(strided_threads(W)) k_fourier_z(IterArgs<T> a)
   const T2* tws = load_twiddles(a.tw[2], n3, kTwStrided, &tile);
   const int x0 = blockIdx.x * W;
   const int py = blockIdx.y;
-  const int kind = blockIdx.z;
   const bool do_green = kind == 0;
   const bool do_eta = !a.eta_real && (a.dual ? (kind == 1) : true);
   const int nx = min(W, g.H - x0);
@@ -833,7 +892,7 @@ __global__ void __launch_bounds__(strided_threads(W)) k_fourier_z(IterArgs<T> a)
   const long long base = ((long long)py * g.H + x0) * NC;
   const long long zstride = (long long)g.n2 * g.H * NC;
   tile_load<C>(tile, spec + base, zstride, n3, cols);
-  tile_fft_strided<C, NT, false>(tile, a.pl[2], tws);
+  tile_fft_strided<C, NT, false>(tile, pl[2], tws);
   T eta_acc = (T)0;
   if constexpr (FAST) {
     static_assert(DIM == 3 && NT % W == 0, "fast Fourier pass: 3D, whole modes per thread");
@@ -879,14 +938,27 @@ __global__ void __launch_bounds__(strided_threads(W)) k_fourier_z(IterArgs<T> a)
   }
   __syncthreads();
   if (do_green) {
-    tile_fft_strided<C, NT, true>(tile, a.pl[2], tws);
+    tile_fft_strided<C, NT, true>(tile, pl[2], tws);
     tile_store<C>(tile, spec + base, zstride, n3, cols);
   }
   if (!a.eta_real) {  // with the real-space eta the x1 pass owns part_eta
     double e1[1] = {(double)eta_acc};
     block_sum<1>(e1);
     if (threadIdx.x == 0)
-      a.part_eta[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = e1[0];
+      a.part_eta[((size_t)kind * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = e1[0];
+  }
+}
+
+// GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
+template <typename T, int DIM, int W, bool FAST, bool GRP>
+__global__ void __launch_bounds__(strided_threads(W)) k_fourier_z(const __grid_constant__ IterArgs<T> a_) {
+  if constexpr (GRP) {
+    const int kinds = gridDim.z / a_.nsmp;
+    IterArgs<T> a = a_;
+    at_sample(a, blockIdx.z / kinds);
+    k_fourier_z_body<T, DIM, W, FAST>(a, a_.pl, (int)(blockIdx.z % kinds));
+  } else {
+    k_fourier_z_body<T, DIM, W, FAST>(a_, a_.pl, (int)blockIdx.z);
   }
 }
 
@@ -894,7 +966,7 @@ __global__ void __launch_bounds__(strided_threads(W)) k_fourier_z(IterArgs<T> a)
 // R: eta, <sigma>, history and stop decision (single block)
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts, int n_mean_parts) {
+__device__ __forceinline__ void k_reduce_eta_body(const IterArgs<T>& a, const AxisPlan* pl, int n_eta_parts, int n_mean_parts) {
   constexpr int NC = Comp<DIM>::NC;
   Ctrl* ctl = a.ctrl;
   const int st = ctl->state;
@@ -954,11 +1026,23 @@ __global__ void k_reduce_eta(IterArgs<T> a, int n_eta_parts, int n_mean_parts) {
   ctl->state = ns;
 }
 
+// GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
+template <typename T, int DIM, bool GRP>
+__global__ void k_reduce_eta(const __grid_constant__ IterArgs<T> a_, int n_eta_parts, int n_mean_parts) {
+  if constexpr (GRP) {
+    IterArgs<T> a = a_;
+    at_sample(a, blockIdx.y);
+    k_reduce_eta_body<T, DIM>(a, a_.pl, n_eta_parts, n_mean_parts);
+  } else {
+    k_reduce_eta_body<T, DIM>(a_, a_.pl, n_eta_parts, n_mean_parts);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K5: inverse x1 transform (half complex -> real) + scheme update
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
+__device__ __forceinline__ void k_inv_x_body(const IterArgs<T>& a, const AxisPlan* pl) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
   constexpr int NPI = (NC + 1) / 2;
@@ -1011,7 +1095,7 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
           asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(base) + off));
       }
     }
-    tile_fft_ct<CP, NPI, true>(tile, nl, BS, a.pl[0], tws, true);
+    tile_fft_ct<CP, NPI, true>(tile, nl, BS, pl[0], tws, true);
     for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
       const int gl = fdiv(idx, fL), x = idx - gl * L1;
       const long long vox = (l0 + gl) * (long long)L1 + x;
@@ -1082,8 +1166,20 @@ __global__ void __launch_bounds__(256) k_inv_x(IterArgs<T> a) {
   }
 }
 
+// GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
+template <typename T, int DIM, bool GRP>
+__global__ void __launch_bounds__(256) k_inv_x(const __grid_constant__ IterArgs<T> a_) {
+  if constexpr (GRP) {
+    IterArgs<T> a = a_;
+    at_sample(a, blockIdx.y);
+    k_inv_x_body<T, DIM>(a, a_.pl);
+  } else {
+    k_inv_x_body<T, DIM>(a_, a_.pl);
+  }
+}
+
 template <typename T>
-__global__ void k_reduce_delta(IterArgs<T> a) {
+__device__ __forceinline__ void k_reduce_delta_body(const IterArgs<T>& a, const AxisPlan* pl) {
   Ctrl* ctl = a.ctrl;
   const int st = ctl->state;
   if (st != kRunning && st != kLast) return;
@@ -1097,6 +1193,18 @@ __global__ void k_reduce_delta(IterArgs<T> a) {
     const double dl = fmax(m[0], m[1]);
     ctl->last_delta = dl;
     if (ctl->stop_rule == 1 && dl < ctl->tol) ctl->state = kConverged;
+  }
+}
+
+// GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
+template <typename T, bool GRP>
+__global__ void k_reduce_delta(const __grid_constant__ IterArgs<T> a_) {
+  if constexpr (GRP) {
+    IterArgs<T> a = a_;
+    at_sample(a, blockIdx.y);
+    k_reduce_delta_body<T>(a, a_.pl);
+  } else {
+    k_reduce_delta_body<T>(a_, a_.pl);
   }
 }
 
@@ -1175,9 +1283,16 @@ __global__ void k_sum_parts(const double* part, int blocks, int width, double* o
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <typename T>
-cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) {
-#define FFTLS_FWD(D, U, V) k_fwd_x<T, D, U, V><<<a.x1_blocks, a.x_threads, a.x1_smem, s>>>(a)
+// Each launcher comes in two variants: GRP = false, a single solve (sample 0 of a
+// group of one, the kernels read their parameters directly), and GRP = true, a
+// grouped launch over a.nsmp samples of one 3D geometry (fftls_solve_batched): the
+// 1D grids take the sample as blockIdx.y, the strided grids fold it into blockIdx.z.
+// The public launchers pick the variant from a.nsmp; the grouped instantiations
+// live in their own translation units (fftls_kernels_{x,y,z}{32,64}g.cu).
+template <typename T, bool GRP>
+cudaError_t launch_fwd_x_t(const IterArgs<T>& a, cudaStream_t s) {
+  const dim3 grid(a.x1_blocks, GRP ? a.nsmp : 1);
+#define FFTLS_FWD(D, U, V) k_fwd_x<T, D, U, V, GRP><<<grid, a.x_threads, a.x1_smem, s>>>(a)
 // FP64 forward passes (the few certification passes of the ladder) load one voxel at a time
 #define FFTLS_FWD_VB(D, U)                                                                              \
   if constexpr (sizeof(T) == 8) FFTLS_FWD(D, U, 1);                                                     \
@@ -1187,27 +1302,30 @@ cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) {
   if (a.dim == 3) {
     if (a.dual) { FFTLS_FWD_VB(3, true); }
     else { FFTLS_FWD_VB(3, false); }
-  } else {
+  } else if constexpr (!GRP) {
     if (a.dual) { FFTLS_FWD_VB(2, true); }
     else { FFTLS_FWD_VB(2, false); }
+  } else {
+    return cudaErrorInvalidValue;
   }
 #undef FFTLS_FWD_VB
 #undef FFTLS_FWD
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_eta_stencil(const IterArgs<T>& a, cudaStream_t s) {
-  if (a.green == kCentered) k_eta_stencil<T, true><<<a.e_blocks, kEThreads, a.e_smem, s>>>(a);
-  else k_eta_stencil<T, false><<<a.e_blocks, kEThreads, a.e_smem, s>>>(a);
+template <typename T, bool GRP>
+cudaError_t launch_eta_stencil_t(const IterArgs<T>& a, cudaStream_t s) {
+  const dim3 grid(a.e_blocks, GRP ? a.nsmp : 1);
+  if (a.green == kCentered) k_eta_stencil<T, true, GRP><<<grid, kEThreads, a.e_smem, s>>>(a);
+  else k_eta_stencil<T, false, GRP><<<grid, kEThreads, a.e_smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s) {
+template <typename T, bool GRP>
+cudaError_t launch_mid_y_t(const IterArgs<T>& a, bool inv, cudaStream_t s) {
   if (a.g.n2 == 1) return cudaSuccess;
-  dim3 grid((a.g.H + a.y_w - 1) / a.y_w, a.g.n3, (!inv && a.dual && !a.eta_real) ? 2 : 1);
-#define FFTLS_MIDY(NCV, WV) k_mid_y<T, NCV, WV><<<grid, strided_threads(WV), a.y_smem, s>>>(a, inv ? 1 : 0)
+  dim3 grid((a.g.H + a.y_w - 1) / a.y_w, a.g.n3, ((!inv && a.dual && !a.eta_real) ? 2 : 1) * (GRP ? a.nsmp : 1));
+#define FFTLS_MIDY(NCV, WV) k_mid_y<T, NCV, WV, GRP><<<grid, strided_threads(WV), a.y_smem, s>>>(a, inv ? 1 : 0)
 #define FFTLS_MIDY_W(NCV)                                                                               \
   switch (a.y_w) {                                                                                      \
     case 1: FFTLS_MIDY(NCV, 1); break;                                                                  \
@@ -1218,7 +1336,8 @@ cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s) {
     default: return cudaErrorInvalidValue;                                                              \
   }
   if (a.dim == 3) { FFTLS_MIDY_W(6) }
-  else { FFTLS_MIDY_W(3) }
+  else if constexpr (!GRP) { FFTLS_MIDY_W(3) }
+  else return cudaErrorInvalidValue;
 #undef FFTLS_MIDY_W
 #undef FFTLS_MIDY
   return cudaGetLastError();
@@ -1230,10 +1349,10 @@ bool fourier_fast(const IterArgs<T>& a) {
   return a.dim == 3 && a.eta_real && (a.green == kCentered || a.green == kRotated);
 }
 
-template <typename T>
-cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s) {
-  dim3 grid((a.g.H + a.z_w - 1) / a.z_w, a.g.n2, (a.dual && !a.eta_real) ? 2 : 1);
-#define FFTLS_FZ(D, WV, F) k_fourier_z<T, D, WV, F><<<grid, strided_threads(WV), a.z_smem, s>>>(a)
+template <typename T, bool GRP>
+cudaError_t launch_fourier_z_t(const IterArgs<T>& a, cudaStream_t s) {
+  dim3 grid((a.g.H + a.z_w - 1) / a.z_w, a.g.n2, ((a.dual && !a.eta_real) ? 2 : 1) * (GRP ? a.nsmp : 1));
+#define FFTLS_FZ(D, WV, F) k_fourier_z<T, D, WV, F, GRP><<<grid, strided_threads(WV), a.z_smem, s>>>(a)
 #define FFTLS_FZ_W(D, F)                                                                                \
   switch (a.z_w) {                                                                                      \
     case 1: FFTLS_FZ(D, 1, F); break;                                                                   \
@@ -1246,35 +1365,51 @@ cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s) {
   if (a.dim == 3) {
     if (fourier_fast(a)) { FFTLS_FZ_W(3, true) }
     else { FFTLS_FZ_W(3, false) }
-  } else {
+  } else if constexpr (!GRP) {
     FFTLS_FZ_W(2, false)
+  } else {
+    return cudaErrorInvalidValue;
   }
 #undef FFTLS_FZ_W
 #undef FFTLS_FZ
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaStream_t s) {
+template <typename T, bool GRP>
+cudaError_t launch_reduce_eta_t(const IterArgs<T>& a, cudaStream_t s) {
   const int nparts = a.eta_real ? a.e_blocks : ((a.g.H + a.z_w - 1) / a.z_w) * a.g.n2 * (a.dual ? 2 : 1);
   const int mparts = a.x1_blocks;
-  if (a.dim == 3) k_reduce_eta<T, 3><<<1, 512, 0, s>>>(a, nparts, mparts);
-  else k_reduce_eta<T, 2><<<1, 512, 0, s>>>(a, nparts, mparts);
+  const dim3 grid(1, GRP ? a.nsmp : 1);
+  if (a.dim == 3) k_reduce_eta<T, 3, GRP><<<grid, 512, 0, s>>>(a, nparts, mparts);
+  else if constexpr (!GRP) k_reduce_eta<T, 2, GRP><<<grid, 512, 0, s>>>(a, nparts, mparts);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_inv_x(const IterArgs<T>& a, cudaStream_t s) {
-  if (a.dim == 3) k_inv_x<T, 3><<<a.x5_blocks, a.x_threads, a.x5_smem, s>>>(a);
-  else k_inv_x<T, 2><<<a.x5_blocks, a.x_threads, a.x5_smem, s>>>(a);
+template <typename T, bool GRP>
+cudaError_t launch_inv_x_t(const IterArgs<T>& a, cudaStream_t s) {
+  const dim3 grid(a.x5_blocks, GRP ? a.nsmp : 1);
+  if (a.dim == 3) k_inv_x<T, 3, GRP><<<grid, a.x_threads, a.x5_smem, s>>>(a);
+  else if constexpr (!GRP) k_inv_x<T, 2, GRP><<<grid, a.x_threads, a.x5_smem, s>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s) {
-  k_reduce_delta<T><<<1, 512, 0, s>>>(a);
+template <typename T, bool GRP>
+cudaError_t launch_reduce_delta_t(const IterArgs<T>& a, cudaStream_t s) {
+  k_reduce_delta<T, GRP><<<dim3(1, GRP ? a.nsmp : 1), 512, 0, s>>>(a);
   return cudaGetLastError();
 }
+
+#define FFTLS_PICK(fn, ...) (a.nsmp > 1 ? fn##_grp<T>(__VA_ARGS__) : fn##_t<T, false>(__VA_ARGS__))
+template <typename T> cudaError_t launch_fwd_x(const IterArgs<T>& a, cudaStream_t s) { return FFTLS_PICK(launch_fwd_x, a, s); }
+template <typename T> cudaError_t launch_eta_stencil(const IterArgs<T>& a, cudaStream_t s) { return FFTLS_PICK(launch_eta_stencil, a, s); }
+template <typename T> cudaError_t launch_mid_y(const IterArgs<T>& a, bool inv, cudaStream_t s) { return FFTLS_PICK(launch_mid_y, a, inv, s); }
+template <typename T> cudaError_t launch_fourier_z(const IterArgs<T>& a, cudaStream_t s) { return FFTLS_PICK(launch_fourier_z, a, s); }
+template <typename T> cudaError_t launch_reduce_eta(const IterArgs<T>& a, cudaStream_t s) { return FFTLS_PICK(launch_reduce_eta, a, s); }
+template <typename T> cudaError_t launch_inv_x(const IterArgs<T>& a, cudaStream_t s) { return FFTLS_PICK(launch_inv_x, a, s); }
+template <typename T> cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s) { return FFTLS_PICK(launch_reduce_delta, a, s); }
+#undef FFTLS_PICK
 
 // Every kernel of the iteration may take up to smax bytes of dynamic shared
 // memory (any tile schedule the host picks stays below it).  One function per
@@ -1282,67 +1417,103 @@ cudaError_t launch_reduce_delta(const IterArgs<T>& a, cudaStream_t s) {
 #define FFTLS_ATTR(fn)                                                                                          \
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
 
-template <typename T>
-cudaError_t set_attrs_y(size_t smax) {
+template <typename T, bool GRP>
+cudaError_t set_attrs_y_t(size_t smax) {
   cudaError_t e = cudaSuccess;
-  FFTLS_ATTR((k_mid_y<T, 6, 1>));
-  FFTLS_ATTR((k_mid_y<T, 6, 2>));
-  FFTLS_ATTR((k_mid_y<T, 6, 4>));
-  FFTLS_ATTR((k_mid_y<T, 6, 8>));
-  FFTLS_ATTR((k_mid_y<T, 6, 16>));
-  FFTLS_ATTR((k_mid_y<T, 3, 1>));
-  FFTLS_ATTR((k_mid_y<T, 3, 2>));
-  FFTLS_ATTR((k_mid_y<T, 3, 4>));
-  FFTLS_ATTR((k_mid_y<T, 3, 8>));
-  FFTLS_ATTR((k_mid_y<T, 3, 16>));
+  FFTLS_ATTR((k_mid_y<T, 6, 1, GRP>));
+  FFTLS_ATTR((k_mid_y<T, 6, 2, GRP>));
+  FFTLS_ATTR((k_mid_y<T, 6, 4, GRP>));
+  FFTLS_ATTR((k_mid_y<T, 6, 8, GRP>));
+  FFTLS_ATTR((k_mid_y<T, 6, 16, GRP>));
+  if constexpr (!GRP) {
+    FFTLS_ATTR((k_mid_y<T, 3, 1, GRP>));
+    FFTLS_ATTR((k_mid_y<T, 3, 2, GRP>));
+    FFTLS_ATTR((k_mid_y<T, 3, 4, GRP>));
+    FFTLS_ATTR((k_mid_y<T, 3, 8, GRP>));
+    FFTLS_ATTR((k_mid_y<T, 3, 16, GRP>));
+  }
   return e;
 }
 
-template <typename T>
-cudaError_t set_attrs_z(size_t smax) {
+template <typename T, bool GRP>
+cudaError_t set_attrs_z_t(size_t smax) {
   cudaError_t e = cudaSuccess;
-  FFTLS_ATTR((k_fourier_z<T, 3, 1, false>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 2, false>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 4, false>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 8, false>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 16, false>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 1, true>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 2, true>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 4, true>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 8, true>));
-  FFTLS_ATTR((k_fourier_z<T, 3, 16, true>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 1, false>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 2, false>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 4, false>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 8, false>));
-  FFTLS_ATTR((k_fourier_z<T, 2, 16, false>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 1, false, GRP>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 2, false, GRP>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 4, false, GRP>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 8, false, GRP>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 16, false, GRP>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 1, true, GRP>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 2, true, GRP>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 4, true, GRP>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 8, true, GRP>));
+  FFTLS_ATTR((k_fourier_z<T, 3, 16, true, GRP>));
+  if constexpr (!GRP) {
+    FFTLS_ATTR((k_fourier_z<T, 2, 1, false, GRP>));
+    FFTLS_ATTR((k_fourier_z<T, 2, 2, false, GRP>));
+    FFTLS_ATTR((k_fourier_z<T, 2, 4, false, GRP>));
+    FFTLS_ATTR((k_fourier_z<T, 2, 8, false, GRP>));
+    FFTLS_ATTR((k_fourier_z<T, 2, 16, false, GRP>));
+  }
   return e;
 }
+
+template <typename T, bool GRP>
+cudaError_t set_attrs_x_t(size_t smax) {
+  cudaError_t e = cudaSuccess;
+  FFTLS_ATTR((k_eta_stencil<T, true, GRP>));
+  FFTLS_ATTR((k_eta_stencil<T, false, GRP>));
+  FFTLS_ATTR((k_fwd_x<T, 3, true, 1, GRP>));
+  FFTLS_ATTR((k_fwd_x<T, 3, false, 1, GRP>));
+  if constexpr (!GRP) {
+    FFTLS_ATTR((k_fwd_x<T, 2, true, 1, GRP>));
+    FFTLS_ATTR((k_fwd_x<T, 2, false, 1, GRP>));
+  }
+  if constexpr (sizeof(T) == 4) {
+    FFTLS_ATTR((k_fwd_x<T, 3, true, 2, GRP>));
+    FFTLS_ATTR((k_fwd_x<T, 3, true, 4, GRP>));
+    FFTLS_ATTR((k_fwd_x<T, 3, false, 2, GRP>));
+    FFTLS_ATTR((k_fwd_x<T, 3, false, 4, GRP>));
+    if constexpr (!GRP) {
+      FFTLS_ATTR((k_fwd_x<T, 2, true, 2, GRP>));
+      FFTLS_ATTR((k_fwd_x<T, 2, true, 4, GRP>));
+      FFTLS_ATTR((k_fwd_x<T, 2, false, 2, GRP>));
+      FFTLS_ATTR((k_fwd_x<T, 2, false, 4, GRP>));
+    }
+  }
+  FFTLS_ATTR((k_inv_x<T, 3, GRP>));
+  if constexpr (!GRP) FFTLS_ATTR((k_inv_x<T, 2, GRP>));
+  return e;
+}
+#ifdef FFTLS_GROUPED_TU
+template <typename T> cudaError_t launch_fwd_x_grp(const IterArgs<T>& a, cudaStream_t s) { return launch_fwd_x_t<T, true>(a, s); }
+template <typename T> cudaError_t launch_eta_stencil_grp(const IterArgs<T>& a, cudaStream_t s) { return launch_eta_stencil_t<T, true>(a, s); }
+template <typename T> cudaError_t launch_mid_y_grp(const IterArgs<T>& a, bool inv, cudaStream_t s) { return launch_mid_y_t<T, true>(a, inv, s); }
+template <typename T> cudaError_t launch_fourier_z_grp(const IterArgs<T>& a, cudaStream_t s) { return launch_fourier_z_t<T, true>(a, s); }
+template <typename T> cudaError_t launch_reduce_eta_grp(const IterArgs<T>& a, cudaStream_t s) { return launch_reduce_eta_t<T, true>(a, s); }
+template <typename T> cudaError_t launch_inv_x_grp(const IterArgs<T>& a, cudaStream_t s) { return launch_inv_x_t<T, true>(a, s); }
+template <typename T> cudaError_t launch_reduce_delta_grp(const IterArgs<T>& a, cudaStream_t s) { return launch_reduce_delta_t<T, true>(a, s); }
+template <typename T> cudaError_t set_attrs_xgrp(size_t smax) { return set_attrs_x_t<T, true>(smax); }
+template <typename T> cudaError_t set_attrs_ygrp(size_t smax) { return set_attrs_y_t<T, true>(smax); }
+template <typename T> cudaError_t set_attrs_zgrp(size_t smax) { return set_attrs_z_t<T, true>(smax); }
+template <typename T>
+cudaError_t set_attrs_grp(size_t smax) {
+  cudaError_t e = set_attrs_xgrp<T>(smax);
+  if (e == cudaSuccess) e = set_attrs_ygrp<T>(smax);
+  if (e == cudaSuccess) e = set_attrs_zgrp<T>(smax);
+  return e;
+}
+#endif
+template <typename T> cudaError_t set_attrs_y(size_t smax) { return set_attrs_y_t<T, false>(smax); }
+template <typename T> cudaError_t set_attrs_z(size_t smax) { return set_attrs_z_t<T, false>(smax); }
 
 template <typename T>
 cudaError_t set_kernel_attributes(const IterArgs<T>& a, size_t smax) {
-  cudaError_t e = cudaSuccess;
   (void)a;
-  FFTLS_ATTR((k_eta_stencil<T, true>));
-  FFTLS_ATTR((k_eta_stencil<T, false>));
-  FFTLS_ATTR((k_fwd_x<T, 3, true, 1>));
-  FFTLS_ATTR((k_fwd_x<T, 3, false, 1>));
-  FFTLS_ATTR((k_fwd_x<T, 2, true, 1>));
-  FFTLS_ATTR((k_fwd_x<T, 2, false, 1>));
-  if constexpr (sizeof(T) == 4) {
-    FFTLS_ATTR((k_fwd_x<T, 3, true, 2>));
-    FFTLS_ATTR((k_fwd_x<T, 3, true, 4>));
-    FFTLS_ATTR((k_fwd_x<T, 3, false, 2>));
-    FFTLS_ATTR((k_fwd_x<T, 3, false, 4>));
-    FFTLS_ATTR((k_fwd_x<T, 2, true, 2>));
-    FFTLS_ATTR((k_fwd_x<T, 2, true, 4>));
-    FFTLS_ATTR((k_fwd_x<T, 2, false, 2>));
-    FFTLS_ATTR((k_fwd_x<T, 2, false, 4>));
-  }
-  FFTLS_ATTR((k_inv_x<T, 3>));
-  FFTLS_ATTR((k_inv_x<T, 2>));
+  cudaError_t e = set_attrs_x_t<T, false>(smax);
   if (e == cudaSuccess) e = set_attrs_y<T>(smax);
   if (e == cudaSuccess) e = set_attrs_z<T>(smax);
+  if (e == cudaSuccess) e = set_attrs_grp<T>(smax);
   return e;
 }
 #undef FFTLS_ATTR

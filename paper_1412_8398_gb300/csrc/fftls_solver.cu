@@ -29,6 +29,11 @@ const char* const kKindNames[2][kNumKinds] = {
      "reduce_delta_f64", "eta_x_f64"}};
 constexpr int kMaxOuter = 8;  // FP64 residual evaluations of the refinement ladder
 constexpr int kMaxWorkers = 64, kDefaultWorkers = 8;  // concurrent solves of fftls_solve_batched
+// grouped launches of fftls_solve_batched: samples per group, and the device memory a
+// group may take (about kGroupBytesPerVoxel bytes per voxel of every sample: both
+// iterates, both spectra in FP64, the ladder's defect and divergence, the phase ids)
+constexpr int kMaxGroup = 256;
+constexpr long long kGroupBytes = 24LL << 30, kGroupBytesPerVoxel = 210;
 
 struct DevBuf {
   void* p = nullptr;
@@ -200,6 +205,9 @@ struct fftls_ctx {
   GraphCache graphs[2];
   Ctrl* h_ctrl = nullptr;  // pinned
   double* h_sums = nullptr;
+  DevBuf gpar;             // per-sample lambda0, mu0, eps_bar of a grouped solve
+  Ctrl* h_gctrl = nullptr;  // pinned control blocks of a grouped solve
+  int h_gcap = 0;
   long long launches = 0;  // kernels launched (graph nodes counted one by one)
   long long graph_launches = 0;
   double prof_ms[2][kNumKinds];
@@ -496,7 +504,9 @@ struct Runner {
   const Setup& S;
   IterArgs<T> a;
   bool capturing = false;
-  Runner(fftls_ctx* c_, const Setup& S_) : c(c_), S(S_) { memset(&a, 0, sizeof(a)); }
+  int ns = 1;          // samples of the group (a single solve: 1)
+  Ctrl* hctl;          // their control blocks on the host (pinned), read after every chunk
+  Runner(fftls_ctx* c_, const Setup& S_) : c(c_), S(S_), hctl(c_->h_ctrl) { memset(&a, 0, sizeof(a)); }
 
   int kernels_per_iter() const { return 4 + (S.g.n2 > 1 ? 2 : 0) + (a.want_delta ? 1 : 0) + (a.eta_real ? 1 : 0); }
 
@@ -554,53 +564,59 @@ struct Runner {
   }
 
   fftls_status read_ctrl() {
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_ctrl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
+    CUDA_TRY(c, cudaMemcpyAsync(hctl, a.ctrl, (size_t)ns * sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
     CUDA_TRY(c, cudaStreamSynchronize(S.s));
     return FFTLS_OK;
   }
+  fftls_status put_ctrl(const Ctrl* init) {
+    memcpy(hctl, init, (size_t)ns * sizeof(Ctrl));
+    CUDA_TRY(c, cudaMemcpyAsync(a.ctrl, hctl, (size_t)ns * sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
+    return FFTLS_OK;
+  }
+  bool running() const {
+    for (int i = 0; i < ns; ++i)
+      if (hctl[i].state == kRunning) return true;
+    return false;
+  }
 
-  // One iteration launched directly (no graph); returns the state after it.
-  fftls_status single(Ctrl init, bool dual, int update, int* final_state) {
-    CUDA_TRY(c, cudaMemcpyAsync(a.ctrl, &init, sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
+  // One iteration launched directly (no graph); the states after it are in hctl.
+  fftls_status single(const Ctrl* init, bool dual, int update) {
     fftls_status st;
+    if ((st = put_ctrl(init))) return st;
     if ((st = iteration(dual, update, S.profile))) return st;
     if ((st = collect_profile())) return st;
-    if ((st = read_ctrl())) return st;
-    *final_state = c->h_ctrl->state;
-    return FFTLS_OK;
+    return read_ctrl();
   }
 
   // eta of the current iterate without the transforms (3D G^C/G^W/G^R): the real-space
   // stencil, the means of sigma and eps, and the reduction's stop decision (no update).
-  fftls_status certify(Ctrl init, int* final_state) {
-    CUDA_TRY(c, cudaMemcpyAsync(a.ctrl, &init, sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
+  fftls_status certify(const Ctrl* init) {
     fftls_status st;
+    if ((st = put_ctrl(init))) return st;
     if ((st = launch(7, [](Runner* r, cudaStream_t s) { return launch_eta_stencil<T>(r->a, s); }, S.profile)))
       return st;
-    CUDA_TRY(c, launch_stress<T>(a.eps, a.phase, a.coef, a.dim, a.g.N, nullptr, a.part_mean, a.x1_blocks, S.s));
-    c->launches += 1;
+    for (int i = 0; i < ns; ++i) {
+      CUDA_TRY(c, launch_stress<T>(a.eps + i * a.st_field, a.phase + i * a.st_phase, a.coef + i * a.st_coef, a.dim,
+                                   a.g.N, nullptr, a.part_mean + i * a.st_pmean, a.x1_blocks, S.s));
+      c->launches += 1;
+    }
     if ((st = launch(3, [](Runner* r, cudaStream_t s) { return launch_reduce_eta<T>(r->a, s); }, S.profile)))
       return st;
     if ((st = collect_profile())) return st;
-    if ((st = read_ctrl())) return st;
-    *final_state = c->h_ctrl->state;
-    return FFTLS_OK;
+    return read_ctrl();
   }
 
-  // Run iterations until the device state leaves kRunning.
-  fftls_status run(Ctrl init, bool first_dual, bool dual, int update, int* final_state) {
-    CUDA_TRY(c, cudaMemcpyAsync(a.ctrl, &init, sizeof(Ctrl), cudaMemcpyHostToDevice, S.s));
+  // Run iterations until no sample's state is kRunning (states in hctl).
+  fftls_status run(const Ctrl* init, bool first_dual, bool dual, int update) {
     fftls_status st;
+    if ((st = put_ctrl(init))) return st;
     if (first_dual && !dual) {
       if ((st = iteration(true, kUpdDirectTau, S.profile))) return st;
       if ((st = collect_profile())) return st;
       if ((st = read_ctrl())) return st;
-      if (c->h_ctrl->state != kRunning) {
-        *final_state = c->h_ctrl->state;
-        return FFTLS_OK;
-      }
+      if (!running()) return FFTLS_OK;
     }
-    const long long N = S.g.N;
+    const long long N = S.g.N * ns;
     const int chunk = (int)std::max<long long>(1, std::min<long long>(32, 40000000LL / std::max<long long>(N, 1)));
     cudaGraphExec_t exec = nullptr;
     if (S.graphs && !S.profile) {
@@ -642,9 +658,8 @@ struct Runner {
         if ((st = collect_profile())) return st;
       }
       if ((st = read_ctrl())) return st;
-      if (c->h_ctrl->state != kRunning) break;
+      if (!running()) break;
     }
-    *final_state = c->h_ctrl->state;
     return FFTLS_OK;
   }
 };
@@ -930,6 +945,8 @@ void fftls_destroy(fftls_ctx* c) {
     cudaEventDestroy(e.b);
   }
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->h_gctrl) cudaFreeHost(c->h_gctrl);
+  c->gpar.release();
   if (c->h_sums) cudaFreeHost(c->h_sums);
   if (c->stream) cudaStreamDestroy(c->stream);
   cudaSetDevice(prev);
@@ -986,14 +1003,31 @@ fftls_status fftls_profile(const fftls_ctx* c, const char** names, double* total
   return FFTLS_OK;
 }
 
-static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls_options* o, fftls_result* r) {
-  fftls_status st = validate(c, p, o);
-  if (st) return st;
-  if (!r) return set_err(c, FFTLS_E_INVALID_ARG, "null result");
+// Solve ns problems that share one grid, dimension, operator and scheme (a single
+// solve is ns = 1; ns > 1 runs every kernel of the iteration as one grouped launch
+// over the samples, 3D only, and every sample follows exactly the path it would
+// take alone: its own control block, stop decisions, precision ladder and
+// history).  Per-sample statuses go to stat[]; the return value is the first
+// error that stopped the whole group (FFTLS_OK otherwise).
+static fftls_status solve_core(fftls_ctx* c, const fftls_problem* const* P, int ns, const fftls_options* o,
+                               fftls_result* const* R, fftls_status* stat) {
+  const fftls_problem* p = P[0];
+  for (int i = 0; i < ns; ++i) {
+    fftls_status st = validate(c, P[i], o);
+    if (st) return st;
+    if (!R[i]) return set_err(c, FFTLS_E_INVALID_ARG, "null result");
+  }
+  if (ns > 1 && o->eps_init) return set_err(c, FFTLS_E_INVALID_ARG, "grouped solve: eps_init must be NULL");
   Setup S;
   memset(&S, 0, sizeof(S));
   setup_geometry(S, p);
   const int d = S.dim, nc = S.nc;
+  if (ns > 1 && d != 3) return set_err(c, FFTLS_E_INVALID_ARG, "grouped solve: 3D grids only");
+  std::vector<Setup> Ss(ns);
+  for (int i = 0; i < ns; ++i) {
+    memset(&Ss[i], 0, sizeof(Setup));
+    setup_geometry(Ss[i], P[i]);
+  }
   S.s = o->stream ? (cudaStream_t)o->stream : c->stream;
   S.profile = o->profile != 0;
   S.graphs = o->use_graphs != 0;
@@ -1004,39 +1038,58 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
     memset(c->prof_ms, 0, sizeof(c->prof_ms));
     memset(c->prof_n, 0, sizeof(c->prof_n));
   }
-  // phase image on the device, ids checked there (< n_phases)
-  if (p->phase_on_device) {
+  // phase images on the device (one slice per sample), ids checked there (< n_phases)
+  if (ns == 1 && p->phase_on_device) {
     S.d_phase = p->phase;
   } else {
-    CUDA_TRY(c, c->phase.ensure((size_t)N));
-    CUDA_TRY(c, cudaMemcpyAsync(c->phase.p, p->phase, (size_t)N, cudaMemcpyHostToDevice, S.s));
+    CUDA_TRY(c, c->phase.ensure((size_t)N * ns));
+    for (int i = 0; i < ns; ++i)
+      CUDA_TRY(c, cudaMemcpyAsync((uint8_t*)c->phase.p + (size_t)i * N, P[i]->phase, (size_t)N,
+                                  P[i]->phase_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S.s));
     S.d_phase = (const uint8_t*)c->phase.p;
   }
   {
+    CUDA_TRY(c, c->sums.ensure(std::max<size_t>(64 * sizeof(double), (size_t)ns * sizeof(unsigned int))));
     const int pb = (int)std::min<long long>((N + 255) / 256, (long long)c->num_sms * 8);
-    CUDA_TRY(c, launch_phase_max(S.d_phase, N, (unsigned int*)c->sums.p, pb, S.s));
-    c->launches += 1;
-    unsigned int pmax = 0;
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_sums, c->sums.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, S.s));
+    for (int i = 0; i < ns; ++i) {
+      CUDA_TRY(c, launch_phase_max(S.d_phase + (size_t)i * N, N, (unsigned int*)c->sums.p + i, pb, S.s));
+      c->launches += 1;
+    }
+    std::vector<unsigned int> pmax(ns);
+    CUDA_TRY(c, cudaMemcpyAsync(pmax.data(), c->sums.p, (size_t)ns * sizeof(unsigned int), cudaMemcpyDeviceToHost, S.s));
     CUDA_TRY(c, cudaStreamSynchronize(S.s));
-    memcpy(&pmax, c->h_sums, sizeof(unsigned int));
-    if ((int)pmax >= p->n_phases)
-      return set_err(c, FFTLS_E_INVALID_ARG, "phase image holds id %u >= n_phases = %d", pmax, p->n_phases);
+    for (int i = 0; i < ns; ++i)
+      if ((int)pmax[i] >= P[i]->n_phases)
+        return set_err(c, FFTLS_E_INVALID_ARG, "%sphase image holds id %u >= n_phases = %d",
+                       ns > 1 ? "sample of the group: " : "", pmax[i], P[i]->n_phases);
   }
   const bool use32 = o->precision != FFTLS_FP64;
   const bool use64 = o->precision != FFTLS_FP32;
   const bool ladder = o->precision == FFTLS_FP32_REFINE64;
   const size_t spec_bytes = (size_t)S.g.modes * nc * (use64 ? 16 : 8);
-  CUDA_TRY(c, c->specA.ensure(spec_bytes));
-  CUDA_TRY(c, c->specB.ensure(spec_bytes));
-  if (use32) CUDA_TRY(c, c->eps32.ensure((size_t)nc * N * sizeof(float)));
-  if (use64 || o->eps_init) CUDA_TRY(c, c->eps64.ensure((size_t)nc * N * sizeof(double)));
+  CUDA_TRY(c, c->specA.ensure(spec_bytes * ns));
+  CUDA_TRY(c, c->specB.ensure(spec_bytes * ns));
+  if (use32) CUDA_TRY(c, c->eps32.ensure((size_t)nc * N * sizeof(float) * ns));
+  if (use64 || o->eps_init) CUDA_TRY(c, c->eps64.ensure((size_t)nc * N * sizeof(double) * ns));
+  const size_t d64_elems = std::max<size_t>((size_t)S.g.modes * 3, (size_t)(3 * N + 1) / 2);  // float2 units
   if (ladder) {
-    CUDA_TRY(c, c->rfield.ensure((size_t)nc * N * sizeof(float)));
-    CUDA_TRY(c, c->d64.ensure(std::max<size_t>((size_t)S.g.modes * 3 * sizeof(float2), (size_t)(3 * N) * sizeof(float))));
+    CUDA_TRY(c, c->rfield.ensure((size_t)nc * N * sizeof(float) * ns));
+    CUDA_TRY(c, c->d64.ensure(d64_elems * sizeof(float2) * ns));
   }
-  CUDA_TRY(c, c->eta_hist.ensure((size_t)o->max_iter * sizeof(double)));
-  CUDA_TRY(c, c->ms_hist.ensure((size_t)o->max_iter * nc * sizeof(double)));
+  CUDA_TRY(c, c->eta_hist.ensure((size_t)o->max_iter * sizeof(double) * ns));
+  CUDA_TRY(c, c->ms_hist.ensure((size_t)o->max_iter * 6 * sizeof(double) * ns));
+  CUDA_TRY(c, c->ctrl.ensure(sizeof(Ctrl) * ns));
+  Ctrl* hctl = c->h_ctrl;
+  if (ns > 1) {
+    if (c->h_gcap < ns) {
+      if (c->h_gctrl) cudaFreeHost(c->h_gctrl);
+      c->h_gctrl = nullptr;
+      c->h_gcap = 0;
+      CUDA_TRY(c, cudaMallocHost((void**)&c->h_gctrl, sizeof(Ctrl) * ns));
+      c->h_gcap = ns;
+    }
+    hctl = c->h_gctrl;
+  }
   // tables shared by both precisions
   std::vector<double> tab;
   std::vector<int> perms;
@@ -1044,7 +1097,7 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
   CUDA_TRY(c, c->perms.ensure(perms.size() * sizeof(int)));
   CUDA_TRY(c, cudaMemcpyAsync(c->perms.p, perms.data(), perms.size() * sizeof(int), cudaMemcpyHostToDevice, S.s));
   const int* d_perms = (const int*)c->perms.p;
-  // initial field
+  // initial fields
   const bool warm = o->eps_init != nullptr;
   if (warm) {
     CUDA_TRY(c, cudaMemcpyAsync(c->eps64.p, o->eps_init, (size_t)nc * N * sizeof(double),
@@ -1054,9 +1107,13 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
       c->launches += 1;
     }
   } else {
-    if (o->precision == FFTLS_FP64) CUDA_TRY(c, launch_fill_eps<double>((double*)c->eps64.p, nc, N, S.eps_bar, S.s));
-    else CUDA_TRY(c, launch_fill_eps<float>((float*)c->eps32.p, nc, N, S.eps_bar, S.s));
-    c->launches += 1;
+    for (int i = 0; i < ns; ++i) {
+      if (o->precision == FFTLS_FP64)
+        CUDA_TRY(c, launch_fill_eps<double>((double*)c->eps64.p + (size_t)i * nc * N, nc, N, Ss[i].eps_bar, S.s));
+      else
+        CUDA_TRY(c, launch_fill_eps<float>((float*)c->eps32.p + (size_t)i * nc * N, nc, N, Ss[i].eps_bar, S.s));
+      c->launches += 1;
+    }
   }
   const bool direct = p->scheme == FFTLS_DIRECT;
   // G^C / G^W / G^R in 3D take eta from the real-space stencil and transform tau
@@ -1064,166 +1121,294 @@ static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls
   // DS uses the sigma form while its iterate is compatible.
   auto upd_of = [&](bool er) { return direct ? (er ? (int)kUpdDirectTau : (int)kUpdDirectSig) : (int)kUpdAccel; };
   const bool dual_steady = !direct;
-  Ctrl ctl;
-  memset(&ctl, 0, sizeof(ctl));
-  ctl.state = kRunning;
-  ctl.max_it = o->max_iter;
-  ctl.mean_guard = (direct || o->eta_only) ? 0 : 1;
-  ctl.best = INFINITY;
-  ctl.stop_rule = o->stop;
-  ctl.tol = o->tol;
-  int state = kRunning;
-  int it32 = 0;
-  bool final64 = o->precision == FFTLS_FP64;
+  // a group's per-sample views: coefficient tables, parameters, partial sums, strides
+  auto group_view = [&](auto& Rn) -> fftls_status {
+    typedef typename std::remove_reference<decltype(Rn.a)>::type ArgsT;
+    typedef typename std::remove_pointer<decltype(Rn.a.eps)>::type T;
+    ArgsT& a = Rn.a;
+    Rn.ns = ns;
+    Rn.hctl = hctl;
+    if (ns == 1) return FFTLS_OK;
+    std::vector<double> cf((size_t)ns * 256 * kCoef), par((size_t)ns * 8);
+    for (int i = 0; i < ns; ++i) {
+      coef_table(Ss[i], P[i], &cf[(size_t)i * 256 * kCoef]);
+      par[8 * (size_t)i] = Ss[i].lam0;
+      par[8 * (size_t)i + 1] = Ss[i].mu0;
+      for (int k = 0; k < 6; ++k) par[8 * (size_t)i + 2 + k] = Ss[i].eps_bar[k];
+    }
+    std::vector<T> cfT(cf.begin(), cf.end());
+    DevBuf& cb = Prec<T>::idx ? c->coef64 : c->coef32;
+    CUDA_TRY(c, cb.ensure(cfT.size() * sizeof(T)));
+    CUDA_TRY(c, c->gpar.ensure(par.size() * sizeof(double)));
+    CUDA_TRY(c, cudaMemcpyAsync(cb.p, cfT.data(), cfT.size() * sizeof(T), cudaMemcpyHostToDevice, S.s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->gpar.p, par.data(), par.size() * sizeof(double), cudaMemcpyHostToDevice, S.s));
+    CUDA_TRY(c, cudaStreamSynchronize(S.s));  // the host vectors go out of scope
+    const size_t pm = max_x_blocks(S) * 2 * nc, pe = max_eta_parts(S), pd = max_x_blocks(S) * 2;
+    CUDA_TRY(c, c->part_mean.ensure(pm * sizeof(double) * ns));
+    CUDA_TRY(c, c->part_eta.ensure(pe * sizeof(double) * ns));
+    CUDA_TRY(c, c->part_delta.ensure(pd * sizeof(double) * ns));
+    a.coef = (const T*)cb.p;
+    a.part_mean = (double*)c->part_mean.p;
+    a.part_eta = (double*)c->part_eta.p;
+    a.part_delta = (double*)c->part_delta.p;
+    a.nsmp = ns;
+    a.st_field = (long long)nc * N;
+    a.st_phase = N;
+    a.st_spec = (long long)S.g.modes * nc;
+    a.st_coef = 256 * kCoef;
+    a.st_pmean = (long long)pm;
+    a.st_peta = (long long)pe;
+    a.st_pdelta = (long long)pd;
+    a.st_hist = o->max_iter;
+    a.st_d64 = a.d64 ? (long long)d64_elems : 0;
+    a.smp_par = (const double*)c->gpar.p;
+    return FFTLS_OK;
+  };
+  Ctrl ctl0;
+  memset(&ctl0, 0, sizeof(ctl0));
+  ctl0.state = kRunning;
+  ctl0.max_it = o->max_iter;
+  ctl0.mean_guard = (direct || o->eta_only) ? 0 : 1;
+  ctl0.best = INFINITY;
+  ctl0.stop_rule = o->stop;
+  ctl0.tol = o->tol;
+  std::vector<Ctrl> ctl(ns, ctl0), init(ns);
+  std::vector<int> state(ns, kRunning), it32(ns, 0);
+  std::vector<char> final64(ns, o->precision == FFTLS_FP64 ? 1 : 0);  // the returned field is the FP64 iterate
+  fftls_status st;
+  auto take = [&](int i) { ctl[i] = hctl[i]; state[i] = hctl[i].state; };
   if (o->precision == FFTLS_FP64) {
     Runner<double> R64(c, S);
     if ((st = prepare<double>(c, S, p, o, R64, (double*)c->eps64.p, tab, d_perms))) return st;
+    if ((st = group_view(R64))) return st;
     const bool er = R64.a.eta_real;
-    if ((st = R64.run(ctl, direct && warm && !er, dual_steady, upd_of(er), &state))) return st;
+    if ((st = R64.run(ctl.data(), direct && warm && !er, dual_steady, upd_of(er)))) return st;
+    for (int i = 0; i < ns; ++i) take(i);
   } else if (o->precision == FFTLS_FP32) {
     Runner<float> R32(c, S);
     if ((st = prepare<float>(c, S, p, o, R32, (float*)c->eps32.p, tab, d_perms))) return st;
+    if ((st = group_view(R32))) return st;
     const bool er = R32.a.eta_real;
-    if ((st = R32.run(ctl, direct && warm && !er, dual_steady, upd_of(er), &state))) return st;
-    it32 = c->h_ctrl->it;
+    if ((st = R32.run(ctl.data(), direct && warm && !er, dual_steady, upd_of(er)))) return st;
+    for (int i = 0; i < ns; ++i) {
+      take(i);
+      it32[i] = ctl[i].it;
+    }
   } else {
     // Ladder.  A: plain FP32 iterations until eta <= refine_switch (or a stall).
     Runner<float> R32(c, S);
     if ((st = prepare<float>(c, S, p, o, R32, (float*)c->eps32.p, tab, d_perms))) return st;
     Runner<double> R64(c, S);
     if ((st = prepare<double>(c, S, p, o, R64, (double*)c->eps64.p, tab, d_perms))) return st;
+    if ((st = group_view(R32))) return st;
+    if ((st = group_view(R64))) return st;
     // both precisions must measure eta the same way (the FP64 divergence feeds the FP32 estimate)
     if (R32.a.eta_real != R64.a.eta_real)
       return set_err(c, FFTLS_E_CUDA, "internal: FP32 and FP64 plans measure eta differently");
-    Ctrl ca = ctl;
-    ca.stop_rule = 0;
-    ca.tol = o->refine_switch > 0.0 ? o->refine_switch : std::max(o->tol, 3e-5);
-    ca.switch_mode = 1;
-    ca.stall_window = 32;
+    for (int i = 0; i < ns; ++i) {
+      init[i] = ctl0;
+      init[i].stop_rule = 0;
+      init[i].tol = o->refine_switch > 0.0 ? o->refine_switch : std::max(o->tol, 3e-5);
+      init[i].switch_mode = 1;
+      init[i].stall_window = 32;
+    }
     R32.a.want_delta = 0;
     const bool er = R32.a.eta_real;
-    if ((st = R32.run(ca, direct && warm && !er, dual_steady, upd_of(er), &state))) return st;
-    it32 = c->h_ctrl->it;
-    ctl = *c->h_ctrl;
-    if (state == kSwitch) {
-      CUDA_TRY(c, launch_convert<double, float>((double*)c->eps64.p, (const float*)c->eps32.p, (long long)nc * N, S.s));
+    if ((st = R32.run(init.data(), direct && warm && !er, dual_steady, upd_of(er)))) return st;
+    std::vector<char> active(ns, 0);
+    bool any = false;
+    for (int i = 0; i < ns; ++i) {
+      take(i);
+      it32[i] = ctl[i].it;
+      active[i] = state[i] == kSwitch;
+      any = any || active[i];
+    }
+    for (int i = 0; i < ns; ++i) final64[i] = active[i];
+    if (any) {
+      CUDA_TRY(c, launch_convert<double, float>((double*)c->eps64.p, (const float*)c->eps32.p, (long long)nc * N * ns, S.s));
       c->launches += 1;
-      final64 = true;
       // B / C: FP64 defect of the iterate (and its exact eta), then an FP32
       // correction solve for delta, eps64 += delta; until the FP64 eta passes.
       R64.a.write_d64 = 1;
       R32.a.corr = 1;
-      state = kRunning;
-      for (int outer = 0; outer < kMaxOuter; ++outer) {
-        if (ctl.it >= o->max_iter) { state = kStopped; break; }
-        Ctrl cb = ctl;
-        cb.state = kRunning;
-        cb.stop_rule = 0;
-        cb.tol = o->tol;
-        cb.switch_mode = 0;
-        cb.stall_window = 0;
-        cb.phase_max = 0;
-        cb.max_it = ctl.it + 1;  // exactly one evaluation; kLast runs the residual update
-        for (int i = 0; i < 6; ++i) cb.off_sig[i] = cb.off_eps[i] = 0.0;
+      for (int i = 0; i < ns; ++i)
+        if (active[i]) state[i] = kRunning;
+      Ctrl idle;
+      memset(&idle, 0, sizeof(idle));
+      idle.state = kStopped;  // samples that take no part: every kernel of theirs exits at once
+      for (int outer = 0; outer < kMaxOuter && any; ++outer) {
+        for (int i = 0; i < ns; ++i) {
+          init[i] = idle;
+          if (!active[i]) continue;
+          if (ctl[i].it >= o->max_iter) {
+            state[i] = kStopped;
+            active[i] = 0;
+            continue;
+          }
+          Ctrl cb = ctl[i];
+          cb.state = kRunning;
+          cb.stop_rule = 0;
+          cb.tol = o->tol;
+          cb.switch_mode = 0;
+          cb.stall_window = 0;
+          cb.phase_max = 0;
+          cb.max_it = ctl[i].it + 1;  // exactly one evaluation; kLast runs the residual update
+          for (int k = 0; k < 6; ++k) cb.off_sig[k] = cb.off_eps[k] = 0.0;
+          init[i] = cb;
+        }
         if (outer > 0 && R64.a.eta_real) {
           // after a correction: certify eta of eps64 first; the full FP64 pass (defect and eta)
           // only runs if the certificate fails, and then its own eta evaluation counts instead
-          if ((st = R64.certify(cb, &state))) return st;
-          if (state == kConverged || state == kDiverged) {
-            ctl = *c->h_ctrl;
-            ctl.max_it = o->max_iter;
-            break;
+          if ((st = R64.certify(init.data()))) return st;
+          for (int i = 0; i < ns; ++i) {
+            if (!active[i]) continue;
+            if (hctl[i].state == kConverged || hctl[i].state == kDiverged) {
+              take(i);
+              ctl[i].max_it = o->max_iter;
+              active[i] = 0;
+              init[i] = idle;
+            }
           }
         }
-        if ((st = R64.single(cb, true, kUpdResidual, &state))) return st;
-        ctl = *c->h_ctrl;
-        ctl.max_it = o->max_iter;
-        if (state == kConverged || state == kDiverged) break;
-        if (ctl.it >= o->max_iter) { state = kStopped; break; }
-        // C: correction delta from 0 with the defect r as source
-        CUDA_TRY(c, cudaMemsetAsync(c->eps32.p, 0, (size_t)nc * N * sizeof(float), S.s));
-        Ctrl cc = ctl;
-        cc.state = kRunning;
-        cc.stop_rule = 0;
-        cc.tol = 0.5 * o->tol;  // the estimate's FP32 error stays well below tol / 2 (FP64 certifies)
-        cc.switch_mode = 1;
-        cc.stall_window = 32;
-        cc.stall = 0;
-        cc.best = INFINITY;
-        cc.phase_it = 0;
-        cc.phase_max = 0;
-        for (int i = 0; i < 6; ++i) {
-          cc.off_sig[i] = ctl.last_ms[i];
-          cc.off_eps[i] = ctl.last_me[i];
+        if ((st = R64.single(init.data(), true, kUpdResidual))) return st;
+        any = false;
+        for (int i = 0; i < ns; ++i) {
+          if (!active[i]) {
+            init[i] = idle;
+            continue;
+          }
+          take(i);
+          ctl[i].max_it = o->max_iter;
+          init[i] = idle;
+          if (state[i] == kConverged || state[i] == kDiverged) {
+            active[i] = 0;
+            continue;
+          }
+          if (ctl[i].it >= o->max_iter) {
+            state[i] = kStopped;
+            active[i] = 0;
+            continue;
+          }
+          // C: correction delta from 0 with the defect r as source
+          CUDA_TRY(c, cudaMemsetAsync((float*)c->eps32.p + (size_t)i * nc * N, 0, (size_t)nc * N * sizeof(float), S.s));
+          Ctrl cc = ctl[i];
+          cc.state = kRunning;
+          cc.stop_rule = 0;
+          cc.tol = 0.5 * o->tol;  // the estimate's FP32 error stays well below tol / 2 (FP64 certifies)
+          cc.switch_mode = 1;
+          cc.stall_window = 32;
+          cc.stall = 0;
+          cc.best = INFINITY;
+          cc.phase_it = 0;
+          cc.phase_max = 0;
+          for (int k = 0; k < 6; ++k) {
+            cc.off_sig[k] = ctl[i].last_ms[k];
+            cc.off_eps[k] = ctl[i].last_me[k];
+          }
+          init[i] = cc;
+          any = true;
         }
-        if ((st = R32.run(cc, false, true, direct ? kUpdCorrDirect : kUpdCorrAccel, &state))) return st;
-        it32 += c->h_ctrl->it - ctl.it;
-        ctl = *c->h_ctrl;
-        CUDA_TRY(c, launch_add_correction((double*)c->eps64.p, (const float*)c->eps32.p, (long long)nc * N, S.s));
-        c->launches += 1;
-        if (state == kDiverged) break;
-        if (state != kSwitch) { state = kStopped; break; }  // max_iter reached inside the correction
-        state = kRunning;
+        if (!any) break;
+        if ((st = R32.run(init.data(), false, true, direct ? kUpdCorrDirect : kUpdCorrAccel))) return st;
+        any = false;
+        for (int i = 0; i < ns; ++i) {
+          if (!active[i]) continue;
+          it32[i] += hctl[i].it - ctl[i].it;
+          take(i);
+          CUDA_TRY(c, launch_add_correction((double*)c->eps64.p + (size_t)i * nc * N,
+                                            (const float*)c->eps32.p + (size_t)i * nc * N, (long long)nc * N, S.s));
+          c->launches += 1;
+          if (state[i] == kDiverged) { active[i] = 0; continue; }
+          if (state[i] != kSwitch) { state[i] = kStopped; active[i] = 0; continue; }  // max_iter inside the correction
+          state[i] = kRunning;
+          any = true;
+        }
       }
-      if (state == kRunning) state = kStopped;
+      for (int i = 0; i < ns; ++i)
+        if (state[i] == kRunning) state[i] = kStopped;
     }
   }
-  const Ctrl fin = *c->h_ctrl;
-  // outputs from the final field
-  const bool out64 = final64;
-  const void* epsf = out64 ? c->eps64.p : c->eps32.p;
+  // outputs from the final fields
   const int sblocks = (int)std::min<long long>((N + 255) / 256, (long long)c->num_sms * 8);
   CUDA_TRY(c, c->part_mean.ensure((size_t)sblocks * 2 * nc * sizeof(double)));
-  double* stress_dev = nullptr;
-  if (r->stress) {
-    if (o->fields_on_device) stress_dev = r->stress;
-    else {
-      CUDA_TRY(c, c->scratch.ensure((size_t)nc * N * sizeof(double)));
-      stress_dev = (double*)c->scratch.p;
+  CUDA_TRY(c, c->sums.ensure((size_t)std::max(ns, 1) * 2 * nc * sizeof(double)));
+  std::vector<double> hs((size_t)ns * 2 * nc);
+  fftls_status worst = FFTLS_OK;
+  for (int i = 0; i < ns; ++i) {
+    fftls_result* r = R[i];
+    const Ctrl fin = ctl[i];
+    const bool o64 = final64[i];  // else the FP32 field (FP32, or a ladder sample stopped in its FP32 phase)
+    const void* epsf = o64 ? (const void*)((const double*)c->eps64.p + (size_t)i * nc * N)
+                           : (const void*)((const float*)c->eps32.p + (size_t)i * nc * N);
+    const uint8_t* ph = S.d_phase + (size_t)i * N;
+    double* stress_dev = nullptr;
+    if (r->stress) {
+      if (o->fields_on_device) stress_dev = r->stress;
+      else {
+        CUDA_TRY(c, c->scratch.ensure((size_t)nc * N * sizeof(double)));
+        stress_dev = (double*)c->scratch.p;
+      }
     }
-  }
-  if (out64)
-    CUDA_TRY(c, launch_stress<double>((const double*)epsf, S.d_phase, (const double*)c->coef64.p, d, N, stress_dev,
-                                      (double*)c->part_mean.p, sblocks, S.s));
-  else
-    CUDA_TRY(c, launch_stress<float>((const float*)epsf, S.d_phase, (const float*)c->coef32.p, d, N, stress_dev,
-                                     (double*)c->part_mean.p, sblocks, S.s));
-  CUDA_TRY(c, launch_sum_parts((const double*)c->part_mean.p, sblocks, 2 * nc, (double*)c->sums.p, S.s));
-  c->launches += 2;
-  CUDA_TRY(c, cudaMemcpyAsync(c->h_sums, c->sums.p, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, S.s));
-  if (r->stress && !o->fields_on_device)
-    CUDA_TRY(c, cudaMemcpyAsync(r->stress, stress_dev, (size_t)nc * N * sizeof(double), cudaMemcpyDeviceToHost, S.s));
-  if (r->strain) {
-    const cudaMemcpyKind kind = o->fields_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (out64) {
-      CUDA_TRY(c, cudaMemcpyAsync(r->strain, epsf, (size_t)nc * N * sizeof(double), kind, S.s));
-    } else if (o->fields_on_device) {
-      CUDA_TRY(c, launch_convert<double, float>(r->strain, (const float*)epsf, (long long)nc * N, S.s));
-    } else {
-      CUDA_TRY(c, c->scratch.ensure((size_t)nc * N * sizeof(double)));
-      CUDA_TRY(c, launch_convert<double, float>((double*)c->scratch.p, (const float*)epsf, (long long)nc * N, S.s));
-      CUDA_TRY(c, cudaMemcpyAsync(r->strain, c->scratch.p, (size_t)nc * N * sizeof(double), kind, S.s));
+    if (o64)
+      CUDA_TRY(c, launch_stress<double>((const double*)epsf, ph, (const double*)c->coef64.p + (size_t)(ns > 1 ? i : 0) * 256 * kCoef,
+                                        d, N, stress_dev, (double*)c->part_mean.p, sblocks, S.s));
+    else
+      CUDA_TRY(c, launch_stress<float>((const float*)epsf, ph, (const float*)c->coef32.p + (size_t)(ns > 1 ? i : 0) * 256 * kCoef,
+                                       d, N, stress_dev, (double*)c->part_mean.p, sblocks, S.s));
+    CUDA_TRY(c, launch_sum_parts((const double*)c->part_mean.p, sblocks, 2 * nc, (double*)c->sums.p + (size_t)i * 2 * nc, S.s));
+    c->launches += 2;
+    if (r->stress && !o->fields_on_device)
+      CUDA_TRY(c, cudaMemcpyAsync(r->stress, stress_dev, (size_t)nc * N * sizeof(double), cudaMemcpyDeviceToHost, S.s));
+    if (r->strain) {
+      const cudaMemcpyKind kind = o->fields_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+      if (o64) {
+        CUDA_TRY(c, cudaMemcpyAsync(r->strain, epsf, (size_t)nc * N * sizeof(double), kind, S.s));
+      } else if (o->fields_on_device) {
+        CUDA_TRY(c, launch_convert<double, float>(r->strain, (const float*)epsf, (long long)nc * N, S.s));
+      } else {
+        CUDA_TRY(c, c->scratch.ensure((size_t)nc * N * sizeof(double)));
+        CUDA_TRY(c, launch_convert<double, float>((double*)c->scratch.p, (const float*)epsf, (long long)nc * N, S.s));
+        CUDA_TRY(c, cudaMemcpyAsync(r->strain, c->scratch.p, (size_t)nc * N * sizeof(double), kind, S.s));
+      }
     }
+    const int hl = std::min(fin.it, r->history_capacity);
+    if (r->eta_history && hl > 0)
+      CUDA_TRY(c, cudaMemcpyAsync(r->eta_history, (const double*)c->eta_hist.p + (size_t)i * o->max_iter,
+                                  (size_t)hl * sizeof(double), cudaMemcpyDeviceToHost, S.s));
+    if (r->mean_stress_history && hl > 0) {
+      // one sample's history: [it][nc] at its slice (per-sample stride max_iter x 6 in a group)
+      const double* src = (const double*)c->ms_hist.p + (size_t)i * o->max_iter * (ns > 1 ? 6 : nc);
+      CUDA_TRY(c, cudaMemcpyAsync(r->mean_stress_history, src, (size_t)hl * nc * sizeof(double), cudaMemcpyDeviceToHost, S.s));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(S.s));  // scratch is reused by the next sample
+    r->iterations = fin.it;
+    r->iterations_fp32 = it32[i];
+    r->final_eta = fin.last_eta;
+    r->final_delta = fin.last_delta;
+    r->history_len = hl;
+    stat[i] = state[i] == kConverged ? FFTLS_OK : state[i] == kDiverged ? FFTLS_E_DIVERGED : FFTLS_E_NOT_CONVERGED;
+    if (stat[i] != FFTLS_OK && worst == FFTLS_OK) worst = stat[i];
   }
-  const int hl = std::min(fin.it, r->history_capacity);
-  if (r->eta_history && hl > 0)
-    CUDA_TRY(c, cudaMemcpyAsync(r->eta_history, c->eta_hist.p, (size_t)hl * sizeof(double), cudaMemcpyDeviceToHost, S.s));
-  if (r->mean_stress_history && hl > 0)
-    CUDA_TRY(c, cudaMemcpyAsync(r->mean_stress_history, c->ms_hist.p, (size_t)hl * nc * sizeof(double),
-                                cudaMemcpyDeviceToHost, S.s));
+  CUDA_TRY(c, cudaMemcpyAsync(hs.data(), c->sums.p, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, S.s));
   CUDA_TRY(c, cudaStreamSynchronize(S.s));
-  for (int i = 0; i < 6; ++i) {
-    r->mean_stress[i] = i < nc ? c->h_sums[i] / (double)N : 0.0;
-    r->mean_strain[i] = i < nc ? c->h_sums[nc + i] / (double)N : 0.0;
-  }
-  r->iterations = fin.it;
-  r->iterations_fp32 = it32;
-  r->final_eta = fin.last_eta;
-  r->final_delta = fin.last_delta;
-  r->history_len = hl;
-  if (state == kConverged) return FFTLS_OK;
-  if (state == kDiverged) return set_err(c, FFTLS_E_DIVERGED, "diverged: eta = %g after %d iterations", fin.last_eta, fin.it);
-  return set_err(c, FFTLS_E_NOT_CONVERGED, "not converged after %d iterations (eta = %g)", fin.it, fin.last_eta);
+  for (int i = 0; i < ns; ++i)
+    for (int k = 0; k < 6; ++k) {
+      R[i]->mean_stress[k] = k < nc ? hs[(size_t)i * 2 * nc + k] / (double)N : 0.0;
+      R[i]->mean_strain[k] = k < nc ? hs[(size_t)i * 2 * nc + nc + k] / (double)N : 0.0;
+    }
+  return FFTLS_OK;
+}
+
+static fftls_status solve_impl(fftls_ctx* c, const fftls_problem* p, const fftls_options* o, fftls_result* r) {
+  fftls_status st = FFTLS_OK;
+  const fftls_status e = solve_core(c, &p, 1, o, &r, &st);
+  if (e != FFTLS_OK) return e;
+  const Ctrl fin = c->h_ctrl[0];
+  (void)fin;
+  if (st == FFTLS_OK) return FFTLS_OK;
+  if (st == FFTLS_E_DIVERGED)
+    return set_err(c, FFTLS_E_DIVERGED, "diverged: eta = %g after %d iterations", r->final_eta, r->iterations);
+  return set_err(c, FFTLS_E_NOT_CONVERGED, "not converged after %d iterations (eta = %g)", r->iterations, r->final_eta);
 }
 
 fftls_status fftls_solve(fftls_ctx* c, const fftls_problem* p, const fftls_options* o, fftls_result* r) {
@@ -1263,28 +1448,89 @@ fftls_status fftls_solve_batched(fftls_ctx* c, const fftls_problem* probs, int c
     cudaSetDevice(prev);
     if (e != cudaSuccess) return set_err(c, FFTLS_E_CUDA, "batched solve: %s", cudaGetErrorString(e));
   }
-  // largest grids first (longest-processing-time order balances the workers)
-  std::vector<int> order(count);
-  std::iota(order.begin(), order.end(), 0);
-  auto voxels = [&](int i) { return (long long)probs[i].n[0] * probs[i].n[1] * probs[i].n[2]; };
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return voxels(x) > voxels(y); });
+  // Tasks: 3D samples that share a grid, operator and scheme form groups solved by
+  // grouped launches (solve_core, at most kGroupBytes of device memory per group);
+  // every other sample is a task of its own.  Largest tasks first (longest-
+  // processing-time order balances the workers).
+  std::vector<std::vector<int>> tasks;
+  std::vector<fftls_status> st(count, FFTLS_OK);
+  std::vector<std::string> msg(count);
+  {
+    std::vector<int> order;
+    for (int i = 0; i < count; ++i) {  // invalid samples are reported, never grouped or run
+      fftls_ctx vc;
+      const fftls_status vs = validate(&vc, &probs[i], o);
+      if (vs != FFTLS_OK) {
+        st[i] = vs;
+        msg[i] = vc.err;
+      } else {
+        order.push_back(i);
+      }
+    }
+    const int nvalid = (int)order.size();
+    auto key_less = [&](int x, int y) {
+      const fftls_problem &a = probs[x], &b = probs[y];
+      if (a.dim != b.dim) return a.dim < b.dim;
+      for (int k = 0; k < 3; ++k)
+        if (a.n[k] != b.n[k]) return a.n[k] < b.n[k];
+      if (a.green != b.green) return a.green < b.green;
+      return a.scheme < b.scheme;
+    };
+    std::stable_sort(order.begin(), order.end(), key_less);
+    for (int k = 0; k < nvalid;) {
+      int e = k + 1;
+      while (e < nvalid && !key_less(order[k], order[e]) && !key_less(order[e], order[k])) ++e;
+      const fftls_problem& q = probs[order[k]];
+      const long long vox = (long long)q.n[0] * q.n[1] * q.n[2];
+      const int per = q.dim == 3 ? (int)std::max<long long>(1, std::min<long long>(kMaxGroup, kGroupBytes / (kGroupBytesPerVoxel * vox))) : 1;
+      for (int b = k; b < e; b += per) tasks.emplace_back(order.begin() + b, order.begin() + std::min(e, b + per));
+      k = e;
+    }
+    auto work_of = [&](const std::vector<int>& t) {
+      return (long long)t.size() * probs[t[0]].n[0] * probs[t[0]].n[1] * probs[t[0]].n[2];
+    };
+    std::stable_sort(tasks.begin(), tasks.end(), [&](const std::vector<int>& x, const std::vector<int>& y) {
+      return work_of(x) > work_of(y);
+    });
+  }
   fftls_options wo = *o;
   wo.stream = nullptr;  // each worker runs on its own stream
   std::atomic<int> next(0);
-  std::vector<fftls_status> st(count, FFTLS_OK);
-  std::vector<std::string> msg(count);
   std::vector<long long> k0(nw), g0(nw);
   for (int t = 0; t < nw; ++t) {
     k0[t] = c->workers[t]->launches;
     g0[t] = c->workers[t]->graph_launches;
   }
+  const int ntask = (int)tasks.size();
   auto work = [&](fftls_ctx* w) {
     for (;;) {
       const int k = next.fetch_add(1);
-      if (k >= count) break;
-      const int i = order[k];
-      st[i] = fftls_solve(w, &probs[i], &wo, &results[i]);
-      if (st[i] != FFTLS_OK) msg[i] = w->err;
+      if (k >= ntask) break;
+      const std::vector<int>& t = tasks[k];
+      if (t.size() == 1) {
+        const int i = t[0];
+        st[i] = fftls_solve(w, &probs[i], &wo, &results[i]);
+        if (st[i] != FFTLS_OK) msg[i] = w->err;
+        continue;
+      }
+      std::vector<const fftls_problem*> P(t.size());
+      std::vector<fftls_result*> Rp(t.size());
+      std::vector<fftls_status> sst(t.size(), FFTLS_OK);
+      for (size_t j = 0; j < t.size(); ++j) {
+        P[j] = &probs[t[j]];
+        Rp[j] = &results[t[j]];
+      }
+      int prev = 0;
+      cudaGetDevice(&prev);
+      cudaSetDevice(w->device);
+      w->err.clear();
+      const fftls_status e = solve_core(w, P.data(), (int)t.size(), &wo, Rp.data(), sst.data());
+      cudaSetDevice(prev);
+      for (size_t j = 0; j < t.size(); ++j) {
+        st[t[j]] = e != FFTLS_OK ? e : sst[j];
+        if (st[t[j]] != FFTLS_OK)
+          msg[t[j]] = e != FFTLS_OK ? w->err : std::string(sst[j] == FFTLS_E_DIVERGED ? "diverged" : "not converged");
+      }
     }
   };
   std::vector<std::thread> pool;

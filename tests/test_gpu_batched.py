@@ -129,3 +129,53 @@ def test_batched_argument_errors(fftls):
         assert "sample 1" in str(e.value)
     finally:
         s.close()
+
+
+def _grouped_batch():
+    """Samples sharing grids, operators and schemes (grouped launches), with different phases,
+    moduli, reference media and loads, interleaved with a 2D and an odd-sized sample."""
+    out = []
+    specs = [((16, 16, 16), "R", "AS")] * 5 + [((12, 10, 9), "W", "DS")] * 3 + [((20, 16), "C", "AS"),
+                                                                             ((9, 5, 15), "MS", "AS")]
+    for i, (shp, g, sch) in enumerate(specs):
+        ph, _ = MS.boolean_spheres(shp, 2.0, 0.2 + 0.03 * i, seed=70 + i)
+        lam, mu = MS.young_poisson_phases([(1.0, 0.3), (3.0 + 7 * i, 0.2 + 0.01 * i)])
+        d = len(shp)
+        eb = np.eye(d) * (0.3 + 0.1 * i)
+        eb[0, d - 1] = eb[d - 1, 0] = 0.1 * (i % 3)
+        item = {"phase": ph, "lam": lam, "mu": mu, "eps_bar": eb, "green": g, "scheme": sch}
+        if i == 2:
+            item["lam0"], item["mu0"] = 2.0, 1.5   # an explicit reference medium inside a group
+        out.append(item)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine64", "fp32"])
+def test_grouped_launch_equals_individual_solves(fftls, precision):
+    """Samples of one 3D grid, operator and scheme run as one grouped launch per kernel; each gives
+    what fftls_solve gives alone, including samples that stop at max_iter while others of the group
+    go on: the same statuses and iteration counts and bit for bit the same fields (same schedule,
+    same per-sample partial sums).  The eta and <sigma> histories agree to one unit in the last place:
+    the reduction kernel's grouped instantiation is compiled on its own and may contract its FP64
+    multiply-adds differently."""
+    batch = _grouped_batch()
+    s = fftls.Solver(0)
+    kw = dict(tol=1e-7 if precision == "fp32" else 1e-9, max_iter=160, precision=precision)
+    try:
+        res, st = s.solve_batched(batch, concurrency=3, want_strain=True, want_stress=True, history=True,
+                                  autotune=False, **kw)
+        single = [s.solve(b["phase"], b["lam"], b["mu"], b["eps_bar"], b["green"], b["scheme"],
+                          lam0=b.get("lam0"), mu0=b.get("mu0"), autotune=False, raise_on_error=False, **kw)
+                  for b in batch]
+    finally:
+        s.close()
+    statuses = {r.status for r in res}
+    assert fftls.OK in statuses
+    for r, q in zip(res, single):
+        assert r.status == q.status
+        assert r.iterations == q.iterations and r.iterations_fp32 == q.iterations_fp32
+        assert np.array_equal(r.strain, q.strain)
+        assert np.array_equal(r.stress, q.stress)
+        np.testing.assert_allclose(r.eta_history, q.eta_history, rtol=1e-15, atol=0)
+        np.testing.assert_allclose(r.mean_stress_history, q.mean_stress_history, rtol=1e-15, atol=1e-300)
+        np.testing.assert_allclose(r.mean_stress, q.mean_stress, rtol=1e-15, atol=1e-300)
