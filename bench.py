@@ -61,6 +61,8 @@ def parse():
                     help="instead of the 512^3 workload, train the warm-start network on COUNT solver-generated "
                          "64^3 samples and compare warm and plain starts on 256^3 samples")
     ap.add_argument("--warm-epochs", type=int, default=4)
+    ap.add_argument("--warm-batch", type=int, default=1, help="samples per training step of the warm start")
+    ap.add_argument("--warm-lr", type=float, default=5e-4, help="initial learning rate (decays 10x over training)")
     ap.add_argument("--ncu-region", action="store_true",
                     help="for ncu --profile-from-start off: tune and warm up on the workload, then bracket two "
                          "FP32 iterations launched without graphs with the profiler start / stop calls")
@@ -540,7 +542,7 @@ def run_batched(args, rank, local, world):
         out = {
             "metric": "time to eta <= 1e-6 over a batch of independent samples (AS, G^R)", "unit": "s",
             "value": t_b_max, "higher_is_better": False, "n_gpus": world, "impl": "ours",
-            "data": "synthetic", "dtype": "f32+f64",
+            "data": "synthetic", "dtype": "f32+f64 solve, bf16 inference",
             "config": {"workload": f"batched_boolean_{args.batched}_samples_L32-128_R3-8_f0.1-0.4_chi10-1000",
                        "samples": args.batched, "voxels_total": int(allreduce([float(vox.sum())], _sum_op(world), world)[0]),
                        "concurrency": args.concurrency, "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -576,7 +578,8 @@ def run_warmstart(args, rank, local, world):
     net = WS.WarmNet(device=local, seed=0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = net.train(data, epochs=args.warm_epochs)
+    losses = net.train(data, epochs=args.warm_epochs, batch=args.warm_batch, lr=args.warm_lr,
+                       lr_final=0.1 * args.warm_lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del data
@@ -617,9 +620,10 @@ def run_warmstart(args, rank, local, world):
     out = {
         "metric": "time to eta <= 1e-6 with the learned warm start (AS, G^R, 256^3)", "unit": "s",
         "value": tot("warm", "time_s") / len(rows), "higher_is_better": False, "n_gpus": 1, "impl": "ours",
-        "data": "synthetic", "dtype": "f32+f64",
+        "data": "synthetic", "dtype": "f32+f64 solve, bf16 inference",
         "config": {"workload": f"warmstart_train_{args.warmstart}x64^3_apply_{args.warm_apply}x256^3_boolean",
-                   "train_samples": args.warmstart, "epochs": args.warm_epochs,
+                   "train_samples": args.warmstart, "epochs": args.warm_epochs, "batch": args.warm_batch,
+                   "lr": args.warm_lr,
                    "parameters": WS.parameter_count()},
         "data_seconds": t_data, "train_seconds": t_train, "train_loss_per_epoch": losses,
         "iterations": {"zero_init": tot("zero", "iterations"), "warm": tot("warm", "iterations"),

@@ -87,8 +87,11 @@ fftls_status fftls_nn_features(const uint8_t* phase, float* x, const int n[3], f
 
 /* Initial strain from a network output y [6][N] (components 11,22,33,23,13,12 of
  * the fluctuation for the unit load eps_bar = e1 (x) e1): eps [6][N] FP64 =
- * eps_bar + scale * (y - <y>), so <eps> = eps_bar exactly.  scratch:
- * FFTLS_NN_STRAIN_SCRATCH doubles of device memory (partial sums). */
+ * eps_bar + scale * (y - <y>).  The component means are compensated FP32 sums
+ * combined in FP64; the fluctuation scale * (y - <y>) is formed in FP32 (this is
+ * an initial guess) and widened exactly, so <eps> = eps_bar up to FP32
+ * rounding of the fluctuation.  scratch: FFTLS_NN_STRAIN_SCRATCH doubles of
+ * device memory (partial sums). */
 #define FFTLS_NN_STRAIN_SCRATCH 1536
 fftls_status fftls_nn_strain_init(const float* y, double* eps, const int n[3], const double eps_bar[6], double scale,
                                   double* scratch, void* stream);
@@ -96,6 +99,44 @@ fftls_status fftls_nn_strain_init(const float* y, double* eps, const int n[3], c
 /* Training target from a solved strain field: t [6][N] (FP32) = eps - eps_bar,
  * eps [6][N] FP64 (device). */
 fftls_status fftls_nn_strain_target(const double* eps, float* t, const int n[3], const double eps_bar[6], void* stream);
+
+/* ---- Tensor-core path: BF16 operands, FP32 accumulation, channels-last BF16 activations ----
+ *
+ * An activation with c channels is stored channels-last, [batch][n3][n2][n1][cs],
+ * in BF16 with cs = 8, 16, 32 or 64 (the smallest of these >= c; channels c..cs-1
+ * zero).  Device pointers must be 16-byte aligned.  The convolutions are the
+ * same periodic convolutions as fftls_nn_conv3d, with the input and the weights
+ * rounded to BF16 and FP32 accumulation. */
+
+/* Bytes of the packed weights of a layer with w [c_out][c_in][k^3] (1 <= c_in, c_out <= 64,
+ * k = 1 or 3): transposed = 0 for the convolution x (c_in channels) -> y (c_out), 1 for the
+ * input gradient dy (c_out channels) -> dx (c_in).  0 for invalid arguments. */
+size_t fftls_nn_tc_packed_bytes(int c_in, int c_out, int ksize, int transposed);
+
+/* Round w (FP32 device) to BF16 and lay it out as the tensor-core operand of
+ * fftls_nn_tc_conv3d; packed: fftls_nn_tc_packed_bytes(...) bytes of device memory. */
+fftls_status fftls_nn_tc_pack(const float* w, void* packed, int c_in, int c_out, int ksize, int transposed,
+                              void* stream);
+
+/* y = act(conv(x', W) + bias + skip) (+ y when accumulate = 1) on the output grid n, where W comes
+ * from fftls_nn_tc_pack for (c_in, c_out) = the channels of x and y here (for transposed packing:
+ * the layer's c_out and c_in), and x' is, by in_mode:
+ *   0: x itself, on the grid n;
+ *   1: the nearest-neighbour 2x upsampling of x, x on the grid n/2 (n even);
+ *   2: the 2x2x2 mean pooling of x, x on the grid 2n (the mean rounded to BF16).
+ * x, skip (may be NULL) and y (when out_planar = 0) are channels-last BF16; with out_planar = 1,
+ * y is FP32 [batch][c_out][N] instead.  act = ReLU when relu = 1.  y must not alias x or skip.
+ * Returns FFTLS_E_UNSUPPORTED_SIZE when no voxel tile fits in shared memory. */
+fftls_status fftls_nn_tc_conv3d(const void* x, const void* packed, const float* bias, const void* skip, void* y,
+                                int batch, int c_in, int c_out, const int n[3], int ksize, int in_mode, int relu,
+                                int out_planar, int accumulate, void* stream);
+
+/* First layer from the phase image (uint8 ids, [n3][n2][n1], device): y = act(conv(x, w) + bias)
+ * for the two-channel input x of fftls_nn_features (indicator of phase 1, log_contrast), w FP32
+ * [c_out][2][27], c_out <= 8, computed in FP32 from the phase bytes; y channels-last BF16
+ * (8 stored channels). */
+fftls_status fftls_nn_tc_conv_phase(const uint8_t* phase, const float* w, const float* bias, void* y, const int n[3],
+                                    int c_out, float log_contrast, int relu, void* stream);
 
 #ifdef __cplusplus
 }

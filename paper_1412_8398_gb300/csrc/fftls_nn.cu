@@ -2,7 +2,7 @@
 // convolutions (forward, input gradient, weight gradient), 2x pooling and
 // upsampling, and the small elementwise pieces of training (loss, Adam) and of
 // turning a prediction into an initial strain field.  FP32 throughout, FP64
-// for reductions.
+// for reductions across threads.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -273,12 +273,29 @@ __global__ void k_features(const uint8_t* __restrict__ phase, float* __restrict_
   }
 }
 
-// partial sums of each of the 6 output components: part[c][block]
+// partial sums of each of the 6 output components: part[c][block]; FP32 compensated (Kahan) sums per
+// thread, FP64 across threads and blocks
 __global__ void k_comp_sums(const float* __restrict__ y, double* __restrict__ part, long long N) {
   const int c = blockIdx.y;
-  double s = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x)
-    s += y[(size_t)c * N + t];
+  const float* yc = y + (size_t)c * N;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  float sum = 0.f, comp = 0.f;
+  auto add = [&](float x) {
+    const float v = x - comp;
+    const float nxt = sum + v;
+    comp = (nxt - sum) - v;
+    sum = nxt;
+  };
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; t + 3 * stride < N; t += 4 * stride) {  // four loads in flight per thread
+    const float a0 = yc[t], a1 = yc[t + stride], a2 = yc[t + 2 * stride], a3 = yc[t + 3 * stride];
+    add(a0);
+    add(a1);
+    add(a2);
+    add(a3);
+  }
+  for (; t < N; t += stride) add(yc[t]);
+  double s = (double)sum - (double)comp;
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   __shared__ double red[kThreads / 32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -290,20 +307,35 @@ __global__ void k_comp_sums(const float* __restrict__ y, double* __restrict__ pa
   }
 }
 
+// exact widening of a finite normal (or zero) float by its IEEE-754 fields: the exponent rebiased
+// from 127 to 1023, the 23 mantissa bits moved to the top of the 52; other values through the
+// conversion instruction
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (u & 0x7fffffffu) == 0u ? ((u >> 31) ? -0.0 : 0.0) : (double)f;
+  const uint64_t bits = ((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// eps = eps_bar + scale (y - <y>): the fluctuation in FP32 (an initial guess), widened exactly to FP64
 __global__ void k_strain_init(const float* __restrict__ y, double* __restrict__ eps, const double* __restrict__ part,
                               int nparts, long long N, double e0, double e1, double e2, double e3, double e4, double e5,
-                              double scale) {
-  __shared__ double mean[6];
+                              float scale) {
+  __shared__ float mean[6];
   if (threadIdx.x < 6) {
     double s = 0.0;
     for (int q = 0; q < nparts; ++q) s += part[(size_t)threadIdx.x * nparts + q];
-    mean[threadIdx.x] = s / (double)N;
+    mean[threadIdx.x] = (float)(s / (double)N);
   }
   __syncthreads();
   const double eb[6] = {e0, e1, e2, e3, e4, e5};
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x)
 #pragma unroll
-    for (int c = 0; c < 6; ++c) eps[(size_t)c * N + t] = eb[c] + scale * ((double)y[(size_t)c * N + t] - mean[c]);
+    for (int c = 0; c < 6; ++c) {
+      const double f = widen(scale * (y[(size_t)c * N + t] - mean[c]));
+      eps[(size_t)c * N + t] = eb[c] == 0.0 ? f : eb[c] + f;
+    }
 }
 
 __global__ void k_strain_target(const double* __restrict__ eps, float* __restrict__ t, long long N, double e0,
@@ -474,7 +506,7 @@ fftls_status fftls_nn_strain_init(const float* y, double* eps, const int n[3], c
   k_comp_sums<<<dim3(kMeanBlocks, 6), kThreads, 0, s>>>(y, scratch, N);
   if (cudaGetLastError() != cudaSuccess) return FFTLS_E_CUDA;
   k_strain_init<<<grid_for(N), kThreads, 0, s>>>(y, eps, scratch, kMeanBlocks, N, eps_bar[0], eps_bar[1], eps_bar[2],
-                                                 eps_bar[3], eps_bar[4], eps_bar[5], scale);
+                                                 eps_bar[3], eps_bar[4], eps_bar[5], (float)scale);
   return launched();
 }
 

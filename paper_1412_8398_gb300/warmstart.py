@@ -15,6 +15,11 @@ device memory.  The paper has no learned component.
 Layout: activations [channel][n3][n2][n1] (batch 1), FP32; parameters are one
 flat FP32 vector, layer by layer in LAYERS order, weights [c_out][c_in][k^3]
 then bias [c_out].
+
+Inference also runs on the tensor cores (``predict_tc``): BF16 weights and
+channels-last BF16 activations, FP32 accumulation, the pooling and upsampling
+folded into the next convolution's input staging and the first layer computed
+from the phase bytes.  Training stays in FP32.
 """
 from __future__ import annotations
 
@@ -49,6 +54,20 @@ _ACTS = {
     "e2": (32, 2), "p2": (32, 3), "a3": (64, 3), "e3": (64, 3), "u2": (64, 2), "d2": (32, 2), "u1": (32, 1),
     "d1": (16, 1), "u0": (16, 0), "d0": (8, 0), "y": (6, 0),
 }
+# channels-last BF16 activations of the tensor-core forward: name -> (stored channels, level)
+_TC_ACTS = {
+    "e0": (8, 0), "a1": (16, 1), "e1": (16, 1), "a2": (32, 2), "e2": (32, 2), "a3": (64, 3), "e3": (64, 3),
+    "d2": (32, 2), "d1": (16, 1), "d0": (8, 0),
+}
+# tensor-core forward: (layer, input, input mode (0 same grid, 1 upsampled coarse, 2 pooled fine), skip)
+_TC_PLAN = [
+    ("enc1a", "e0", 2, None), ("enc1b", "a1", 0, None), ("enc2a", "e1", 2, None), ("enc2b", "a2", 0, None),
+    ("enc3a", "e2", 2, None), ("enc3b", "a3", 0, None), ("dec2", "e3", 1, "e2"), ("dec1", "d2", 1, "e1"),
+    ("dec0", "d1", 1, "e0"),
+]
+_TC_OUT = {"enc1a": "a1", "enc1b": "e1", "enc2a": "a2", "enc2b": "e2", "enc3a": "a3", "enc3b": "e3",
+           "dec2": "d2", "dec1": "d1", "dec0": "d0"}
+
 # gradient buffers: name -> (channels, level)
 _GRADS = {
     "gy": (6, 0), "gd0": (8, 0), "gu0": (16, 0), "gd1": (16, 1), "gu1": (32, 1), "gd2": (32, 2), "gu2": (64, 2),
@@ -78,6 +97,11 @@ _NN_SIGNATURES = {
     "fftls_nn_features": (ctypes.c_int, [_P, _P, _I3, ctypes.c_float, _P]),
     "fftls_nn_strain_init": (ctypes.c_int, [_P, _P, _I3, ctypes.POINTER(ctypes.c_double), ctypes.c_double, _P, _P]),
     "fftls_nn_strain_target": (ctypes.c_int, [_P, _P, _I3, ctypes.POINTER(ctypes.c_double), _P]),
+    "fftls_nn_tc_packed_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "fftls_nn_tc_pack": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "fftls_nn_tc_conv3d": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I3,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "fftls_nn_tc_conv_phase": (ctypes.c_int, [_P, _P, _P, _P, _I3, ctypes.c_int, ctypes.c_float, ctypes.c_int, _P]),
 }
 STRAIN_SCRATCH = 1536  # FFTLS_NN_STRAIN_SCRATCH
 
@@ -144,6 +168,9 @@ class WarmNet:
         self.steps = 0
         self._grid = None
         self.losses = []
+        self.version = 0          # bumped whenever the parameters change
+        self._tc_packed = None    # (version, {layer: packed BF16 weights})
+        self._tc_grid = None
 
     # -- parameters ------------------------------------------------------
     def _w(self, name, grad=False):
@@ -172,6 +199,7 @@ class WarmNet:
             host[o:o + nw] = np.asarray(arrays[name][0], dtype=np.float32).reshape(-1)
             host[ob:ob + nb] = np.asarray(arrays[name][1], dtype=np.float32).reshape(-1)
         self.params.copy_(self.torch.from_numpy(host).to(self.dev))
+        self.version += 1
 
     def save(self, path):
         np.savez(path, params=self.params.cpu().numpy(), layers=np.array([str(l) for l in LAYERS]))
@@ -181,27 +209,31 @@ class WarmNet:
         if z["params"].size != self.count:
             raise ValueError("parameter file does not match this network")
         self.params.copy_(self.torch.from_numpy(z["params"].astype(np.float32)).to(self.dev))
+        self.version += 1
 
     # -- buffers ----------------------------------------------------------
-    def _buffers(self, n, train):
+    def _buffers(self, n, train, batch=1):
         n = tuple(int(v) for v in n)
         if any(v % (1 << LEVELS) for v in n):
             raise ValueError(f"grid lengths must be multiples of {1 << LEVELS}")
-        key = (n, train)
+        key = (n, train, batch)
         if self._grid == key:
             return
         torch = self.torch
-        vox = lambda lvl: (n[0] >> lvl) * (n[1] >> lvl) * (n[2] >> lvl)
+        vox = lambda lvl: batch * (n[0] >> lvl) * (n[1] >> lvl) * (n[2] >> lvl)
         self.a = {k: torch.empty(c * vox(l), dtype=torch.float32, device=self.dev) for k, (c, l) in _ACTS.items()}
         self.g = {}
         self.scratch = None
         if train:
             self.g = {k: torch.empty(c * vox(l), dtype=torch.float32, device=self.dev) for k, (c, l) in _GRADS.items()}
-            need = max(self.lib.fftls_nn_wgrad_scratch(1, ci, co, self._dims(n, lvl), k) for _, ci, co, k, lvl in LAYERS)
+            self.target = torch.empty(6 * vox(0), dtype=torch.float32, device=self.dev)
+            need = max(self.lib.fftls_nn_wgrad_scratch(batch, ci, co, self._dims(n, lvl), k)
+                       for _, ci, co, k, lvl in LAYERS)
             self.scratch = torch.empty(int(need), dtype=torch.float32, device=self.dev)
             self.loss_buf = torch.zeros(1, dtype=torch.float64, device=self.dev)
         self.mean_scratch = torch.empty(STRAIN_SCRATCH, dtype=torch.float64, device=self.dev)
         self.n = n
+        self.batch = batch
         self._grid = key
 
     @staticmethod
@@ -212,24 +244,28 @@ class WarmNet:
     def _conv(self, name, src, dst, skip=None, relu=True):
         _, ci, co, k, lvl = next(l for l in LAYERS if l[0] == name)
         st = self.lib.fftls_nn_conv3d(_p(self.a[src]), self._w(name), self._b(name),
-                                      _p(self.a[skip]) if skip else None, _p(self.a[dst]), 1, ci, co,
+                                      _p(self.a[skip]) if skip else None, _p(self.a[dst]), self.batch, ci, co,
                                       self._dims(self.n, lvl), k, 1 if relu else 0, self.stream)
         _check(st, f"conv {name}")
 
     def _pool(self, src, dst, channels, lvl):
-        _check(self.lib.fftls_nn_pool2(_p(self.a[src]), _p(self.a[dst]), channels, self._dims(self.n, lvl),
+        _check(self.lib.fftls_nn_pool2(_p(self.a[src]), _p(self.a[dst]), self.batch * channels, self._dims(self.n, lvl),
                                        self.stream), "pool")
 
     def _up(self, src, dst, channels, lvl_coarse):
-        _check(self.lib.fftls_nn_upsample2(_p(self.a[src]), _p(self.a[dst]), channels,
+        _check(self.lib.fftls_nn_upsample2(_p(self.a[src]), _p(self.a[dst]), self.batch * channels,
                                            self._dims(self.n, lvl_coarse), self.stream), "upsample")
 
-    def features(self, phase, contrast):
-        """Fill the input channels from a device phase image (uint8, (n3, n2, n1))."""
+    def features(self, phase, contrast, slot=0):
+        """Fill the input channels of batch entry `slot` from a device phase image (uint8, (n3, n2, n1))."""
         n = (phase.shape[2], phase.shape[1], phase.shape[0])
-        self._buffers(n, self._grid[1] if self._grid and self._grid[0] == n else False)
-        _check(self.lib.fftls_nn_features(_p(phase), _p(self.a["x"]), _I3(*n), float(log_contrast(contrast)),
-                                          self.stream), "features")
+        if self._grid is None or self._grid[0] != n:
+            self._buffers(n, False)
+        if not 0 <= slot < self.batch:
+            raise ValueError("batch entry out of range")
+        x = ctypes.c_void_p(self.a["x"].data_ptr() + 4 * 2 * n[0] * n[1] * n[2] * slot)
+        _check(self.lib.fftls_nn_features(_p(phase), x, _I3(*n), float(log_contrast(contrast)), self.stream),
+               "features")
 
     def forward(self):
         c = self._conv
@@ -254,7 +290,7 @@ class WarmNet:
 
     def backward(self):
         """Parameter gradients of the loss whose output gradient is in self.g['gy']."""
-        lib, s, n = self.lib, self.stream, self.n
+        lib, s, n, B = self.lib, self.stream, self.n, self.batch
         a, g = self.a, self.g
         scratch = _p(self.scratch)
         ns = self.scratch.numel()
@@ -262,23 +298,23 @@ class WarmNet:
         def wgrad(name, src, gout):
             _, ci, co, k, lvl = next(l for l in LAYERS if l[0] == name)
             _check(lib.fftls_nn_conv3d_backward_weights(_p(a[src]), _p(g[gout]), self._w(name, True),
-                                                        self._b(name, True), 1, ci, co, self._dims(n, lvl), k,
+                                                        self._b(name, True), B, ci, co, self._dims(n, lvl), k,
                                                         scratch, ns, s), f"wgrad {name}")
 
         def dgrad(name, gout, gin):
             _, ci, co, k, lvl = next(l for l in LAYERS if l[0] == name)
-            _check(lib.fftls_nn_conv3d_backward_data(_p(g[gout]), self._w(name), _p(g[gin]), 1, ci, co,
+            _check(lib.fftls_nn_conv3d_backward_data(_p(g[gout]), self._w(name), _p(g[gin]), B, ci, co,
                                                      self._dims(n, lvl), k, 0, s), f"dgrad {name}")
 
         def relu(gname, act):
             _check(lib.fftls_nn_relu_backward(_p(g[gname]), _p(a[act]), a[act].numel(), s), "relu")
 
         def up_bwd(gsrc, gdst, ch, lvl_coarse):
-            _check(lib.fftls_nn_upsample2_backward(_p(g[gsrc]), _p(g[gdst]), ch, self._dims(n, lvl_coarse), s),
+            _check(lib.fftls_nn_upsample2_backward(_p(g[gsrc]), _p(g[gdst]), B * ch, self._dims(n, lvl_coarse), s),
                    "upsample backward")
 
         def pool_bwd_acc(gsrc, gdst, ch, lvl_fine):
-            _check(lib.fftls_nn_pool2_backward(_p(g[gsrc]), _p(g[gdst]), ch, self._dims(n, lvl_fine), 1, s),
+            _check(lib.fftls_nn_pool2_backward(_p(g[gsrc]), _p(g[gdst]), B * ch, self._dims(n, lvl_fine), 1, s),
                    "pool backward")
 
         wgrad("out", "d0", "gy")
@@ -326,29 +362,89 @@ class WarmNet:
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self.steps += 1
+        self.version += 1
         _check(self.lib.fftls_nn_adam(_p(self.params), _p(self.grads), _p(self.m), _p(self.v), self.count,
                                       float(lr), beta1, beta2, eps, self.steps, self.stream), "adam")
 
+    # -- tensor-core inference -------------------------------------------
+    def _tc_weights(self):
+        """Packed BF16 weights of every layer after the first, repacked when the parameters changed."""
+        if self._tc_packed is not None and self._tc_packed[0] == self.version:
+            return self._tc_packed[1]
+        torch = self.torch
+        packed = {}
+        for name, ci, co, k, _ in LAYERS[1:]:
+            nbytes = int(self.lib.fftls_nn_tc_packed_bytes(ci, co, k, 0))
+            buf = torch.empty(nbytes, dtype=torch.uint8, device=self.dev)
+            _check(self.lib.fftls_nn_tc_pack(self._w(name), _p(buf), ci, co, k, 0, self.stream), f"pack {name}")
+            packed[name] = buf
+        self._tc_packed = (self.version, packed)
+        return packed
+
+    def _tc_buffers(self, n):
+        n = tuple(int(v) for v in n)
+        if any(v % (1 << LEVELS) for v in n):
+            raise ValueError(f"grid lengths must be multiples of {1 << LEVELS}")
+        if self._tc_grid == n:
+            return
+        torch = self.torch
+        vox = lambda lvl: (n[0] >> lvl) * (n[1] >> lvl) * (n[2] >> lvl)
+        self.tc = {k: torch.empty(c * vox(l), dtype=torch.bfloat16, device=self.dev) for k, (c, l) in _TC_ACTS.items()}
+        self.tc["y"] = torch.empty(6 * vox(0), dtype=torch.float32, device=self.dev)
+        self.tc_mean_scratch = torch.empty(STRAIN_SCRATCH, dtype=torch.float64, device=self.dev)
+        self._tc_grid = n
+
+    def forward_tc(self, phase, contrast):
+        """The network on the tensor cores for a device phase image (uint8, (n3, n2, n1)); returns the
+        FP32 output [6][N]."""
+        n = (phase.shape[2], phase.shape[1], phase.shape[0])
+        self._tc_buffers(n)
+        packed = self._tc_weights()
+        lib, s, t = self.lib, self.stream, self.tc
+        _check(lib.fftls_nn_tc_conv_phase(_p(phase), self._w("enc0"), self._b("enc0"), _p(t["e0"]), _I3(*n), 8,
+                                          float(log_contrast(contrast)), 1, s), "conv enc0")
+        layer = {l[0]: l for l in LAYERS}
+        for name, src, mode, skip in _TC_PLAN:
+            _, ci, co, k, lvl = layer[name]
+            _check(lib.fftls_nn_tc_conv3d(_p(t[src]), _p(packed[name]), self._b(name), _p(t[skip]) if skip else None,
+                                          _p(t[_TC_OUT[name]]), 1, ci, co, self._dims(n, lvl), k, mode, 1, 0, 0, s),
+                   f"conv {name}")
+        _, ci, co, k, lvl = layer["out"]
+        _check(lib.fftls_nn_tc_conv3d(_p(t["d0"]), _p(packed["out"]), self._b("out"), None, _p(t["y"]), 1, ci, co,
+                                      self._dims(n, 0), k, 0, 0, 1, 0, s), "conv out")
+        return t["y"]
+
     # -- training and prediction -----------------------------------------
-    def train(self, data, epochs: int, lr: float = 5e-4, lr_final: float = 5e-5, seed: int = 0):
-        """Adam on the MSE between prediction and solver fluctuation, one sample per step, in a
-        seeded random order; the learning rate decays geometrically from lr to lr_final (at
-        2e-3 the ReLU units of this network die within the first epoch).  Returns the mean
-        loss of each epoch."""
+    def train(self, data, epochs: int, lr: float = 5e-4, lr_final: float = 5e-5, seed: int = 0, batch: int = 1):
+        """Adam on the MSE between prediction and solver fluctuation, `batch` samples (of one grid
+        size) per step in a seeded random order (each epoch leaves out the len(data) % batch samples
+        its permutation puts last); the learning rate decays geometrically from lr to lr_final (at
+        2e-3 the ReLU units of this network die within the first epoch).  Returns the mean loss of
+        each epoch."""
         torch = self.torch
         rng = np.random.default_rng(seed)
-        total = epochs * len(data)
+        per = len(data) // batch
+        if per < 1:
+            raise ValueError("fewer samples than one batch")
+        total = epochs * per
         per_epoch = []
         step = 0
         for _ in range(epochs):
-            losses = torch.zeros(len(data), dtype=torch.float64, device=self.dev)
-            for j, idx in enumerate(rng.permutation(len(data))):
-                d = data[idx]
-                n = (d["phase"].shape[2], d["phase"].shape[1], d["phase"].shape[0])
-                self._buffers(n, True)
-                self.features(d["phase"], d["contrast"])
+            losses = torch.zeros(per, dtype=torch.float64, device=self.dev)
+            order = rng.permutation(len(data))
+            for j in range(per):
+                group = [data[i] for i in order[j * batch:(j + 1) * batch]]
+                n = (group[0]["phase"].shape[2], group[0]["phase"].shape[1], group[0]["phase"].shape[0])
+                self._buffers(n, True, batch)
+                N6 = 6 * n[0] * n[1] * n[2]
+                for slot, d in enumerate(group):
+                    if d["phase"].shape != group[0]["phase"].shape:
+                        raise ValueError("the samples of a batch must share one grid")
+                    self.features(d["phase"], d["contrast"], slot)
+                    if batch > 1:
+                        self.target[slot * N6:(slot + 1) * N6].copy_(d["target"].reshape(-1))
                 self.forward()
-                self.loss_and_grad(d["target"])
+                self.loss_and_grad(self.target if batch > 1 else group[0]["target"])
                 losses[j:j + 1].copy_(self.loss_buf)
                 self.backward()
                 rate = lr * (lr_final / lr) ** (step / max(1, total - 1))
@@ -358,17 +454,23 @@ class WarmNet:
         self.losses += per_epoch
         return per_epoch
 
-    def initial_strain(self, phase, contrast: float, eps11: float = 1.0):
-        """eps^0 (FP64 device tensor [6][n3][n2][n1]) for the load eps11 e1 (x) e1."""
+    def initial_strain(self, phase, contrast: float, eps11: float = 1.0, tensor_cores: bool = True):
+        """eps^0 (FP64 device tensor [6][n3][n2][n1]) for the load eps11 e1 (x) e1, from the
+        tensor-core forward (BF16) or the FP32 one."""
         torch = self.torch
         n = (phase.shape[2], phase.shape[1], phase.shape[0])
-        self._buffers(n, self._grid[1] if self._grid and self._grid[0] == n else False)
-        self.features(phase, contrast)
-        self.forward()
+        if tensor_cores:
+            y = self.forward_tc(phase, contrast)
+            scratch = self.tc_mean_scratch
+        else:
+            self._buffers(n, self._grid[1] if self._grid and self._grid[0] == n else False)
+            self.features(phase, contrast)
+            y = self.forward()
+            scratch = self.mean_scratch
         eps = torch.empty((6,) + tuple(phase.shape), dtype=torch.float64, device=self.dev)
         eb = (ctypes.c_double * 6)(eps11, 0, 0, 0, 0, 0)
-        _check(self.lib.fftls_nn_strain_init(_p(self.a["y"]), _p(eps), _I3(*n), eb, float(eps11),
-                                             _p(self.mean_scratch), self.stream), "strain init")
+        _check(self.lib.fftls_nn_strain_init(_p(y), _p(eps), _I3(*n), eb, float(eps11), _p(scratch), self.stream),
+               "strain init")
         # the solver reads eps_init on its own stream
         torch.cuda.synchronize(self.dev)
         return eps

@@ -6,7 +6,8 @@ and what the trained network gains over the solver started from eps_bar.
 * the whole network: output and every parameter gradient against the oracle's
   analytic backward (itself pinned by finite differences);
 * a short training on solver-generated fields cuts the iterations to
-  eta <= 1e-6 on held-out samples, the solver deciding convergence.
+  eta <= 1e-6 on held-out samples, the solver deciding convergence, without
+  making the time to tolerance (tensor-core inference included) grow.
 """
 import ctypes
 
@@ -143,10 +144,10 @@ def test_features_and_strain_init(env):
     eb = (ctypes.c_double * 6)(0.5, 0, 0, 0, 0, 0)
     assert lib.fftls_nn_strain_init(_ptr(_dev(torch, y)), _ptr(eps), n, eb, 0.5, _ptr(scratch), None) == 0
     yf = y.astype(np.float32).astype(np.float64)
-    want = 0.5 * (yf - yf.mean(axis=(1, 2, 3), keepdims=True))
-    want[0] += 0.5
-    _close(eps.cpu().numpy(), want, 1e-12)
-    assert abs(eps.cpu().numpy()[0].mean() - 0.5) < 1e-12
+    fluct = 0.5 * (yf - yf.mean(axis=(1, 2, 3), keepdims=True))
+    got = eps.cpu().numpy() - np.array([0.5, 0, 0, 0, 0, 0])[:, None, None, None]
+    _close(got, fluct, 4e-7)   # the fluctuation is formed in FP32: a few units of 2^-24 of its scale
+    assert np.abs(got.mean(axis=(1, 2, 3))).max() < 1e-7
     t = torch.empty((6, 8, 8, 16), dtype=torch.float32, device="cuda")
     assert lib.fftls_nn_strain_target(_ptr(eps), _ptr(t), n, eb, None) == 0
     _close(t.cpu().numpy(), eps.cpu().numpy() - np.array([0.5, 0, 0, 0, 0, 0])[:, None, None, None], 1e-6)
@@ -180,39 +181,93 @@ def test_network_forward_and_gradients_match_oracle(env):
         _close(got[name][1], gref[name][1], 2e-3)
 
 
+def test_batched_step_gradient_is_mean_of_samples(env):
+    """A training step over a batch of two samples gives the mean of the two single-sample
+    gradients (the loss is the mean over every output value of the batch)."""
+    torch, fftls, ws, lib = env
+    net = ws.WarmNet(seed=1)
+    net.load_arrays(W.random_params(seed=21))
+    rng = np.random.default_rng(9)
+    samples = []
+    for i in range(2):
+        ph, _ = MS.boolean_spheres((16, 16, 8), 2.5, 0.3, seed=30 + i)
+        samples.append({"phase": torch.from_numpy(ph).cuda(), "contrast": 10.0 ** (1 + i),
+                        "target": _dev(torch, rng.standard_normal((6, 8, 16, 16)))})
+    single = []
+    for d in samples:
+        net._buffers((16, 16, 8), True, 1)
+        net.features(d["phase"], d["contrast"])
+        net.forward()
+        net.loss_and_grad(d["target"])
+        net.backward()
+        single.append(net.grads.clone())
+    net._buffers((16, 16, 8), True, 2)
+    for slot, d in enumerate(samples):
+        net.features(d["phase"], d["contrast"], slot)
+        net.target[slot * 6 * 2048:(slot + 1) * 6 * 2048].copy_(d["target"].reshape(-1))
+    net.forward()
+    net.loss_and_grad(net.target)
+    net.backward()
+    want = 0.5 * (single[0] + single[1])
+    assert float((net.grads - want).abs().max()) <= 1e-4 * float(want.abs().max())
+
+
+def _timed(torch, fn):
+    import time
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t
+
+
 def test_trained_network_gain_over_plain_start(env):
-    """What a short training buys on held-out samples: the initial field's error
-    against the converged solution drops well below that of eps_bar, the solver
-    (which decides convergence) reaches the same moduli from it, and the iteration count to
-    eta <= 1e-6 is not worse.  The accelerated scheme's iteration count depends
-    only logarithmically on the starting error (scaling the exact fluctuation by
-    0.5 saves about 5 % of the iterations), so the iteration gain itself is small."""
+    """What a short training on 32^3 samples buys on held-out 256^3 samples, every solve through the
+    FP32 -> FP64 ladder to eta <= 1e-6 (the solver decides convergence): the initial field's error
+    against the converged solution drops well below that of eps_bar, the moduli agree with the
+    plain start's, the iteration count does not grow, and neither does the time to tolerance with
+    the tensor-core inference counted in (best of three runs of each; 3 % allowed for timing noise,
+    about twice the inference's share of a solve at this size).
+    The accelerated scheme's iteration count depends only logarithmically on the starting error
+    (scaling the exact fluctuation by 0.5 saves about 5 % of the iterations), so the gain itself
+    is small."""
     torch, fftls, ws, lib = env
     solver = fftls.Solver(0)
+    eb = np.diag([1.0, 0.0, 0.0])
+    kw = dict(tol=1e-6, max_iter=3000, precision="fp32_refine64", want_strain=False, want_stress=False)
     try:
-        train, _ = ws.make_dataset(solver, 48, 32, first_seed=5000, concurrency=8)
-        held, _ = ws.make_dataset(solver, 8, 32, first_seed=9000, concurrency=8)
+        train, _ = ws.make_dataset(solver, 192, 32, first_seed=5000, concurrency=8)
+        held, _ = ws.make_dataset(solver, 2, 256, first_seed=9000, concurrency=2)
         assert all(d["converged"] for d in train + held)
         net = ws.WarmNet(seed=0)
-        losses = net.train(train, epochs=12)
+        losses = net.train(train, epochs=16)
         assert losses[-1] < 0.6 * losses[0]
-        zero, warm, err_zero, err_warm = [], [], [], []
+        zero, warm, err_zero, err_warm, t_zero, t_warm = [], [], [], [], [], []
         for d in held:
             lam, mu = MS.young_poisson_phases([(1.0, 0.3), (d["contrast"], 0.3)])
-            eb = np.diag([1.0, 0.0, 0.0])
-            r0 = solver.solve(d["phase"], lam, mu, eb, "R", "AS", tol=1e-6, max_iter=3000, precision="fp64",
-                              want_strain=False, want_stress=False)
-            e0 = net.initial_strain(d["phase"], d["contrast"])
+            ph, c = d["phase"], d["contrast"]
+            solve = lambda **extra: solver.solve(ph, lam, mu, eb, "R", "AS", **kw, **extra)
+            solver.solve(ph, lam, mu, eb, "R", "AS", **dict(kw, max_iter=3), raise_on_error=False)   # tile schedules
+            e0 = net.initial_strain(ph, c)
             fluct = e0.float() - torch.tensor([1.0, 0, 0, 0, 0, 0], device="cuda").view(6, 1, 1, 1)
-            err_warm.append(float(((fluct - d["target"]) ** 2).mean()))
+            err_warm.append(float(((fluct - d["target"].view(fluct.shape)) ** 2).mean()))
             err_zero.append(float((d["target"] ** 2).mean()))
-            r1 = solver.solve(d["phase"], lam, mu, eb, "R", "AS", tol=1e-6, max_iter=3000, precision="fp64",
-                              eps_init=e0, want_strain=False, want_stress=False)
+            del e0, fluct
+            r0, r1 = None, None
+            best0 = best1 = float("inf")
+            for _ in range(3):
+                r0, t = _timed(torch, lambda: solve())
+                best0 = min(best0, t)
+                r1, t = _timed(torch, lambda: solve(eps_init=net.initial_strain(ph, c)))
+                best1 = min(best1, t)
             assert r0.converged and r1.converged
             assert np.abs(r1.mean_stress - r0.mean_stress).max() < 1e-5 * np.abs(r0.mean_stress).max()
             zero.append(r0.iterations)
             warm.append(r1.iterations)
+            t_zero.append(best0)
+            t_warm.append(best1)
     finally:
         solver.close()
     assert np.mean(err_warm) < 0.7 * np.mean(err_zero)
-    assert np.mean(warm) <= np.mean(zero) + 0.5
+    assert sum(warm) <= sum(zero)
+    assert sum(t_warm) <= 1.03 * sum(t_zero), (t_warm, t_zero, warm, zero)
