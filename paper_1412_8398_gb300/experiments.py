@@ -23,6 +23,8 @@ periodic spheres) built by ``microstructure``.
   (f = 20 %, chi = 1e-4) of Sec. 5.3 at grid length L.
 * ``boolean_reference_study``: N(E0) and its minimum on the 64^3 Boolean model of Sec. 6
   (743 spheres of diameter 5, f = 17 %).
+* ``accelerated_rate_study``: the initial eta, decades and asymptotic eta ratio of the accelerated
+  scheme per operator on that model (where its iterations go);
 * ``modulus_rate_study``: Sec. 6.4, the apparent C~_1111 after each iteration of AS with each
   operator (each at its optimal E0 on the 64^3 model) on the Sec. 6 Boolean model refined to
   L^3, and the iterations after which it stays within 1 % of its converged value.
@@ -206,6 +208,34 @@ def boolean_reference_study(solver, chi=1e-5, green="R", scheme="AS", tol=1e-8, 
             "fraction": float(info["fraction"]), "sweep": sweep, "optimal_E0": E0, "optimal_iterations": N}
 
 
+def accelerated_rate_study(solver, chi=1e-5, greens=("R", "C", "W", "MS"), E0_grid=(0.03, 0.05, 0.07, 0.09, 0.12),
+                           tol=1e-8, max_iter=1500, seed=39, looser=(256.0, 512.0)):
+    """Where the accelerated scheme's iterations go on the Sec. 6 instance (64^3, 17 %, chi): per
+    operator and reference Young's modulus E0 (nu0 = 0.25, FP64, the paper's eta-only criterion), the
+    initial eta, the decades from it to tol, the asymptotic eta ratio per iteration (geometric mean
+    over the last 100 iterations), the iterations to tol, and the iterations to thresholds `looser`
+    times tol (a test of readings of eta's normalisation)."""
+    ph, info = MS.boolean_spheres((64, 64, 64), 2.5, 0.17, seed=seed)
+    lam, mu = paper_phases(chi, 3)
+    eb = np.diag([1.0, 0.0, 0.0])
+    rows = []
+    for g in greens:
+        for E0 in E0_grid:
+            l0, m0 = lame(float(E0), 0.25)
+            r = solver.solve(ph, lam, mu, eb, g, "AS", lam0=l0, mu0=m0, tol=tol, max_iter=max_iter, precision="fp64",
+                             want_strain=False, want_stress=False, history=True, raise_on_error=False, eta_only=True)
+            eta = np.asarray(r.eta_history, dtype=np.float64)
+            n = eta.size
+            k0 = max(0, n - 101)
+            ratio = float((eta[-1] / eta[k0]) ** (1.0 / (n - 1 - k0))) if n - 1 > k0 and eta[k0] > 0 else float("nan")
+            to = {f"x{int(f)}": int(np.argmax(eta <= f * tol)) + 1 if (eta <= f * tol).any() else None for f in looser}
+            rows.append({"green": g, "E0": float(E0), "iterations": int(r.iterations), "converged": bool(r.converged),
+                         "eta0": float(eta[0]), "decades": float(np.log10(eta[0] / tol)), "ratio": ratio,
+                         "iterations_to_looser": to})
+    return {"chi": chi, "tol": tol, "spheres": int(info["n_centers"]), "fraction": float(info["fraction"]),
+            "rows": rows}
+
+
 def boolean_model(L: int, seed: int = 39):
     """The Sec. 6 Boolean model (spheres of diameter 5 on 64^3, f = 17 %) at L^3: the generator draws
     the same number of centres at the same relative positions for any L when the radius scales with
@@ -306,7 +336,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="the paper's studies on the GPU path, one JSON line per case")
     ap.add_argument("--study", action="append",
                     choices=["four_cell", "four_cell_floor", "periodic_sphere", "eight_cube", "boolean_reference",
-                             "modulus_rate"],
+                             "modulus_rate", "accelerated_rate"],
                     help="run only these studies (repeatable; default: all)")
     ap.add_argument("--cube-sizes", default="128,256", help="grid lengths of the eight-cube study")
     ap.add_argument("--cell-sizes", default="512", help="grid lengths of the four-cell study (up to 2048)")
@@ -333,6 +363,8 @@ def main(argv=None):
         if "modulus_rate" in studies:  # quasi-porous at 512^3, quasi-rigid at 256^3 (Figs. itPorous, itRigid)
             for L, chi in ((512, 1e-4), (256, 1e4)):
                 print(json.dumps({"study": "modulus_rate", **modulus_rate_study(s, L, chi)}), flush=True)
+        if "accelerated_rate" in studies and args.study:  # on request only
+            print(json.dumps({"study": "accelerated_rate", **accelerated_rate_study(s)}), flush=True)
         if "boolean_reference" in studies:
             for g in ("R", "W", "C"):
                 for eta_only in (True, False):
