@@ -217,6 +217,24 @@ __device__ __forceinline__ void tile_store(const T2* tile, T2* g, long long gstr
   }
 }
 
+// two adjacent complex values (16-byte aligned in FP32: one vector store)
+__device__ __forceinline__ void store_pair(float2* d, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(d) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store_pair(double2* d, double2 a, double2 b) {
+  d[0] = a;
+  d[1] = b;
+}
+__device__ __forceinline__ void load_pair(const float2* d, float2& a, float2& b) {
+  const float4 v = *reinterpret_cast<const float4*>(d);
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void load_pair(const double2* d, double2& a, double2& b) {
+  a = d[0];
+  b = d[1];
+}
+
 // ---------------------------------------------------------------------------
 // K1: constitutive law + forward x1 transform (real -> half complex)
 // ---------------------------------------------------------------------------
@@ -244,7 +262,7 @@ __device__ __forceinline__ void k_fwd_x_body(const IterArgs<T>& a, const AxisPla
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < 8 * 2 * NC; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
 
-  const FastDiv fL = make_fastdiv(L1), fH = make_fastdiv(H), fNP = make_fastdiv(NP);
+  const FastDiv fL = make_fastdiv(L1), fH = make_fastdiv(H);
   for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
     const int nl = (int)min((long long)G, nlines - l0);
     T accf[2 * NC];
@@ -314,21 +332,29 @@ __device__ __forceinline__ void k_fwd_x_body(const IterArgs<T>& a, const AxisPla
       if (ln < nlines) prefetch_voxels<T>(a.eps, a.phase, g.N, NC, ln * L1, (int)min((long long)G, nlines - ln) * L1);
     }
     tile_fft_ct<CP, NP, true>(tile, nl, BS, pl[0], tws, false);
-    for (int idx = threadIdx.x; idx < nl * H * NP; idx += blockDim.x) {
-      const int rest = fdiv(idx, fNP);
-      const int p = idx - rest * NP;
-      const int gl = fdiv(rest, fH), k = rest - gl * H;
-      const T2 Z = tile[gl * BS + prow(__ldg(&pos[k]), 1) * CP + p];
-      const T2 Zm = tile[gl * BS + prow(__ldg(&pos[k == 0 ? 0 : L1 - k]), 1) * CP + p];
-      T2 A, B;
-      A.x = (T)0.5 * (Z.x + Zm.x);
-      A.y = (T)0.5 * (Z.y - Zm.y);
-      B.x = (T)0.5 * (Z.y + Zm.y);
-      B.y = (T)-0.5 * (Z.x - Zm.x);
+    // untangle the packed real transforms: one thread per mode k, every component of it
+    for (int idx = threadIdx.x; idx < nl * H; idx += blockDim.x) {
+      const int gl = fdiv(idx, fH), k = idx - gl * H;
+      const T2* r0 = tile + gl * BS + prow(__ldg(&pos[k]), 1) * CP;
+      const T2* r1 = tile + gl * BS + prow(__ldg(&pos[k == 0 ? 0 : L1 - k]), 1) * CP;
       const long long m = (l0 + gl) * (long long)H + k;
-      const int o0 = 2 * p, o1 = 2 * p + 1;
-      (o0 < NC ? a.specA : a.specB)[m * NC + (o0 % NC)] = A;
-      if (o1 < nout) (o1 < NC ? a.specA : a.specB)[m * NC + (o1 % NC)] = B;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const T2 Z = r0[p], Zm = r1[p];
+        T2 A, B;
+        A.x = (T)0.5 * (Z.x + Zm.x);
+        A.y = (T)0.5 * (Z.y - Zm.y);
+        B.x = (T)0.5 * (Z.y + Zm.y);
+        B.y = (T)-0.5 * (Z.x - Zm.x);
+        const int o0 = 2 * p, o1 = 2 * p + 1;
+        T2* d0 = (o0 < NC ? a.specA : a.specB) + m * NC + (o0 % NC);
+        if (NC % 2 == 0 && o1 < nout && (o0 < NC) == (o1 < NC)) {
+          store_pair(d0, A, B);   // components o0 (even), o1 adjacent in one spectrum: 16-byte aligned
+        } else {
+          *d0 = A;
+          if (o1 < nout) (o1 < NC ? a.specA : a.specB)[m * NC + (o1 % NC)] = B;
+        }
+      }
     }
     __syncthreads();
   }
@@ -423,36 +449,44 @@ __device__ __forceinline__ void k_eta_stencil_body(const IterArgs<T>& a, const A
   double acce = 0.0;
   const int zstart = z0 - (CEN ? 2 : 1);
   const int zend = CEN ? z1 : z1 - 1;
+  // a thread's (at most kEFill) halo-tile elements: their place in the shared tile and in an x3-plane,
+  // the same for every plane of the march
+  constexpr int kEFill = (HR * HC + kEThreads - 1) / kEThreads;
+  int soff[kEFill], goff[kEFill];
+#pragma unroll
+  for (int u = 0; u < kEFill; ++u) {
+    const int e = threadIdx.x + u * kEThreads;
+    soff[u] = -1;
+    goff[u] = 0;
+    if (e < HR * HC) {
+      const int r = e / HC, ci = e - r * HC;
+      soff[u] = r * SX + ci;
+      goff[u] = wrap_index(y0 - 1 + r, n2) * n1 + wrap_index(x0 - 1 + ci, n1);
+    }
+  }
   for (int zz = zstart; zz <= zend; ++zz) {
     const int z = wrap_index(zz, n3);
     T* S = sS + ((zz - zstart) & 1) * 6 * PL;
-    const long long plane = (long long)z * n2;
-    // sigma on the tile and its halo; a thread's (at most kEFill) elements issue
-    // all their loads before any is used
-    constexpr int kEFill = (HR * HC + kEThreads - 1) / kEThreads;
+    const T* __restrict__ ez = eps + (long long)z * n2 * n1;
+    const uint8_t* __restrict__ pz = phase + (long long)z * n2 * n1;
+    // sigma on the tile and its halo; all of a thread's loads are issued before any is used
     T ev[kEFill][6];
     int pv[kEFill];
 #pragma unroll
     for (int u = 0; u < kEFill; ++u) {
-      const int e = threadIdx.x + u * kEThreads;
-      if (e < HR * HC) {
-        const int r = e / HC, ci = e - r * HC;
-        const int y = wrap_index(y0 - 1 + r, n2), x = wrap_index(x0 - 1 + ci, n1);
-        const long long v = (plane + y) * n1 + x;
-        pv[u] = phase[v];
+      if (soff[u] >= 0) {
+        pv[u] = pz[goff[u]];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) ev[u][c] = eps[(long long)c * N + v];
+        for (int c = 0; c < 6; ++c) ev[u][c] = ez[(long long)c * N + goff[u]];
       }
     }
 #pragma unroll
     for (int u = 0; u < kEFill; ++u) {
-      const int e = threadIdx.x + u * kEThreads;
-      if (e < HR * HC) {
-        const int r = e / HC, ci = e - r * HC;
+      if (soff[u] >= 0) {
         const T* cf = coef + pv[u] * kCoef;
         const T tr = ev[u][0] + ev[u][1] + ev[u][2];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) S[c * PL + r * SX + ci] = cf[1] * ev[u][c] + (c < 3 ? cf[0] * tr : (T)0);
+        for (int c = 0; c < 6; ++c) S[c * PL + soff[u]] = cf[1] * ev[u][c] + (c < 3 ? cf[0] * tr : (T)0);
       }
     }
     __syncthreads();
@@ -1063,25 +1097,35 @@ __device__ __forceinline__ void k_inv_x_body(const IterArgs<T>& a, const AxisPla
     const int nl = (int)min((long long)G, nlines - l0);
     // eps and the phase ids are read after the transform: bring them towards L2 now
     if (a.update != kUpdDirectTau) prefetch_voxels<T>(a.eps, a.phase, g.N, NC, l0 * L1, nl * L1);
-    for (int idx = threadIdx.x; idx < nl * H * NPI; idx += blockDim.x) {
-      const int p = idx % NPI;
-      const int rest = idx / NPI;
-      const int gl = fdiv(rest, fH), k = rest - gl * H;
+    // pack pairs of components into complex lines: one thread per mode k, every component of it
+    for (int idx = threadIdx.x; idx < nl * H; idx += blockDim.x) {
+      const int gl = fdiv(idx, fH), k = idx - gl * H;
       const long long m = (l0 + gl) * (long long)H + k;
-      T2 A = a.specA[m * NC + 2 * p];
-      T2 B;
-      if (2 * p + 1 < NC) B = a.specA[m * NC + 2 * p + 1];
-      else { B.x = (T)0; B.y = (T)0; }
-      if (k == 0 || 2 * k == L1) { A.y = (T)0; B.y = (T)0; }
-      T2 z;
-      z.x = A.x - B.y;
-      z.y = A.y + B.x;
-      tile[gl * BS + prow(__ldg(&pos[k]), 1) * CP + p] = z;
-      if (k > 0 && L1 - k >= H) {
-        T2 zm;
-        zm.x = A.x + B.y;
-        zm.y = B.x - A.y;
-        tile[gl * BS + prow(__ldg(&pos[L1 - k]), 1) * CP + p] = zm;
+      const bool edge = k == 0 || 2 * k == L1;
+      const bool mirror = k > 0 && L1 - k >= H;
+      T2* r0 = tile + gl * BS + prow(__ldg(&pos[k]), 1) * CP;
+      T2* r1 = tile + gl * BS + prow(__ldg(&pos[mirror ? L1 - k : k]), 1) * CP;
+#pragma unroll
+      for (int p = 0; p < NPI; ++p) {
+        T2 A, B;
+        if (NC % 2 == 0) {
+          load_pair(a.specA + m * NC + 2 * p, A, B);   // 16-byte aligned in FP32
+        } else {
+          A = a.specA[m * NC + 2 * p];
+          if (2 * p + 1 < NC) B = a.specA[m * NC + 2 * p + 1];
+          else { B.x = (T)0; B.y = (T)0; }
+        }
+        if (edge) { A.y = (T)0; B.y = (T)0; }
+        T2 z;
+        z.x = A.x - B.y;
+        z.y = A.y + B.x;
+        r0[p] = z;
+        if (mirror) {
+          T2 zm;
+          zm.x = A.x + B.y;
+          zm.y = B.x - A.y;
+          r1[p] = zm;
+        }
       }
     }
     __syncthreads();
