@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--warm-epochs", type=int, default=4)
     ap.add_argument("--warm-batch", type=int, default=1, help="samples per training step of the warm start")
     ap.add_argument("--warm-lr", type=float, default=5e-4, help="initial learning rate (decays 10x over training)")
+    ap.add_argument("--warm-tc", action="store_true", help="train the warm start on the tensor cores")
     ap.add_argument("--ncu-region", action="store_true",
                     help="for ncu --profile-from-start off: tune and warm up on the workload, then bracket two "
                          "FP32 iterations launched without graphs with the profiler start / stop calls")
@@ -579,7 +580,7 @@ def run_warmstart(args, rank, local, world):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     losses = net.train(data, epochs=args.warm_epochs, batch=args.warm_batch, lr=args.warm_lr,
-                       lr_final=0.1 * args.warm_lr)
+                       lr_final=0.1 * args.warm_lr, tensor_cores=args.warm_tc)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del data
@@ -623,7 +624,7 @@ def run_warmstart(args, rank, local, world):
         "data": "synthetic", "dtype": "f32+f64 solve, bf16 inference",
         "config": {"workload": f"warmstart_train_{args.warmstart}x64^3_apply_{args.warm_apply}x256^3_boolean",
                    "train_samples": args.warmstart, "epochs": args.warm_epochs, "batch": args.warm_batch,
-                   "lr": args.warm_lr,
+                   "lr": args.warm_lr, "training": "tensor cores (BF16)" if args.warm_tc else "FP32",
                    "parameters": WS.parameter_count()},
         "data_seconds": t_data, "train_seconds": t_train, "train_loss_per_epoch": losses,
         "iterations": {"zero_init": tot("zero", "iterations"), "warm": tot("warm", "iterations"),

@@ -138,6 +138,50 @@ fftls_status fftls_nn_tc_conv3d(const void* x, const void* packed, const float* 
 fftls_status fftls_nn_tc_conv_phase(const uint8_t* phase, const float* w, const float* bias, void* y, const int n[3],
                                     int c_out, float log_contrast, int relu, void* stream);
 
+/* ---- Tensor-core training pieces (same layouts as above) ---- */
+
+/* Scratch floats of fftls_nn_tc_conv3d_backward_weights (0 for invalid arguments). */
+size_t fftls_nn_tc_wgrad_scratch(int batch, int c_in, int c_out, const int n[3], int ksize);
+
+/* Weight and bias gradients of fftls_nn_tc_conv3d on the tensor cores: dw[o][i][k] = sum over the
+ * batch and the output voxels v of dy(v)[o] x'(v + offset(k))[i] and db[o] = sum of dy(v)[o] (db may be
+ * NULL), FP32 [c_out][c_in][k^3], written.  x: the layer input (channels-last BF16, c_in channels) on
+ * the grid in_mode gives (as in fftls_nn_tc_conv3d: 0 the grid n, 1 n/2 upsampled, 2 2n pooled); dy:
+ * the gradient at the layer output before its activation, channels-last BF16 on the grid n.  Products
+ * of BF16 values accumulated in FP32 per voxel tile, the tiles summed in a fixed order in FP64.
+ * scratch: at least fftls_nn_tc_wgrad_scratch(...) floats of device memory. */
+fftls_status fftls_nn_tc_conv3d_backward_weights(const void* x, const void* dy, float* dw, float* db, int batch,
+                                                 int c_in, int c_out, const int n[3], int ksize, int in_mode,
+                                                 float* scratch, size_t scratch_floats, void* stream);
+
+/* Scratch floats of fftls_nn_tc_conv_phase_backward_weights. */
+size_t fftls_nn_tc_phase_wgrad_scratch(const int n[3]);
+
+/* Weight and bias gradients of fftls_nn_tc_conv_phase (one sample): dw [c_out][2][27] FP32 (channel 0:
+ * sums of dy(v)[o] over the voxels whose neighbour at offset k is phase 1; channel 1: log_contrast
+ * times the sum of dy(v)[o], the constant input channel), db [c_out] (may be NULL), written; dy
+ * channels-last BF16 with 8 stored channels. */
+fftls_status fftls_nn_tc_conv_phase_backward_weights(const uint8_t* phase, const void* dy, float* dw, float* db,
+                                                     const int n[3], int c_out, float log_contrast, float* scratch,
+                                                     size_t scratch_floats, void* stream);
+
+/* Channels-last BF16 y [batch][voxels][cs] from planar FP32 x [batch][channels][voxels] (channels <= 64,
+ * cs the stored channel count, the padding channels zero). */
+fftls_status fftls_nn_tc_from_planar(const float* x, void* y, int batch, int channels, long long voxels, void* stream);
+
+/* Channels-last BF16 elementwise pieces of the backward pass; count = values (a multiple of 8):
+ * dy = y > 0 ? dy : 0 (ReLU backward, y the activation); y += x. */
+fftls_status fftls_nn_tc_relu_backward(void* dy, const void* y, long long count, void* stream);
+fftls_status fftls_nn_tc_add(void* y, const void* x, long long count, void* stream);
+
+/* Adjoints of the 2x resampling on channels-last BF16 (nc = the coarse grid): upsampling's, dx on nc =
+ * the sum of dy (grid 2 nc) over each 2x2x2 block (written); mean pooling's, dx on 2 nc (=|+=) dy (grid
+ * nc) / 8 spread over each block. */
+fftls_status fftls_nn_tc_upsample2_backward(const void* dy, void* dx, int batch, int channels, const int nc[3],
+                                            void* stream);
+fftls_status fftls_nn_tc_pool2_backward(const void* dy, void* dx, int batch, int channels, const int nc[3],
+                                        int accumulate, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

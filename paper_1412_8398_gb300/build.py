@@ -22,7 +22,8 @@ SOURCES = ["fftls_kernels_x32.cu", "fftls_kernels_x64.cu", "fftls_kernels_y32.cu
            "fftls_kernels_z32.cu", "fftls_kernels_z64.cu", "fftls_kernels_x32g.cu", "fftls_kernels_x64g.cu",
            "fftls_kernels_y32g.cu", "fftls_kernels_y64g.cu", "fftls_kernels_z32g.cu", "fftls_kernels_z64g.cu",
            "fftls_solver.cu", "fftls_nn.cu", "fftls_nn_tc.cu",
-           "fftls_nn_tc_conv1.cu", "fftls_nn_tc_conv3.cu", "fftls_nn_tc_conv3p.cu"]
+           "fftls_nn_tc_conv1.cu", "fftls_nn_tc_conv3.cu", "fftls_nn_tc_conv3p.cu",
+           "fftls_nn_tc_wgrad1.cu", "fftls_nn_tc_wgrad3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -135,6 +135,210 @@ __global__ void __launch_bounds__(kThreads) k_conv_phase(const uint8_t* __restri
   }
 }
 
+// dW[o][i][k] (FP32 layout of the layer, i < cin) and db[o] from the tiles' partial sums, summed in FP64
+// in tile order
+__global__ void k_wgrad_reduce(const float* __restrict__ part, const float* __restrict__ partb, float* __restrict__ dw,
+                               float* __restrict__ db, int tiles, int cout, int cin, int C, int KT) {
+  const int ncols = KT * C;
+  const long long M = (long long)cout * cin * KT;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < M + cout; q += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    if (q < M) {
+      const int k = (int)(q % KT);
+      const long long r = q / KT;
+      const int i = (int)(r % cin), o = (int)(r / cin);
+      const size_t col = (size_t)o * ncols + (size_t)k * C + i;
+      for (int t = 0; t < tiles; ++t) s += part[(size_t)t * cout * ncols + col];
+      dw[q] = (float)s;
+    } else {
+      const int o = (int)(q - M);
+      for (int t = 0; t < tiles; ++t) s += partb[(size_t)t * cout + o];
+      if (db) db[o] = (float)s;
+    }
+  }
+}
+
+__device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float2 v = __bfloat1622float2(h[e]);
+    f[2 * e] = v.x;
+    f[2 * e + 1] = v.y;
+  }
+}
+
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+  uint4 u;
+  u.x = pack_bf16(f[0], f[1]);
+  u.y = pack_bf16(f[2], f[3]);
+  u.z = pack_bf16(f[4], f[5]);
+  u.w = pack_bf16(f[6], f[7]);
+  return u;
+}
+
+// channels-last BF16 [b][v][cs] from planar FP32 [b][c][N] (channels c..cs-1 zero)
+__global__ void k_cl_from_planar(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, int c, int cs, long long N,
+                                 long long total8) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total8; t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t % (cs / 8));
+    const long long bv = t / (cs / 8);
+    const long long b = bv / N, v = bv - b * N;
+    float f[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int ch = q * 8 + e;
+      f[e] = ch < c ? x[((size_t)b * c + ch) * N + v] : 0.f;
+    }
+    reinterpret_cast<uint4*>(y)[t] = pack8(f);
+  }
+}
+
+// dy = y > 0 ? dy : 0, eight values at a time
+__global__ void k_cl_relu_bwd(__nv_bfloat16* __restrict__ dy, const __nv_bfloat16* __restrict__ y, long long total8) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total8; t += (long long)gridDim.x * blockDim.x) {
+    float g[8], a[8];
+    unpack8(reinterpret_cast<const uint4*>(dy)[t], g);
+    unpack8(reinterpret_cast<const uint4*>(y)[t], a);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) g[e] = a[e] > 0.f ? g[e] : 0.f;
+    reinterpret_cast<uint4*>(dy)[t] = pack8(g);
+  }
+}
+
+// coarse (grid m) = sum over each 2x2x2 block of fine (grid 2m): the adjoint of nearest upsampling
+__global__ void k_cl_up2_bwd(const __nv_bfloat16* __restrict__ fine, __nv_bfloat16* __restrict__ coarse, int cs, int m1,
+                             int m2, int m3, long long total8) {
+  const int cq = cs / 8;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total8; t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t % cq);
+    long long r = t / cq;
+    const int a1 = (int)(r % m1);
+    r /= m1;
+    const int a2 = (int)(r % m2);
+    r /= m2;
+    const int a3 = (int)(r % m3);
+    const long long b = r / m3;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) {
+      const size_t v = (((size_t)b * 2 * m3 + 2 * a3 + (c8 >> 2)) * 2 * m2 + 2 * a2 + ((c8 >> 1) & 1)) * 2 * m1 + 2 * a1 +
+                       (c8 & 1);
+      float f[8];
+      unpack8(reinterpret_cast<const uint4*>(fine)[v * cq + q], f);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) s[e] += f[e];
+    }
+    reinterpret_cast<uint4*>(coarse)[t] = pack8(s);
+  }
+}
+
+// fine (grid 2m) (+)= coarse / 8 spread over each 2x2x2 block: the adjoint of mean pooling
+__global__ void k_cl_pool2_bwd(const __nv_bfloat16* __restrict__ coarse, __nv_bfloat16* __restrict__ fine, int cs,
+                               int m1, int m2, int m3, int accumulate, long long total8) {
+  const int cq = cs / 8;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total8; t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t % cq);
+    long long r = t / cq;
+    const int f1 = (int)(r % (2 * m1));
+    r /= 2 * m1;
+    const int f2 = (int)(r % (2 * m2));
+    r /= 2 * m2;
+    const int f3 = (int)(r % (2 * m3));
+    const long long b = r / (2 * m3);
+    const size_t u = (((size_t)b * m3 + (f3 >> 1)) * m2 + (f2 >> 1)) * m1 + (f1 >> 1);
+    float g[8];
+    unpack8(reinterpret_cast<const uint4*>(coarse)[u * cq + q], g);
+    if (accumulate) {
+      float o[8];
+      unpack8(reinterpret_cast<const uint4*>(fine)[t], o);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) g[e] = o[e] + 0.125f * g[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) g[e] *= 0.125f;
+    }
+    reinterpret_cast<uint4*>(fine)[t] = pack8(g);
+  }
+}
+
+// y += x, eight values at a time
+__global__ void k_cl_add(__nv_bfloat16* __restrict__ y, const __nv_bfloat16* __restrict__ x, long long total8) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total8; t += (long long)gridDim.x * blockDim.x) {
+    float a[8], b[8];
+    unpack8(reinterpret_cast<const uint4*>(y)[t], a);
+    unpack8(reinterpret_cast<const uint4*>(x)[t], b);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a[e] += b[e];
+    reinterpret_cast<uint4*>(y)[t] = pack8(a);
+  }
+}
+
+// weight gradient of the first layer (fftls_nn_tc_conv_phase): part[tile][o][k] = sum over the tile's
+// voxels of dy(v)[o] 1{phase(v + d(k)) = 1}, and part[tile][o][27] = sum of dy(v)[o].  A block stages the
+// indicator of a 32 x 8 x 4 tile with its halo and the tile's dy in shared memory; thread (o, k) sums
+// over the tile's voxels in FP32.
+constexpr int kWX = 32, kWY = 8, kWZ = 4;
+__global__ void __launch_bounds__(kThreads) k_wgrad_phase(const uint8_t* __restrict__ ph,
+                                                          const __nv_bfloat16* __restrict__ dy, float* __restrict__ part,
+                                                          int n1, int n2, int n3, int tiles1, int tiles2, int cout) {
+  __shared__ float sp[kWZ + 2][kWY + 2][kWX + 2];
+  __shared__ float sg[kWZ * kWY * kWX][8];
+  int t = blockIdx.x;
+  const int i1 = t % tiles1;
+  t /= tiles1;
+  const int i2 = t % tiles2, i3 = t / tiles2;
+  const int x0 = i1 * kWX, y0 = i2 * kWY, z0 = i3 * kWZ;
+  constexpr int NP = (kWZ + 2) * (kWY + 2) * (kWX + 2);
+  for (int q = threadIdx.x; q < NP; q += kThreads) {
+    const int px = q % (kWX + 2), rq = q / (kWX + 2);
+    const int py = rq % (kWY + 2), pz = rq / (kWY + 2);
+    (&sp[0][0][0])[q] =
+        __ldg(ph + ((size_t)wrapn(z0 + pz - 1, n3) * n2 + wrapn(y0 + py - 1, n2)) * n1 + wrapn(x0 + px - 1, n1)) == 1
+            ? 1.f
+            : 0.f;
+  }
+  for (int m = threadIdx.x; m < kWZ * kWY * kWX; m += kThreads) {
+    const int x = x0 + (m & 31), y = y0 + ((m >> 5) & 7), z = z0 + (m >> 8);
+    float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (x < n1 && y < n2 && z < n3) unpack8(reinterpret_cast<const uint4*>(dy)[((size_t)z * n2 + y) * n1 + x], g);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sg[m][e] = g[e];
+  }
+  __syncthreads();
+  const int q = threadIdx.x;
+  if (q >= cout * 28) return;
+  const int o = q / 28, k = q % 28;
+  const int dz = k / 9, dyy = (k / 3) % 3, dx = k % 3;
+  float s4[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int m = 0; m < kWZ * kWY * kWX; m += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int mm = m + u;
+      const float f = k < 27 ? sp[(mm >> 8) + dz][((mm >> 5) & 7) + dyy][(mm & 31) + dx] : 1.f;
+      s4[u] += f * sg[mm][o];
+    }
+  }
+  part[((size_t)blockIdx.x * cout + o) * 28 + k] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+}
+
+// dW of the first layer [cout][2][27] and db: channel 0 from the indicator sums, channel 1 = lc times
+// the sum of dy (the constant input channel), summed over tiles in FP64
+__global__ void k_wgrad_phase_reduce(const float* __restrict__ part, float* __restrict__ dw, float* __restrict__ db,
+                                     int tiles, int cout, float lc) {
+  for (int q = threadIdx.x; q < cout * 28; q += blockDim.x) {
+    const int o = q / 28, k = q % 28;
+    double s = 0.0;
+    for (int t = 0; t < tiles; ++t) s += part[((size_t)t * cout + o) * 28 + k];
+    if (k < 27) {
+      dw[(o * 2) * 27 + k] = (float)s;
+    } else {
+      for (int kk = 0; kk < 27; ++kk) dw[(o * 2 + 1) * 27 + kk] = (float)(s * (double)lc);
+      if (db) db[o] = (float)s;
+    }
+  }
+}
+
 bool dims_ok(const int* n) { return n && n[0] >= 1 && n[1] >= 1 && n[2] >= 1; }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -206,6 +410,127 @@ fftls_status fftls_nn_tc_conv_phase(const uint8_t* phase, const float* w, const 
   if (tiles > 0x7fffffffLL) return FFTLS_E_UNSUPPORTED_SIZE;
   k_conv_phase<<<(unsigned)tiles, kThreads, 0, (cudaStream_t)stream>>>(
       phase, w, bias, static_cast<__nv_bfloat16*>(y), n[0], n[1], n[2], t1, t2, c_out, log_contrast, relu ? 1 : 0);
+  return cudaGetLastError() == cudaSuccess ? FFTLS_OK : FFTLS_E_CUDA;
+}
+
+size_t fftls_nn_tc_wgrad_scratch(int batch, int c_in, int c_out, const int n[3], int ksize) {
+  if (!dims_ok(n) || batch < 1 || c_in < 1 || c_out < 1 || c_in > 64 || c_out > 64 || (ksize != 1 && ksize != 3))
+    return 0;
+  const int C = stored_of(c_in), MO = (c_out + 15) / 16 > 2 ? 4 : (c_out + 15) / 16;
+  const long long tiles = wgrad_tiles(n, ksize, C, MO);
+  if (tiles == 0) return 0;
+  return (size_t)batch * tiles * c_out * ((size_t)ksize * ksize * ksize * C + 1);
+}
+
+fftls_status fftls_nn_tc_conv3d_backward_weights(const void* x, const void* dy, float* dw, float* db, int batch,
+                                                 int c_in, int c_out, const int n[3], int ksize, int in_mode,
+                                                 float* scratch, size_t scratch_floats, void* stream) {
+  if (!x || !dy || !dw || !scratch || !dims_ok(n) || batch < 1 || c_in < 1 || c_out < 1 || c_in > 64 ||
+      c_out > 64 || (ksize != 1 && ksize != 3) || in_mode < 0 || in_mode > 2 || !aligned16(x) || !aligned16(dy))
+    return FFTLS_E_INVALID_ARG;
+  if (in_mode == 1 && ((n[0] | n[1] | n[2]) & 1)) return FFTLS_E_INVALID_ARG;
+  const size_t need = fftls_nn_tc_wgrad_scratch(batch, c_in, c_out, n, ksize);
+  if (need == 0) return FFTLS_E_UNSUPPORTED_SIZE;
+  if (scratch_floats < need) return FFTLS_E_INVALID_ARG;
+  const int C = stored_of(c_in), MO = (c_out + 15) / 16 > 2 ? 4 : (c_out + 15) / 16;
+  const int KT = ksize * ksize * ksize;
+  WgradArgs a{};
+  a.x = static_cast<const __nv_bfloat16*>(x);
+  a.dy = static_cast<const __nv_bfloat16*>(dy);
+  a.n1 = n[0];
+  a.n2 = n[1];
+  a.n3 = n[2];
+  const int f = in_mode == 1 ? -1 : in_mode == 2 ? 1 : 0;
+  a.m1 = f < 0 ? n[0] / 2 : n[0] << f;
+  a.m2 = f < 0 ? n[1] / 2 : n[1] << f;
+  a.m3 = f < 0 ? n[2] / 2 : n[2] << f;
+  a.mode = in_mode;
+  a.cout = c_out;
+  a.cso = stored_of(c_out);
+  a.ncols = KT * C;
+  a.tiles = (int)wgrad_tiles(n, ksize, C, MO);
+  a.part = scratch;
+  a.partb = scratch + (size_t)batch * a.tiles * c_out * a.ncols;
+  const int tv = wgrad_tile_voxels(n, ksize, C, MO);
+  cudaStream_t s = (cudaStream_t)stream;
+  const fftls_status st = ksize == 3 ? launch_wgrad_k3(in_mode == 2, C, MO, a, n, batch, tv, s)
+                                     : launch_wgrad_k1(in_mode == 2, C, MO, a, n, batch, tv, s);
+  if (st != FFTLS_OK) return st;
+  const long long M = (long long)c_out * c_in * KT + c_out;
+  k_wgrad_reduce<<<grid_for(M), kThreads, 0, s>>>(a.part, a.partb, dw, db, batch * a.tiles, c_out, c_in, C, KT);
+  return cudaGetLastError() == cudaSuccess ? FFTLS_OK : FFTLS_E_CUDA;
+}
+
+size_t fftls_nn_tc_phase_wgrad_scratch(const int n[3]) {
+  if (!dims_ok(n)) return 0;
+  const long long tiles = (long long)((n[0] + kWX - 1) / kWX) * ((n[1] + kWY - 1) / kWY) * ((n[2] + kWZ - 1) / kWZ);
+  return (size_t)tiles * 8 * 28;
+}
+
+fftls_status fftls_nn_tc_conv_phase_backward_weights(const uint8_t* phase, const void* dy, float* dw, float* db,
+                                                     const int n[3], int c_out, float log_contrast, float* scratch,
+                                                     size_t scratch_floats, void* stream) {
+  if (!phase || !dy || !dw || !scratch || !dims_ok(n) || c_out < 1 || c_out > 8 || !aligned16(dy))
+    return FFTLS_E_INVALID_ARG;
+  if (scratch_floats < fftls_nn_tc_phase_wgrad_scratch(n)) return FFTLS_E_INVALID_ARG;
+  const int t1 = (n[0] + kWX - 1) / kWX, t2 = (n[1] + kWY - 1) / kWY, t3 = (n[2] + kWZ - 1) / kWZ;
+  const long long tiles = (long long)t1 * t2 * t3;
+  if (tiles > 0x7fffffffLL) return FFTLS_E_UNSUPPORTED_SIZE;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_wgrad_phase<<<(unsigned)tiles, kThreads, 0, s>>>(phase, static_cast<const __nv_bfloat16*>(dy), scratch, n[0], n[1],
+                                                     n[2], t1, t2, c_out);
+  if (cudaGetLastError() != cudaSuccess) return FFTLS_E_CUDA;
+  k_wgrad_phase_reduce<<<1, kThreads, 0, s>>>(scratch, dw, db, (int)tiles, c_out, log_contrast);
+  return cudaGetLastError() == cudaSuccess ? FFTLS_OK : FFTLS_E_CUDA;
+}
+
+fftls_status fftls_nn_tc_from_planar(const float* x, void* y, int batch, int channels, long long voxels, void* stream) {
+  if (!x || !y || batch < 1 || channels < 1 || channels > 64 || voxels < 1 || !aligned16(y)) return FFTLS_E_INVALID_ARG;
+  const int cs = stored_of(channels);
+  const long long total8 = (long long)batch * voxels * (cs / 8);
+  k_cl_from_planar<<<grid_for(total8), kThreads, 0, (cudaStream_t)stream>>>(x, static_cast<__nv_bfloat16*>(y), channels,
+                                                                            cs, voxels, total8);
+  return cudaGetLastError() == cudaSuccess ? FFTLS_OK : FFTLS_E_CUDA;
+}
+
+fftls_status fftls_nn_tc_relu_backward(void* dy, const void* y, long long count, void* stream) {
+  if (!dy || !y || count < 0 || (count & 7) || !aligned16(dy) || !aligned16(y)) return FFTLS_E_INVALID_ARG;
+  if (count == 0) return FFTLS_OK;
+  k_cl_relu_bwd<<<grid_for(count / 8), kThreads, 0, (cudaStream_t)stream>>>(
+      static_cast<__nv_bfloat16*>(dy), static_cast<const __nv_bfloat16*>(y), count / 8);
+  return cudaGetLastError() == cudaSuccess ? FFTLS_OK : FFTLS_E_CUDA;
+}
+
+fftls_status fftls_nn_tc_upsample2_backward(const void* dy, void* dx, int batch, int channels, const int nc[3],
+                                            void* stream) {
+  if (!dy || !dx || batch < 1 || channels < 1 || channels > 64 || !dims_ok(nc) || !aligned16(dy) || !aligned16(dx) ||
+      dy == dx)
+    return FFTLS_E_INVALID_ARG;
+  const int cs = stored_of(channels);
+  const long long total8 = (long long)batch * nc[0] * nc[1] * nc[2] * (cs / 8);
+  k_cl_up2_bwd<<<grid_for(total8), kThreads, 0, (cudaStream_t)stream>>>(
+      static_cast<const __nv_bfloat16*>(dy), static_cast<__nv_bfloat16*>(dx), cs, nc[0], nc[1], nc[2], total8);
+  return cudaGetLastError() == cudaSuccess ? FFTLS_OK : FFTLS_E_CUDA;
+}
+
+fftls_status fftls_nn_tc_pool2_backward(const void* dy, void* dx, int batch, int channels, const int nc[3],
+                                        int accumulate, void* stream) {
+  if (!dy || !dx || batch < 1 || channels < 1 || channels > 64 || !dims_ok(nc) || !aligned16(dy) || !aligned16(dx) ||
+      dy == dx)
+    return FFTLS_E_INVALID_ARG;
+  const int cs = stored_of(channels);
+  const long long total8 = (long long)batch * 8 * nc[0] * nc[1] * nc[2] * (cs / 8);
+  k_cl_pool2_bwd<<<grid_for(total8), kThreads, 0, (cudaStream_t)stream>>>(
+      static_cast<const __nv_bfloat16*>(dy), static_cast<__nv_bfloat16*>(dx), cs, nc[0], nc[1], nc[2],
+      accumulate ? 1 : 0, total8);
+  return cudaGetLastError() == cudaSuccess ? FFTLS_OK : FFTLS_E_CUDA;
+}
+
+fftls_status fftls_nn_tc_add(void* y, const void* x, long long count, void* stream) {
+  if (!y || !x || count < 0 || (count & 7) || !aligned16(y) || !aligned16(x)) return FFTLS_E_INVALID_ARG;
+  if (count == 0) return FFTLS_OK;
+  k_cl_add<<<grid_for(count / 8), kThreads, 0, (cudaStream_t)stream>>>(static_cast<__nv_bfloat16*>(y),
+                                                                       static_cast<const __nv_bfloat16*>(x), count / 8);
   return cudaGetLastError() == cudaSuccess ? FFTLS_OK : FFTLS_E_CUDA;
 }
 

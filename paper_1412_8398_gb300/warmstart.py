@@ -68,6 +68,18 @@ _TC_PLAN = [
 _TC_OUT = {"enc1a": "a1", "enc1b": "e1", "enc2a": "a2", "enc2b": "e2", "enc3a": "a3", "enc3b": "e3",
            "dec2": "d2", "dec1": "d1", "dec0": "d0"}
 
+# channels-last BF16 gradients of the tensor-core backward: name -> (channels, level)
+_TC_GRADS = {
+    "gy": (6, 0), "gd0": (8, 0), "gu0": (16, 0), "gd1": (16, 1), "gu1": (32, 1), "gd2": (32, 2), "gu2": (64, 2),
+    "ge3": (64, 3), "ga3": (64, 3), "gp2": (32, 3), "ga2": (32, 2), "gp1": (16, 2), "ga1": (16, 1), "gp0": (8, 1),
+}
+
+
+def _stored(c):
+    """Stored channels of a channels-last activation with c channels."""
+    return 8 if c <= 8 else 16 if c <= 16 else 32 if c <= 32 else 64
+
+
 # gradient buffers: name -> (channels, level)
 _GRADS = {
     "gy": (6, 0), "gd0": (8, 0), "gu0": (16, 0), "gd1": (16, 1), "gu1": (32, 1), "gd2": (32, 2), "gu2": (64, 2),
@@ -102,6 +114,17 @@ _NN_SIGNATURES = {
     "fftls_nn_tc_conv3d": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I3,
                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "fftls_nn_tc_conv_phase": (ctypes.c_int, [_P, _P, _P, _P, _I3, ctypes.c_int, ctypes.c_float, ctypes.c_int, _P]),
+    "fftls_nn_tc_wgrad_scratch": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _I3, ctypes.c_int]),
+    "fftls_nn_tc_conv3d_backward_weights": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                           _I3, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t, _P]),
+    "fftls_nn_tc_phase_wgrad_scratch": (ctypes.c_size_t, [_I3]),
+    "fftls_nn_tc_conv_phase_backward_weights": (ctypes.c_int, [_P, _P, _P, _P, _I3, ctypes.c_int, ctypes.c_float, _P,
+                                                               ctypes.c_size_t, _P]),
+    "fftls_nn_tc_from_planar": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _P]),
+    "fftls_nn_tc_relu_backward": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
+    "fftls_nn_tc_add": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
+    "fftls_nn_tc_upsample2_backward": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _I3, _P]),
+    "fftls_nn_tc_pool2_backward": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _I3, ctypes.c_int, _P]),
 }
 STRAIN_SCRATCH = 1536  # FFTLS_NN_STRAIN_SCRATCH
 
@@ -170,6 +193,7 @@ class WarmNet:
         self.losses = []
         self.version = 0          # bumped whenever the parameters change
         self._tc_packed = None    # (version, {layer: packed BF16 weights})
+        self._tc_packed_t = None  # the same, transposed for the input gradient
         self._tc_grid = None
 
     # -- parameters ------------------------------------------------------
@@ -367,60 +391,194 @@ class WarmNet:
                                       float(lr), beta1, beta2, eps, self.steps, self.stream), "adam")
 
     # -- tensor-core inference -------------------------------------------
-    def _tc_weights(self):
-        """Packed BF16 weights of every layer after the first, repacked when the parameters changed."""
-        if self._tc_packed is not None and self._tc_packed[0] == self.version:
-            return self._tc_packed[1]
+    def _tc_weights(self, transposed=False):
+        """Packed BF16 weights of every layer after the first (transposed: for the input gradient),
+        repacked when the parameters changed."""
+        cache = self._tc_packed_t if transposed else self._tc_packed
+        if cache is not None and cache[0] == self.version:
+            return cache[1]
         torch = self.torch
         packed = {}
         for name, ci, co, k, _ in LAYERS[1:]:
-            nbytes = int(self.lib.fftls_nn_tc_packed_bytes(ci, co, k, 0))
+            nbytes = int(self.lib.fftls_nn_tc_packed_bytes(ci, co, k, int(transposed)))
             buf = torch.empty(nbytes, dtype=torch.uint8, device=self.dev)
-            _check(self.lib.fftls_nn_tc_pack(self._w(name), _p(buf), ci, co, k, 0, self.stream), f"pack {name}")
+            _check(self.lib.fftls_nn_tc_pack(self._w(name), _p(buf), ci, co, k, int(transposed), self.stream),
+                   f"pack {name}")
             packed[name] = buf
-        self._tc_packed = (self.version, packed)
+        if transposed:
+            self._tc_packed_t = (self.version, packed)
+        else:
+            self._tc_packed = (self.version, packed)
         return packed
 
-    def _tc_buffers(self, n):
+    def _tc_buffers(self, n, batch=1, train=False):
         n = tuple(int(v) for v in n)
         if any(v % (1 << LEVELS) for v in n):
             raise ValueError(f"grid lengths must be multiples of {1 << LEVELS}")
-        if self._tc_grid == n:
+        key = (n, batch, train)
+        if self._tc_grid == key:
             return
         torch = self.torch
-        vox = lambda lvl: (n[0] >> lvl) * (n[1] >> lvl) * (n[2] >> lvl)
+        vox = lambda lvl: batch * (n[0] >> lvl) * (n[1] >> lvl) * (n[2] >> lvl)
         self.tc = {k: torch.empty(c * vox(l), dtype=torch.bfloat16, device=self.dev) for k, (c, l) in _TC_ACTS.items()}
         self.tc["y"] = torch.empty(6 * vox(0), dtype=torch.float32, device=self.dev)
         self.tc_mean_scratch = torch.empty(STRAIN_SCRATCH, dtype=torch.float64, device=self.dev)
-        self._tc_grid = n
+        self.tcg = {}
+        if train:
+            self.tcg = {k: torch.empty(_stored(c) * vox(l), dtype=torch.bfloat16, device=self.dev)
+                        for k, (c, l) in _TC_GRADS.items()}
+            self.tc_gy = torch.empty(6 * vox(0), dtype=torch.float32, device=self.dev)
+            self.tc_target = torch.empty(6 * vox(0), dtype=torch.float32, device=self.dev)
+            self.tc_loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
+            need = max(self.lib.fftls_nn_tc_wgrad_scratch(batch, ci, co, self._dims(n, lvl), k)
+                       for _, ci, co, k, lvl in LAYERS[1:])
+            need = max(int(need), int(self.lib.fftls_nn_tc_phase_wgrad_scratch(self._dims(n, 0))))
+            self.tc_scratch = torch.empty(need, dtype=torch.float32, device=self.dev)
+            self.tc_dw0 = torch.empty(self.offsets["enc0"][1] + 8, dtype=torch.float32, device=self.dev)
+        self.tc_batch = batch
+        self._tc_grid = key
 
     def forward_tc(self, phase, contrast):
         """The network on the tensor cores for a device phase image (uint8, (n3, n2, n1)); returns the
         FP32 output [6][N]."""
-        n = (phase.shape[2], phase.shape[1], phase.shape[0])
-        self._tc_buffers(n)
+        return self.forward_tc_batch([phase], [contrast])
+
+    def forward_tc_batch(self, phases, contrasts, train=False):
+        """The network on the tensor cores for a batch of phase images of one grid; returns the FP32
+        output [batch][6][N]."""
+        n = (phases[0].shape[2], phases[0].shape[1], phases[0].shape[0])
+        B = len(phases)
+        if self._tc_grid is None or self._tc_grid[0] != n or self._tc_grid[1] != B or (train and not self._tc_grid[2]):
+            self._tc_buffers(n, B, train)
         packed = self._tc_weights()
         lib, s, t = self.lib, self.stream, self.tc
-        _check(lib.fftls_nn_tc_conv_phase(_p(phase), self._w("enc0"), self._b("enc0"), _p(t["e0"]), _I3(*n), 8,
-                                          float(log_contrast(contrast)), 1, s), "conv enc0")
+        N = n[0] * n[1] * n[2]
+        for b, (ph, c) in enumerate(zip(phases, contrasts)):
+            if tuple(ph.shape) != tuple(phases[0].shape):
+                raise ValueError("the samples of a batch must share one grid")
+            e0 = ctypes.c_void_p(t["e0"].data_ptr() + 2 * 8 * N * b)
+            _check(lib.fftls_nn_tc_conv_phase(_p(ph), self._w("enc0"), self._b("enc0"), e0, _I3(*n), 8,
+                                              float(log_contrast(c)), 1, s), "conv enc0")
         layer = {l[0]: l for l in LAYERS}
         for name, src, mode, skip in _TC_PLAN:
             _, ci, co, k, lvl = layer[name]
             _check(lib.fftls_nn_tc_conv3d(_p(t[src]), _p(packed[name]), self._b(name), _p(t[skip]) if skip else None,
-                                          _p(t[_TC_OUT[name]]), 1, ci, co, self._dims(n, lvl), k, mode, 1, 0, 0, s),
+                                          _p(t[_TC_OUT[name]]), B, ci, co, self._dims(n, lvl), k, mode, 1, 0, 0, s),
                    f"conv {name}")
         _, ci, co, k, lvl = layer["out"]
-        _check(lib.fftls_nn_tc_conv3d(_p(t["d0"]), _p(packed["out"]), self._b("out"), None, _p(t["y"]), 1, ci, co,
+        _check(lib.fftls_nn_tc_conv3d(_p(t["d0"]), _p(packed["out"]), self._b("out"), None, _p(t["y"]), B, ci, co,
                                       self._dims(n, 0), k, 0, 0, 1, 0, s), "conv out")
         return t["y"]
 
+    def backward_tc(self, phases, contrasts):
+        """Parameter gradients (into self.grads) of the loss whose output gradient is in self.tc_gy, after
+        forward_tc_batch(..., train=True) on the same batch: the forward's chain backwards on the
+        tensor cores (BF16 channels-last gradients, FP32 weight gradients)."""
+        lib, s, t, g = self.lib, self.stream, self.tc, self.tcg
+        n = self._tc_grid[0]
+        B = self.tc_batch
+        N = n[0] * n[1] * n[2]
+        packed_t = self._tc_weights(transposed=True)
+        layer = {l[0]: l for l in LAYERS}
+        scratch, ns = _p(self.tc_scratch), self.tc_scratch.numel()
+        vox = lambda lvl: B * (n[0] >> lvl) * (n[1] >> lvl) * (n[2] >> lvl)
+
+        def wgrad(name, src, gout, mode):
+            _, ci, co, k, lvl = layer[name]
+            _check(lib.fftls_nn_tc_conv3d_backward_weights(_p(src), _p(g[gout]), self._w(name, True),
+                                                           self._b(name, True), B, ci, co, self._dims(n, lvl), k, mode,
+                                                           scratch, ns, s), f"wgrad {name}")
+
+        def dgrad(name, gout, gin):
+            _, ci, co, k, lvl = layer[name]
+            _check(lib.fftls_nn_tc_conv3d(_p(g[gout]), _p(packed_t[name]), None, None, _p(g[gin]), B, co, ci,
+                                          self._dims(n, lvl), k, 0, 0, 0, 0, s), f"dgrad {name}")
+
+        def relu(gname, act):
+            _check(lib.fftls_nn_tc_relu_backward(_p(g[gname]), _p(t[act]), t[act].numel(), s), "relu")
+
+        def up_bwd(gsrc, gdst, ch, lvl_coarse):
+            _check(lib.fftls_nn_tc_upsample2_backward(_p(g[gsrc]), _p(g[gdst]), B, ch, self._dims(n, lvl_coarse), s),
+                   "upsample backward")
+
+        def pool_bwd_acc(gsrc, gdst, ch, lvl_coarse):
+            _check(lib.fftls_nn_tc_pool2_backward(_p(g[gsrc]), _p(g[gdst]), B, ch, self._dims(n, lvl_coarse), 1, s),
+                   "pool backward")
+
+        _check(lib.fftls_nn_tc_from_planar(_p(self.tc_gy), _p(g["gy"]), B, 6, N, s), "gradient layout")
+        wgrad("out", t["d0"], "gy", 0)
+        dgrad("out", "gy", "gd0")
+        relu("gd0", "d0")
+        wgrad("dec0", t["d1"], "gd0", 1)
+        dgrad("dec0", "gd0", "gu0")
+        up_bwd("gu0", "gd1", 16, 1)
+        relu("gd1", "d1")
+        wgrad("dec1", t["d2"], "gd1", 1)
+        dgrad("dec1", "gd1", "gu1")
+        up_bwd("gu1", "gd2", 32, 2)
+        relu("gd2", "d2")
+        wgrad("dec2", t["e3"], "gd2", 1)
+        dgrad("dec2", "gd2", "gu2")
+        up_bwd("gu2", "ge3", 64, 3)
+        relu("ge3", "e3")
+        wgrad("enc3b", t["a3"], "ge3", 0)
+        dgrad("enc3b", "ge3", "ga3")
+        relu("ga3", "a3")
+        wgrad("enc3a", t["e2"], "ga3", 2)
+        dgrad("enc3a", "ga3", "gp2")
+        pool_bwd_acc("gp2", "gd2", 32, 3)   # gd2 now holds the gradient of e2
+        relu("gd2", "e2")
+        wgrad("enc2b", t["a2"], "gd2", 0)
+        dgrad("enc2b", "gd2", "ga2")
+        relu("ga2", "a2")
+        wgrad("enc2a", t["e1"], "ga2", 2)
+        dgrad("enc2a", "ga2", "gp1")
+        pool_bwd_acc("gp1", "gd1", 16, 2)   # gradient of e1
+        relu("gd1", "e1")
+        wgrad("enc1b", t["a1"], "gd1", 0)
+        dgrad("enc1b", "gd1", "ga1")
+        relu("ga1", "a1")
+        wgrad("enc1a", t["e0"], "ga1", 2)
+        dgrad("enc1a", "ga1", "gp0")
+        pool_bwd_acc("gp0", "gd0", 8, 1)    # gradient of e0
+        relu("gd0", "e0")
+        # first layer, one sample at a time (each has its own log-contrast channel)
+        nw0 = self.offsets["enc0"][1]
+        for b, (ph, c) in enumerate(zip(phases, contrasts)):
+            dy = ctypes.c_void_p(g["gd0"].data_ptr() + 2 * 8 * N * b)
+            dw = self._w("enc0", True) if b == 0 else _p(self.tc_dw0)
+            db = self._b("enc0", True) if b == 0 else ctypes.c_void_p(self.tc_dw0.data_ptr() + 4 * nw0)
+            _check(lib.fftls_nn_tc_conv_phase_backward_weights(_p(ph), dy, dw, db, _I3(*n), 8, float(log_contrast(c)),
+                                                               scratch, ns, s), "wgrad enc0")
+            if b > 0:
+                _check(lib.fftls_nn_add(self._w("enc0", True), _p(self.tc_dw0), nw0, s), "wgrad enc0 sum")
+                _check(lib.fftls_nn_add(self._b("enc0", True), ctypes.c_void_p(self.tc_dw0.data_ptr() + 4 * nw0), 8,
+                                        s), "bias grad enc0 sum")
+
     # -- training and prediction -----------------------------------------
-    def train(self, data, epochs: int, lr: float = 5e-4, lr_final: float = 5e-5, seed: int = 0, batch: int = 1):
+    def _train_step_tc(self, group, rate, loss_out):
+        """One Adam step on a batch on the tensor cores; the batch's loss into loss_out (device)."""
+        phases = [d["phase"] for d in group]
+        contrasts = [d["contrast"] for d in group]
+        self.forward_tc_batch(phases, contrasts, train=True)
+        n = self._tc_grid[0]
+        N6 = 6 * n[0] * n[1] * n[2]
+        for slot, d in enumerate(group):
+            self.tc_target[slot * N6:(slot + 1) * N6].copy_(d["target"].reshape(-1))
+        _check(self.lib.fftls_nn_mse(_p(self.tc["y"]), _p(self.tc_target), _p(self.tc_gy), _p(self.tc_loss),
+                                     self.tc["y"].numel(), self.stream), "mse")
+        loss_out.copy_(self.tc_loss)
+        self.backward_tc(phases, contrasts)
+        self.adam(rate)
+
+    def train(self, data, epochs: int, lr: float = 5e-4, lr_final: float = 5e-5, seed: int = 0, batch: int = 1,
+              tensor_cores: bool = False):
         """Adam on the MSE between prediction and solver fluctuation, `batch` samples (of one grid
         size) per step in a seeded random order (each epoch leaves out the len(data) % batch samples
         its permutation puts last); the learning rate decays geometrically from lr to lr_final (at
-        2e-3 the ReLU units of this network die within the first epoch).  Returns the mean loss of
-        each epoch."""
+        2e-3 the ReLU units of this network die within the first epoch).  tensor_cores: forward and
+        backward on the tensor cores (BF16 activations and gradients, FP32 weights and Adam).
+        Returns the mean loss of each epoch."""
         torch = self.torch
         rng = np.random.default_rng(seed)
         per = len(data) // batch
@@ -435,6 +593,10 @@ class WarmNet:
             for j in range(per):
                 group = [data[i] for i in order[j * batch:(j + 1) * batch]]
                 n = (group[0]["phase"].shape[2], group[0]["phase"].shape[1], group[0]["phase"].shape[0])
+                if tensor_cores:
+                    self._train_step_tc(group, lr * (lr_final / lr) ** (step / max(1, total - 1)), losses[j:j + 1])
+                    step += 1
+                    continue
                 self._buffers(n, True, batch)
                 N6 = 6 * n[0] * n[1] * n[2]
                 for slot, d in enumerate(group):
