@@ -999,6 +999,32 @@ __global__ void __launch_bounds__(strided_threads(W)) k_fourier_z(const __grid_c
 // ---------------------------------------------------------------------------
 // R: eta, <sigma>, history and stop decision (single block)
 // ---------------------------------------------------------------------------
+// Block sums of W values per thread for the kRedThreads threads of k_reduce_eta, returned to every
+// thread: the values go through shared memory column by column, and warp w sums the columns w,
+// w + 8, ... (8 FP64 additions per lane and a 5-level shuffle per column), so the block issues about
+// 13 W warp-wide FP64 additions instead of the 5 W per warp of a shuffle tree in every warp (GB300's
+// FP64 pipe takes about 16 cycles for one).
+constexpr int kRedThreads = 256;
+template <int W>
+__device__ void block_sum_columns(double (&v)[W]) {
+  __shared__ double col[W][kRedThreads];
+  __shared__ double out[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) col[i][threadIdx.x] = v[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < W; i += kRedThreads / 32) {
+    double x = 0.0;
+#pragma unroll
+    for (int k = 0; k < kRedThreads / 32; ++k) x += col[i][lane + 32 * k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) out[i] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < W; ++i) v[i] = out[i];
+}
+
 template <typename T, int DIM>
 __device__ __forceinline__ void k_reduce_eta_body(const IterArgs<T>& a, const AxisPlan* pl, int n_eta_parts, int n_mean_parts) {
   constexpr int NC = Comp<DIM>::NC;
@@ -1015,14 +1041,14 @@ __device__ __forceinline__ void k_reduce_eta_body(const IterArgs<T>& a, const Ax
 #pragma unroll
     for (int c = 0; c < 2 * NC; ++c) s[c] += a.part_mean[(size_t)b * 2 * NC + c];
   for (int b = threadIdx.x; b < n_eta_parts; b += blockDim.x) s[2 * NC] += a.part_eta[b];
-  block_sum<2 * NC + 1>(s);
+  block_sum_columns<2 * NC + 1>(s);
   if (threadIdx.x != 0) return;
-  const double N = (double)a.g.N;
+  const double N = (double)a.g.N, invN = 1.0 / N;
   double fro2 = 0.0, eb2 = 0.0, d2 = 0.0;
   const int it = ctl->it;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const double ms = ctl->off_sig[c] + s[c] / N, me = ctl->off_eps[c] + s[NC + c] / N;
+    const double ms = ctl->off_sig[c] + s[c] * invN, me = ctl->off_eps[c] + s[NC + c] * invN;
     const double wgt = c < DIM ? 1.0 : 2.0;
     fro2 += wgt * ms * ms;
     eb2 += wgt * a.eps_bar[c] * a.eps_bar[c];
@@ -1424,8 +1450,8 @@ cudaError_t launch_reduce_eta_t(const IterArgs<T>& a, cudaStream_t s) {
   const int nparts = a.eta_real ? a.e_blocks : ((a.g.H + a.z_w - 1) / a.z_w) * a.g.n2 * (a.dual ? 2 : 1);
   const int mparts = a.x1_blocks;
   const dim3 grid(1, GRP ? a.nsmp : 1);
-  if (a.dim == 3) k_reduce_eta<T, 3, GRP><<<grid, 512, 0, s>>>(a, nparts, mparts);
-  else if constexpr (!GRP) k_reduce_eta<T, 2, GRP><<<grid, 512, 0, s>>>(a, nparts, mparts);
+  if (a.dim == 3) k_reduce_eta<T, 3, GRP><<<grid, kRedThreads, 0, s>>>(a, nparts, mparts);
+  else if constexpr (!GRP) k_reduce_eta<T, 2, GRP><<<grid, kRedThreads, 0, s>>>(a, nparts, mparts);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
