@@ -190,6 +190,14 @@ __host__ __device__ constexpr int p2_msize(int L, int s) { return s == 0 ? L : p
 
 // Lengths whose transforms run the compile-time stages (tile_fft_ct).
 __host__ __device__ constexpr bool ct_length(int L) { return L == 64 || L == 128 || L == 256 || L == 512; }
+// Radix-3 lengths whose strided (x2 / x3) transforms also run compile-time stages, with the host plan:
+// the power-of-two plan of L / 3, then one radix-3 stage (48 = 4 4 3, 96 = 4 8 3).
+__host__ __device__ constexpr bool r3_length(int L) { return L == 48 || L == 96; }
+__host__ __device__ constexpr int ct_nst(int L) { return r3_length(L) ? p2_nst(L / 3) + 1 : p2_nst(L); }
+__host__ __device__ constexpr int ct_radix(int L, int s) {
+  return r3_length(L) ? (s < p2_nst(L / 3) ? p2_radix(L / 3, s) : 3) : p2_radix(L, s);
+}
+__host__ __device__ constexpr int ct_msize(int L, int s) { return s == 0 ? L : ct_msize(L, s - 1) / ct_radix(L, s - 1); }
 // Twiddle table of a compile-time length, laid out by stage (read by the
 // padded x1 tiles): stage s with MR = M / R > 1 (M = msize, R = radix) holds MR
 // rows of R complex values, row j = {w^(j T), w^(2 j T), ..., w^((R-1) j T),
@@ -210,8 +218,8 @@ __host__ __device__ constexpr int srow(int R) { return R == 8 ? 10 : R; }
 __host__ __device__ constexpr int strided_tw_offset(int L, int s) {
   return s == 0 ? 0
                 : strided_tw_offset(L, s - 1) +
-                      (p2_msize(L, s - 1) > p2_radix(L, s - 1)
-                           ? (p2_msize(L, s - 1) / p2_radix(L, s - 1)) * srow(p2_radix(L, s - 1))
+                      (ct_msize(L, s - 1) > ct_radix(L, s - 1)
+                           ? (ct_msize(L, s - 1) / ct_radix(L, s - 1)) * srow(ct_radix(L, s - 1))
                            : 0);
 }
 // Complex entries of an axis's shared-memory twiddle table (even, so that the
@@ -220,7 +228,8 @@ __host__ __device__ constexpr int strided_tw_offset(int L, int s) {
 // that a kernel pays no run-time recursion for it.
 __host__ __device__ constexpr int tw_count(int L, int layout) {
   return layout == kTwX1 ? (L == 64 ? 64 : L == 128 ? 160 : L == 256 ? 320 : L == 512 ? 576 : ((L + 1) & ~1))
-       : layout == kTwStrided ? (L == 64 ? 80 : L == 128 ? 160 : L == 256 ? 336 : L == 512 ? 720 : ((L + 1) & ~1))
+       : layout == kTwStrided ? (L == 48 ? 60 : L == 64 ? 80 : L == 96 ? 126 : L == 128 ? 160 : L == 256 ? 336
+                                 : L == 512 ? 720 : ((L + 1) & ~1))
        : ((L + 1) & ~1);
 }
 static_assert(tw_count(64, kTwX1) == stage_tw_offset(64, p2_nst(64)) &&
@@ -228,7 +237,9 @@ static_assert(tw_count(64, kTwX1) == stage_tw_offset(64, p2_nst(64)) &&
                   tw_count(256, kTwX1) == stage_tw_offset(256, p2_nst(256)) &&
                   tw_count(512, kTwX1) == stage_tw_offset(512, p2_nst(512)),
               "stage twiddle counts");
-static_assert(tw_count(64, kTwStrided) == strided_tw_offset(64, p2_nst(64)) &&
+static_assert(tw_count(48, kTwStrided) == strided_tw_offset(48, ct_nst(48)) &&
+                  tw_count(96, kTwStrided) == strided_tw_offset(96, ct_nst(96)) &&
+                  tw_count(64, kTwStrided) == strided_tw_offset(64, p2_nst(64)) &&
                   tw_count(128, kTwStrided) == strided_tw_offset(128, p2_nst(128)) &&
                   tw_count(256, kTwStrided) == strided_tw_offset(256, p2_nst(256)) &&
                   tw_count(512, kTwStrided) == strided_tw_offset(512, p2_nst(512)),
@@ -237,6 +248,7 @@ static_assert(tw_count(64, kTwStrided) == strided_tw_offset(64, p2_nst(64)) &&
 template <int R, typename T2>
 __device__ __forceinline__ void dft_fixed(T2* v, bool inv) {
   if (R == 2) dft2(v);
+  else if (R == 3) dft3(v, inv);
   else if (R == 4) dft4(v, inv);
   else dft8(v, inv);
 }
@@ -510,8 +522,8 @@ __device__ void tile_fft_rt(T2* buf, int nblk, int BS, int C, int ncols, const A
 // the unit twiddles of its row instead of branching.
 template <int L, int S, int C, int NT, bool INV, typename T2>
 __device__ __forceinline__ void strided_stage(T2* __restrict__ buf, const T2* __restrict__ tw) {
-  constexpr int R = p2_radix(L, S);
-  constexpr int M = p2_msize(L, S);
+  constexpr int R = ct_radix(L, S);
+  constexpr int M = ct_msize(L, S);
   constexpr int MR = M / R;
   constexpr int NB = L / R;
   constexpr int ITEMS = NB * C;
@@ -523,7 +535,7 @@ __device__ __forceinline__ void strided_stage(T2* __restrict__ buf, const T2* __
     if ((ITEMS % NT) != 0 && it >= ITEMS) break;
     const int bf = it / C;
     const int c = it - bf * C;
-    const int j = bf & (MR - 1);
+    const int j = bf % MR;  // MR, C compile-time: shifts or multiply-shifts
     T2* base = buf + ((bf / MR) * M + j) * C + c;
     T2 v[R];
 #pragma unroll
@@ -553,7 +565,7 @@ __device__ __forceinline__ void strided_stage(T2* __restrict__ buf, const T2* __
 
 template <int L, int C, int NT, bool INV, typename T2>
 __device__ __forceinline__ void strided_fft(T2* buf, const T2* tw) {
-  constexpr int NST = p2_nst(L);
+  constexpr int NST = ct_nst(L);
   if (!INV) {
     if constexpr (NST > 0) strided_stage<L, 0, C, NT, false>(buf, tw);
     if constexpr (NST > 1) strided_stage<L, 1, C, NT, false>(buf, tw);
@@ -568,8 +580,8 @@ __device__ __forceinline__ void strided_fft(T2* buf, const T2* tw) {
 }
 
 // In-place transform of a strided tile (x2 / x3 passes): the compile-time
-// lengths run strided_fft (twiddles in the kTwStrided layout), any other length
-// the run-time paths (plain table).  All C columns are transformed.
+// lengths and the radix-3 lengths 48 and 96 run strided_fft (twiddles in the
+// kTwStrided layout), any other length the run-time paths (plain table).  All C columns are transformed.
 // A tile of L rows of C columns fits the 227 KB of shared memory of a block (the
 // compile-time stages are generated only for tiles that can run).
 template <typename T2>
@@ -578,7 +590,9 @@ __host__ __device__ constexpr bool strided_fits(int L, int C) { return (long lon
 template <int C, int NT, bool INV, typename T2>
 __device__ void tile_fft_strided(T2* buf, const AxisPlan& p, const T2* tw) {
   switch (p.L) {
+    case 48: if constexpr (strided_fits<T2>(48, C)) { strided_fft<48, C, NT, INV>(buf, tw); return; } break;
     case 64: if constexpr (strided_fits<T2>(64, C)) { strided_fft<64, C, NT, INV>(buf, tw); return; } break;
+    case 96: if constexpr (strided_fits<T2>(96, C)) { strided_fft<96, C, NT, INV>(buf, tw); return; } break;
     case 128: if constexpr (strided_fits<T2>(128, C)) { strided_fft<128, C, NT, INV>(buf, tw); return; } break;
     case 256: if constexpr (strided_fits<T2>(256, C)) { strided_fft<256, C, NT, INV>(buf, tw); return; } break;
     case 512: if constexpr (strided_fits<T2>(512, C)) { strided_fft<512, C, NT, INV>(buf, tw); return; } break;

@@ -132,10 +132,10 @@ void axis_tables(int L, int layout, int green, const int* perm, double* tw, doub
   }
   const int ntw = fftls::tw_count(L, layout);
   for (int t = 0; t < 2 * ntw; ++t) tw[t] = t < 2 * L ? plain[t] : 0.0;
-  if (layout != fftls::kTwPlain && fftls::ct_length(L)) {
+  if ((layout != fftls::kTwPlain && fftls::ct_length(L)) || (layout == fftls::kTwStrided && fftls::r3_length(L))) {
     for (int t = 0; t < 2 * ntw; ++t) tw[t] = 0.0;
-    for (int st = 0; st < fftls::p2_nst(L); ++st) {
-      const int R = fftls::p2_radix(L, st), M = fftls::p2_msize(L, st), MR = M / R, T = L / M;
+    for (int st = 0; st < fftls::ct_nst(L); ++st) {
+      const int R = fftls::ct_radix(L, st), M = fftls::ct_msize(L, st), MR = M / R, T = L / M;
       if (MR == 1) continue;
       const int row = layout == fftls::kTwX1 ? R : fftls::srow(R);
       const size_t off = layout == fftls::kTwX1 ? (size_t)fftls::stage_tw_offset(L, st)

@@ -90,6 +90,25 @@ def test_fixed_iterations_match_oracle(solver, shape_np, green, scheme):
                                        rtol=1e-11, atol=1e-13)
 
 
+@pytest.mark.parametrize("shape_np", [(48, 96, 20), (96, 48, 16)])
+@pytest.mark.parametrize("green", range(4))
+@pytest.mark.parametrize("scheme", range(2))
+def test_radix3_strided_lengths_match_oracle(solver, shape_np, green, scheme):
+    """x2 / x3 lengths 48 and 96, whose strided transforms run compile-time stages with a radix-3
+    stage (48 = 4 4 3, 96 = 4 8 3): eps^2, the eta and <sigma> histories against the oracle (FP64)."""
+    ph = random_phase(shape_np, seed=7 + green * 10 + scheme)
+    lam, mu = MS.binary_moduli(20.0, 3)
+    eb = load(3)
+    ref = O.solve(ph, lam, mu, eb, green, scheme, tol=0.0, max_iter=2)
+    got = solver.solve(ph, lam, mu, eb, GREEN_NAMES[green], SCHEME_NAMES[scheme], tol=0.0, max_iter=2)
+    assert got.iterations == 2
+    assert np.abs(got.strain - to_components(ref["strain"])).max() < FIELD_TOL
+    np.testing.assert_allclose(got.eta_history, ref["eta_history"], rtol=1e-9, atol=1e-14)
+    for i in range(2):
+        np.testing.assert_allclose(got.mean_stress_history[i], vec_components(ref["mean_stress_history"][i]),
+                                   rtol=1e-11, atol=1e-13)
+
+
 @pytest.mark.parametrize("green", range(4))
 @pytest.mark.parametrize("scheme", range(2))
 def test_converged_moduli_match_oracle(solver, green, scheme):
