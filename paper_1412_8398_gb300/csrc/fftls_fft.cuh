@@ -535,8 +535,8 @@ __device__ __forceinline__ void strided_stage(T2* __restrict__ buf, const T2* __
     if ((ITEMS % NT) != 0 && it >= ITEMS) break;
     const int bf = it / C;
     const int c = it - bf * C;
-    const int j = bf % MR;  // MR, C compile-time: shifts or multiply-shifts
-    T2* base = buf + ((bf / MR) * M + j) * C + c;
+    const int j = (int)((unsigned)bf % (unsigned)MR);  // MR compile-time: a mask or a multiply-shift
+    T2* base = buf + ((int)((unsigned)bf / (unsigned)MR) * M + j) * C + c;
     T2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = base[r * MR * C];
