@@ -53,6 +53,7 @@ struct Ctrl {
   double off_eps[6];
   double last_ms[6];   // <sigma>, <eps> of the last eta evaluation (with offsets)
   double last_me[6];
+  int fault;           // 1: a tile copy did not complete within its wait limit; the solve was stopped
 };
 
 // Geometry: grid n1 x n2 x n3, half spectrum of H = n1/2 + 1 modes along x1,

@@ -566,6 +566,10 @@ struct Runner {
   fftls_status read_ctrl() {
     CUDA_TRY(c, cudaMemcpyAsync(hctl, a.ctrl, (size_t)ns * sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
     CUDA_TRY(c, cudaStreamSynchronize(S.s));
+    for (int i = 0; i < ns; ++i)
+      if (hctl[i].fault)
+        return set_err(c, FFTLS_E_CUDA, "%s",
+                       "a shared-memory tile copy did not complete within its wait limit; the solve was stopped");
     return FFTLS_OK;
   }
   fftls_status put_ctrl(const Ctrl* init) {
@@ -1755,6 +1759,7 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   for (;;) {
     NA_TRY(cudaMemcpyAsync(&ctl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
     NA_TRY(cudaStreamSynchronize(S.s));
+    if (ctl.fault) return FFTLS_E_CUDA;  // a tile copy did not complete within its wait limit
     if (ctl.state != kRunning) break;
     for (int i = 0; i < chunk; ++i) NA_TRY(iteration(dual, upd));
   }
