@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--batched", type=int, default=0,
                     help="instead of the 512^3 workload, time COUNT batched Boolean samples of uneven sizes")
     ap.add_argument("--concurrency", type=int, default=8, help="worker streams of the batched solve")
+    ap.add_argument("--batched-per-length", action="store_true",
+                    help="with --batched: also time each grid length's samples alone (one worker) and one FP32 "
+                         "iteration of a single sample per length")
     ap.add_argument("--warmstart", type=int, default=0,
                     help="instead of the 512^3 workload, train the warm-start network on COUNT solver-generated "
                          "64^3 samples and compare warm and plain starts on 256^3 samples")
@@ -528,6 +531,23 @@ def run_batched(args, rank, local, world):
     r64, t_64 = timed(lambda: [solver.solve(s["phase"], s["lam"], s["mu"], s["eps_bar"], precision="fp64",
                                             want_strain=False, want_stress=False, history=False, **kw)
                                for s in samples])
+    per_length = None
+    if args.batched_per_length:  # where the batch's time goes, one grid length at a time
+        per_length = []
+        for L in sorted({int(s["phase"].shape[0]) for s in samples}):
+            grp = [s for s in samples if int(s["phase"].shape[0]) == L]
+            solver.solve_batched(grp, precision="fp32_refine64", concurrency=1, **kw)
+            (rg, _), tg = timed(lambda: solver.solve_batched(grp, precision="fp32_refine64", concurrency=1, **kw))
+            s0 = grp[0]
+            one = dict(kw, tol=0.0)
+            solver.solve(s0["phase"], s0["lam"], s0["mu"], s0["eps_bar"], precision="fp32", want_strain=False,
+                         want_stress=False, history=False, **dict(one, max_iter=5), raise_on_error=False)
+            _, t1 = timed(lambda: solver.solve(s0["phase"], s0["lam"], s0["mu"], s0["eps_bar"], precision="fp32",
+                                               want_strain=False, want_stress=False, history=False,
+                                               **dict(one, max_iter=105), raise_on_error=False))
+            per_length.append({"L": L, "samples": len(grp), "time_s": tg,
+                               "voxel_iters_per_s": sum(L ** 3 * r.iterations for r in rg) / tg,
+                               "single_fp32_ms_per_iteration": 1e3 * t1 / 105})
     its_b = np.array([r.iterations for r in res], dtype=np.float64)
     its_64 = np.array([r.iterations for r in r64], dtype=np.float64)
     rel = max(float(np.abs(a.mean_stress - b.mean_stress).max() / np.abs(b.mean_stress).max())
@@ -543,7 +563,7 @@ def run_batched(args, rank, local, world):
         out = {
             "metric": "time to eta <= 1e-6 over a batch of independent samples (AS, G^R)", "unit": "s",
             "value": t_b_max, "higher_is_better": False, "n_gpus": world, "impl": "ours",
-            "data": "synthetic", "dtype": "f32+f64 solve, bf16 inference",
+            "data": "synthetic", "dtype": "f32+f64",
             "config": {"workload": f"batched_boolean_{args.batched}_samples_L32-128_R3-8_f0.1-0.4_chi10-1000",
                        "samples": args.batched, "voxels_total": int(allreduce([float(vox.sum())], _sum_op(world), world)[0]),
                        "concurrency": args.concurrency, "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -554,6 +574,7 @@ def run_batched(args, rank, local, world):
                                 "iterations_mean": float(its_64.mean())},
             "speedup_vs_fp64": t_64_max / t_b_max,
             "max_rel_mean_stress_diff_vs_fp64": rel,
+            "per_length": per_length,
             "tile_plans": solver.tile_plans(),
         }
         print(json.dumps(out))
