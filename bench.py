@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--warm-batch", type=int, default=1, help="samples per training step of the warm start")
     ap.add_argument("--warm-lr", type=float, default=5e-4, help="initial learning rate (decays 10x over training)")
     ap.add_argument("--warm-tc", action="store_true", help="train the warm start on the tensor cores")
+    ap.add_argument("--warm-layers", type=int, default=0,
+                    help="instead of the 512^3 workload, time each layer of the warm start's tensor-core inference "
+                         "on an N^3 grid (random weights; CUDA events, best of 10)")
     ap.add_argument("--ncu-region", action="store_true",
                     help="for ncu --profile-from-start off: tune and warm up on the workload, then bracket two "
                          "FP32 iterations launched without graphs with the profiler start / stop calls")
@@ -658,6 +661,69 @@ def run_warmstart(args, rank, local, world):
     solver.close()
 
 
+def run_warm_layers(args, rank, local, world):
+    """Per-layer CUDA-event times of the warm start's tensor-core inference on an N^3 Boolean sample
+    (random weights: the times do not depend on the values), the whole forward, the initial strain,
+    and the FP32 forward for comparison.  Rank 0 only."""
+    import ctypes
+    import torch
+    from paper_1412_8398_gb300 import build, microstructure as MS, warmstart as WS
+
+    if rank != 0:
+        return
+    build.build()
+    torch.cuda.set_device(local)
+    L = args.warm_layers
+    net = WS.WarmNet(device=local, seed=0)
+    ph, _ = MS.boolean_spheres((L, L, L), 5.0, 0.2, seed=1)
+    dph = torch.from_numpy(ph).cuda()
+    n = (L, L, L)
+
+    def ms(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    out = {"metric": "warm-start tensor-core inference, per layer", "unit": "ms", "grid": L, "layers": []}
+    out["forward_tc_ms"] = ms(lambda: net.forward_tc(dph, 100.0))
+    lib, t = net.lib, net.tc
+    packed = net._tc_weights()
+    layer = {l[0]: l for l in WS.LAYERS}
+    _p = WS._p
+    t_enc0 = ms(lambda: lib.fftls_nn_tc_conv_phase(_p(dph), net._w("enc0"), net._b("enc0"), _p(t["e0"]),
+                                                   WS._I3(*n), 8, 0.0, 1, None))
+    out["layers"].append({"layer": "enc0", "ms": t_enc0, "flop": 2.0 * L ** 3 * 27 * 2 * 8})
+    cs = WS._stored
+    for name, src, mode, skip in WS._TC_PLAN + [("out", "d0", 0, None)]:
+        _, ci, co, k, lvl = layer[name]
+        dst, planar, relu = (t["y"], 1, 0) if name == "out" else (t[WS._TC_OUT[name]], 0, 1)
+        f = (lambda name=name, src=src, mode=mode, skip=skip, ci=ci, co=co, k=k, lvl=lvl, dst=dst, planar=planar,
+             relu=relu: lib.fftls_nn_tc_conv3d(_p(t[src]), _p(packed[name]), net._b(name),
+                                               _p(t[skip]) if skip else None, _p(dst), 1, ci, co,
+                                               net._dims(n, lvl), k, mode, relu, planar, 0, None))
+        vox = (L >> lvl) ** 3
+        tl = ms(f)
+        out["layers"].append({"layer": name, "ms": tl, "flop": 2.0 * vox * k ** 3 * cs(ci) * cs(co),
+                              "tflops_padded": 2.0 * vox * k ** 3 * cs(ci) * cs(co) / tl / 1e9})
+    y = net.forward_tc(dph, 100.0)
+    eps = torch.empty((6, L, L, L), dtype=torch.float64, device="cuda")
+    eb = (ctypes.c_double * 6)(1.0, 0, 0, 0, 0, 0)
+    out["strain_init_ms"] = ms(lambda: lib.fftls_nn_strain_init(_p(y), _p(eps), WS._I3(*n), eb, 1.0,
+                                                                _p(net.tc_mean_scratch), None))
+    net._buffers(n, False)
+    out["forward_fp32_ms"] = ms(lambda: (net.features(dph, 100.0), net.forward()))
+    print(json.dumps(out))
+
+
 def run_ncu_region(args, local):
     """A profiler region of two steady-state FP32 iterations of the workload (size --n)."""
     import torch
@@ -688,6 +754,9 @@ def main():
         return
     if args.batched > 0:
         run_batched(args, rank, local, world)
+        return
+    if args.warm_layers > 0:
+        run_warm_layers(args, rank, local, world)
         return
     if args.warmstart > 0:
         run_warmstart(args, rank, local, world)
