@@ -74,6 +74,12 @@ def parse():
                     help="for ncu --profile-from-start off: tune and warm up on the workload, then bracket two "
                          "FP32 iterations launched without graphs with the profiler start / stop calls")
     ap.add_argument("--warm-apply", type=int, default=4, help="256^3 samples of the warm-start comparison")
+    ap.add_argument("--x1-sweep", action="store_true",
+                    help="instead of the workload's timing, the forward x1 pass's time for every batch size and "
+                         "load variant (imported schedules, the solver's profile mode)")
+    ap.add_argument("--thin-grids", default="",
+                    help="instead of the workload, per-kernel FP32 times on 512 x 512 x n3 grids for the listed n3 "
+                         "(comma-separated), scaled to 512^3 voxels: does a pass speed up once its fields fit L2?")
     return ap.parse_args()
 
 
@@ -661,6 +667,83 @@ def run_warmstart(args, rank, local, world):
     solver.close()
 
 
+def run_x1_sweep(args, rank, local):
+    """The forward x1 pass (k_fwd_x) on the workload (--n) for lines per batch 1..8 and the load variants
+    (voxels per thread loaded together 1, 2, 4; 0 = the batch staged in shared memory by bulk copies),
+    the other passes on the tuned schedule: CUDA-event ms per launch over 8 FP32 iterations (the
+    solver's profile mode), best of two rounds.  Rank 0 only."""
+    import numpy as np
+    import torch
+    from paper_1412_8398_gb300 import build, fftls
+
+    if rank != 0:
+        return
+    build.build()
+    torch.cuda.set_device(local)
+    ph, lam, mu, _ = workload(args.n)
+    dph = torch.from_numpy(ph).cuda()
+    eb = np.diag([1.0, 0.0, 0.0])
+    s = fftls.Solver(local)
+    res = {}
+    try:
+        s.solve(dph, lam, mu, eb, "R", "AS", tol=0.0, max_iter=3, precision="fp32", want_strain=False,
+                want_stress=False)
+        base = [p for p in s.tile_plans() if p["precision"] == 0][0]
+        for _ in range(2):
+            for lines in range(1, 9):
+                for vb in (1, 2, 4, 0):
+                    try:
+                        s.set_tile_plans([dict(base, x1_lines=lines, x1_vb=vb)])
+                        s.solve(dph, lam, mu, eb, "R", "AS", tol=0.0, max_iter=8, precision="fp32",
+                                want_strain=False, want_stress=False, profile=True)
+                    except fftls.FftlsError:
+                        continue  # does not fit shared memory
+                    v = [t for k, t in s.profile().items() if k.startswith("fwd_x")][0]
+                    key = f"{lines},{vb}"
+                    res[key] = min(res.get(key, float("inf")), v[0] / v[1])
+    finally:
+        s.close()
+    print(json.dumps({"metric": f"k_fwd_x ms per launch at {args.n}^3 FP32 by (lines per batch, voxels per load; "
+                                "0 = staged by bulk copies)", "tuned": {k: base[k] for k in ("x1_lines", "x1_vb")},
+                      "ms": res}), flush=True)
+
+
+def run_thin_grids(args, rank, local):
+    """Per-kernel CUDA-event times (the solver's profile mode: no graphs, events around every launch) of
+    20 FP32 iterations of the workload's recipe on 512 x 512 x n3 grids, tuned schedules, each scaled to
+    512^3 voxels.  The half spectrum takes 6.3 MB per x3-plane, so at n3 <= 16 every pass's fields fit
+    the 129 MB L2: a pass bound by DRAM bandwidth would run faster per voxel there.  Rank 0 only."""
+    import numpy as np
+    import torch
+    from paper_1412_8398_gb300 import build, fftls, microstructure as MS
+
+    if rank != 0:
+        return
+    build.build()
+    torch.cuda.set_device(local)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (1000.0, 0.2)])
+    eb = np.diag([1.0, 0.0, 0.0])
+    out = {"metric": "FP32 ms per launch scaled to 512^3 voxels, 512 x 512 x n3 grids", "unit": "ms", "rows": []}
+    for n3 in [int(v) for v in args.thin_grids.split(",") if v]:
+        ph, _ = MS.boolean_spheres((512, 512, n3), 8.0, 0.25, seed=1)
+        dph = torch.from_numpy(ph).cuda()
+        s = fftls.Solver(local)
+        try:
+            s.solve(dph, lam, mu, eb, "R", "AS", tol=0.0, max_iter=3, precision="fp32", want_strain=False,
+                    want_stress=False)
+            s.solve(dph, lam, mu, eb, "R", "AS", tol=0.0, max_iter=20, precision="fp32", want_strain=False,
+                    want_stress=False, profile=True)
+            prof = s.profile()
+            plan = [p for p in s.tile_plans() if p["precision"] == 0][0]
+        finally:
+            s.close()
+        scale = 512.0 ** 3 / (512 * 512 * n3)
+        out["rows"].append({"n3": n3, "spectrum_mb": 512 * 512 * n3 * 6 * 8 * 257 / 256 / 2 / 1e6,
+                            "ms_scaled": {k: v[0] / v[1] * scale for k, v in prof.items()},
+                            "plan": {k: plan[k] for k in ("x1_lines", "x1_vb", "x5_lines", "y_w", "z_w", "e_planes")}})
+    print(json.dumps(out), flush=True)
+
+
 def run_warm_layers(args, rank, local, world):
     """Per-layer CUDA-event times of the warm start's tensor-core inference on an N^3 Boolean sample
     (random weights: the times do not depend on the values), the whole forward, the initial strain,
@@ -757,6 +840,12 @@ def main():
         return
     if args.warm_layers > 0:
         run_warm_layers(args, rank, local, world)
+        return
+    if args.thin_grids:
+        run_thin_grids(args, rank, local)
+        return
+    if args.x1_sweep:
+        run_x1_sweep(args, rank, local)
         return
     if args.warmstart > 0:
         run_warmstart(args, rank, local, world)

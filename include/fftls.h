@@ -215,7 +215,8 @@ fftls_status fftls_solve_batched(fftls_ctx* ctx, const fftls_problem* probs, int
 
 /* Tile schedules held by this context, one row of FFTLS_PLAN_FIELDS ints per grid,
  * operator and precision: {precision (0 float, 1 double), n1, n2, n3, green,
- * lines per batch of the forward x1 pass, voxels per thread it loads together,
+ * lines per batch of the forward x1 pass, voxels per thread it loads together
+ * (0: each batch staged in shared memory by bulk copies, FP32 only),
  * lines per batch of the inverse x1 pass, modes per tile of the x2 pass, of the
  * x3 pass, x3-planes per block of the real-space eta kernel (0: not used),
  * 1 if tuned on the device else 0, threads per block of the x2 pass and of
@@ -224,6 +225,22 @@ fftls_status fftls_solve_batched(fftls_ctx* ctx, const fftls_problem* probs, int
  * The paper has no counterpart (an implementation detail of the GPU path). */
 #define FFTLS_PLAN_FIELDS 14
 fftls_status fftls_tile_plans(const fftls_ctx* ctx, int* rows, int* count);
+
+/* Imports `count` rows in the layout of fftls_tile_plans (host memory, copied;
+ * the caller keeps ownership): later solves on this context use each row's
+ * schedule for its grid, operator and precision as it is, without tuning (a
+ * row with n3 = 1 also serves the 2D problem on n1 x n2; a row with 0 planes
+ * for the real-space eta kernel serves only the operators that do not use it).
+ * Rows replace schedules held for the same key.  FFTLS_E_INVALID_ARG, with
+ * nothing imported, for a row outside the values the tuner can choose (lines
+ * 1..8, voxels per load 1, 2 or 4, or 0 for FP32 with n1 a multiple of 16;
+ * widths 1..16, powers of two;
+ * thread counts 0 or those of the width); a schedule that does not fit shared
+ * memory makes the solve that would use it fail with FFTLS_E_UNSUPPORTED_SIZE.
+ * Lets a caller reuse the schedules tuned once on another context (the
+ * arithmetic of a solve does not depend on its schedule beyond the grouping
+ * of partial sums). */
+fftls_status fftls_set_tile_plans(fftls_ctx* ctx, const int* rows, int count);
 
 /* Kernels launched on this context since creation (nodes of CUDA graphs
  * counted one by one, including kernels that exit early once the solve has

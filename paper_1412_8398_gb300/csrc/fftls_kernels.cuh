@@ -125,7 +125,7 @@ struct IterArgs {
   const double* smp_par;
   // launch shapes (host-computed)
   int x1_lines, x1_blocks;  // forward x1 pass: lines per batch, blocks (grid-stride over batches)
-  int x1_vb;                // forward x1 pass: voxels per thread loaded together (1, 2 or 4)
+  int x1_vb;                // forward x1 pass: voxels per thread loaded together (1, 2 or 4; 0: staged by bulk copies)
   int x5_lines, x5_blocks;  // inverse x1 pass
   int x_threads;
   int y_w, y_threads, z_w, z_threads;
@@ -133,6 +133,13 @@ struct IterArgs {
   int e_planes, e_blocks;  // real-space eta: x3-planes per block, blocks (tiles x slabs)
   size_t e_smem;
 };
+
+// Shared memory of the forward x1 pass: twiddles, the tile of G lines, and for the
+// staged variant the batch's eps (n_c rows of G n1 floats) and phase ids, 16-byte aligned.
+__host__ __device__ inline size_t fwd_x_stage_offset(size_t tw_and_tile) { return (tw_and_tile + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t fwd_x_stage_bytes(int G, int n1, int nc) {
+  return (size_t)G * n1 * (nc * sizeof(float) + 1);
+}
 
 // Threads per block of the strided (x2 / x3) passes with W modes per tile: a
 // compile-time count, so that every stage of the tile transforms has a fixed

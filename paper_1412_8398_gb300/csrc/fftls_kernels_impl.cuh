@@ -332,6 +332,81 @@ __device__ __forceinline__ void load_pair(const double2* d, double2& a, double2&
 // ---------------------------------------------------------------------------
 // VB: voxels per thread whose loads are issued together (a tuned trade of
 // registers against loads in flight).
+// One voxel of the forward x1 pass: sigma = C(x) : eps and the packed row of the
+// transformed fields (tau, or sigma in the sigma form; tau and sigma for DUAL),
+// two real components per complex column; the FP32 sums of sigma and eps gathered.
+template <typename T, int DIM, bool DUAL>
+__device__ __forceinline__ void fwd_x_voxel(const IterArgs<T>& a, const T (&e)[Comp<DIM>::NC], int ph,
+                                            T (&accf)[2 * Comp<DIM>::NC], typename Cplx<T>::type* row) {
+  typedef typename Cplx<T>::type T2;
+  constexpr int NC = Comp<DIM>::NC;
+  constexpr int nout = DUAL ? 2 * NC : NC;
+  constexpr int NP = (nout + 1) / 2;
+  const T* cf = a.coef + ph * kCoef;
+  const T lam = cf[0], mu2 = cf[1], dlam = cf[2], dmu2 = cf[3];
+  T tr = e[0] + e[1];
+  if (DIM == 3) tr += e[2];
+  T out[nout];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const bool diag = c < DIM;
+    const T s = mu2 * e[c] + (diag ? lam * tr : (T)0);
+    accf[c] += s;
+    accf[NC + c] += e[c];
+    if (DUAL) {
+      out[c] = dmu2 * e[c] + (diag ? dlam * tr : (T)0);
+      out[NC + c] = s;
+    } else {
+      out[c] = a.tauform ? dmu2 * e[c] + (diag ? dlam * tr : (T)0) : s;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    T2 w;
+    w.x = out[2 * p];
+    w.y = (2 * p + 1 < nout) ? out[2 * p + 1] : (T)0;
+    row[p] = w;
+  }
+}
+
+// The packed real transforms of a batch of nl lines (tile, line stride BS) untangled
+// into the half spectrum of lines l0 ... l0 + nl - 1: one thread per mode k, every
+// component of it.
+template <typename T, int DIM, bool DUAL>
+__device__ __forceinline__ void fwd_x_untangle(const IterArgs<T>& a, const typename Cplx<T>::type* tile, int nl,
+                                               long long l0, int BS, const FastDiv& fH) {
+  typedef typename Cplx<T>::type T2;
+  constexpr int NC = Comp<DIM>::NC;
+  constexpr int nout = DUAL ? 2 * NC : NC;
+  constexpr int NP = (nout + 1) / 2;
+  constexpr int CP = odd_stride(NP);
+  const int L1 = a.g.n1, H = a.g.H;
+  const int* __restrict__ pos = a.pos[0];
+  for (int idx = threadIdx.x; idx < nl * H; idx += blockDim.x) {
+    const int gl = fdiv(idx, fH), k = idx - gl * H;
+    const T2* r0 = tile + gl * BS + prow(__ldg(&pos[k]), 1) * CP;
+    const T2* r1 = tile + gl * BS + prow(__ldg(&pos[k == 0 ? 0 : L1 - k]), 1) * CP;
+    const long long m = (l0 + gl) * (long long)H + k;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const T2 Z = r0[p], Zm = r1[p];
+      T2 A, B;
+      A.x = (T)0.5 * (Z.x + Zm.x);
+      A.y = (T)0.5 * (Z.y - Zm.y);
+      B.x = (T)0.5 * (Z.y + Zm.y);
+      B.y = (T)-0.5 * (Z.x - Zm.x);
+      const int o0 = 2 * p, o1 = 2 * p + 1;
+      T2* d0 = (o0 < NC ? a.specA : a.specB) + m * NC + (o0 % NC);
+      if (NC % 2 == 0 && o1 < nout && (o0 < NC) == (o1 < NC)) {
+        store_pair(d0, A, B);  // components o0 (even), o1 adjacent in one spectrum: 16-byte aligned
+      } else {
+        *d0 = A;
+        if (o1 < nout) (o1 < NC ? a.specA : a.specB)[m * NC + (o1 % NC)] = B;
+      }
+    }
+  }
+}
+
 template <typename T, int DIM, bool DUAL, int VB>
 __device__ __forceinline__ void k_fwd_x_body(const IterArgs<T>& a, const AxisPlan* pl) {
   typedef typename Cplx<T>::type T2;
@@ -345,7 +420,6 @@ __device__ __forceinline__ void k_fwd_x_body(const IterArgs<T>& a, const AxisPla
   constexpr int NP = (nout + 1) / 2;
   constexpr int CP = odd_stride(NP);
   const int BS = padded_rows(L1) * CP;
-  const int* __restrict__ pos = a.pos[0];
   const long long nlines = (long long)g.n2 * g.n3;
   const int G = a.x1_lines;
   // FP64 running sums of <sigma>, <eps> per warp (the FP32 sums of one batch are
@@ -379,37 +453,7 @@ __device__ __forceinline__ void k_fwd_x_body(const IterArgs<T>& a, const AxisPla
       const int idx = ib + v * blockDim.x;
       if (idx >= nl * L1) break;
       const int gl = fdiv(idx, fL), x = idx - gl * L1;
-      const T* cf = a.coef + phv[v] * kCoef;
-      const T lam = cf[0], mu2 = cf[1], dlam = cf[2], dmu2 = cf[3];
-      T e[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) e[c] = ev[v][c];
-      T tr = e[0] + e[1];
-      if (DIM == 3) tr += e[2];
-      T out[nout];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const bool diag = c < DIM;
-        const T s = mu2 * e[c] + (diag ? lam * tr : (T)0);
-        accf[c] += s;
-        accf[NC + c] += e[c];
-        if (DUAL) {
-          out[c] = dmu2 * e[c] + (diag ? dlam * tr : (T)0);
-          out[NC + c] = s;
-        } else {
-          out[c] = a.tauform ? dmu2 * e[c] + (diag ? dlam * tr : (T)0) : s;
-        }
-      }
-      T2* row = tile + gl * BS + prow(x, 1) * CP;
-#pragma unroll
-      for (int p = 0; p < NC; ++p) {
-        if (p < NP) {
-          T2 w;
-          w.x = out[2 * p];
-          w.y = (2 * p + 1 < nout) ? out[2 * p + 1] : (T)0;
-          row[p] = w;
-        }
-      }
+      fwd_x_voxel<T, DIM, DUAL>(a, ev[v], phv[v], accf, tile + gl * BS + prow(x, 1) * CP);
       }
     }
 #pragma unroll
@@ -424,30 +468,131 @@ __device__ __forceinline__ void k_fwd_x_body(const IterArgs<T>& a, const AxisPla
       if (ln < nlines) prefetch_voxels<T>(a.eps, a.phase, g.N, NC, ln * L1, (int)min((long long)G, nlines - ln) * L1);
     }
     tile_fft_ct<CP, NP, true>(tile, nl, BS, pl[0], tws, false);
-    // untangle the packed real transforms: one thread per mode k, every component of it
-    for (int idx = threadIdx.x; idx < nl * H; idx += blockDim.x) {
-      const int gl = fdiv(idx, fH), k = idx - gl * H;
-      const T2* r0 = tile + gl * BS + prow(__ldg(&pos[k]), 1) * CP;
-      const T2* r1 = tile + gl * BS + prow(__ldg(&pos[k == 0 ? 0 : L1 - k]), 1) * CP;
-      const long long m = (l0 + gl) * (long long)H + k;
+    fwd_x_untangle<T, DIM, DUAL>(a, tile, nl, l0, BS, fH);
+    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * NC) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wacc[w][threadIdx.x];
+    a.part_mean[(size_t)blockIdx.x * 2 * NC + threadIdx.x] = t;
+  }
+}
+
+// Whether the forward x1 pass may stage its batches by bulk copies (x1_vb == 0):
+// FP32, every component row of a batch and its phase ids 16-byte aligned and a
+// multiple of 16 bytes long (n1 a multiple of 16, aligned field starts).
+template <typename T>
+__host__ __device__ inline bool fwd_x_staged_ok(const IterArgs<T>& a) {
+  return sizeof(T) == 4 && a.g.n1 % 16 == 0 && ((size_t)a.eps & 15) == 0 && ((size_t)a.phase & 15) == 0 &&
+         (a.nsmp <= 1 || ((a.st_field * (long long)sizeof(T)) % 16 == 0 && a.st_phase % 16 == 0));
+}
+
+// The forward x1 pass with each batch's eps and phase ids moved into shared memory by bulk copies
+// (one copy per component row of the batch, completion counted in bytes on an mbarrier).  The copies
+// of the next batch start as soon as this batch has been read out of the staging area, so they run
+// under its transform and untangling; the voxels, their order per thread and the arithmetic are
+// those of the register-loading variant, so the transformed fields are the same bit for bit (the
+// FP32 partial sums of <sigma> and <eps> agree to rounding: the compiler may contract them into
+// fused multiply-adds differently).  A copy that has not completed after kBulkWaitRounds waits
+// stops the solve (ctl->fault).
+template <int DIM, bool DUAL>
+__device__ __forceinline__ void k_fwd_x_staged_body(const IterArgs<float>& a, const AxisPlan* pl) {
+  typedef float T;
+  typedef float2 T2;
+  constexpr int NC = Comp<DIM>::NC;
+  constexpr int VB = 2;
+  if (a.ctrl->state != kRunning) return;
+  const Geom g = a.g;
+  const int L1 = g.n1, H = g.H;
+  T2* tile;
+  const T2* tws = load_twiddles(a.tw[0], L1, kTwX1, &tile);
+  constexpr int nout = DUAL ? 2 * NC : NC;
+  constexpr int NP = (nout + 1) / 2;
+  constexpr int CP = odd_stride(NP);
+  const int BS = padded_rows(L1) * CP;
+  const long long nlines = (long long)g.n2 * g.n3;
+  const int G = a.x1_lines;
+  const long long step = (long long)gridDim.x * G;
+  __shared__ double wacc[8][2 * NC];
+  __shared__ __align__(8) unsigned long long bar_word;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < 8 * 2 * NC; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const size_t so = fwd_x_stage_offset((size_t)((const unsigned char*)(tile + G * BS) - smem_raw));
+  const T* raw = reinterpret_cast<const T*>(smem_raw + so);
+  const uint8_t* rph = smem_raw + so + (size_t)NC * G * L1 * sizeof(T);
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_word);
+  const uint32_t sraw = (uint32_t)__cvta_generic_to_shared(raw);
+  const uint32_t sph = (uint32_t)__cvta_generic_to_shared(rph);
+  const int cstride = G * L1;  // floats between the staged component rows
+  auto issue = [&](long long l) {
+    const int n = (int)min((long long)G, nlines - l) * L1;
+    const uint32_t eb = (uint32_t)n * (uint32_t)sizeof(T);
+    mbar_arrive_expect_tx(bar, NC * eb + (uint32_t)n);
 #pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const T2 Z = r0[p], Zm = r1[p];
-        T2 A, B;
-        A.x = (T)0.5 * (Z.x + Zm.x);
-        A.y = (T)0.5 * (Z.y - Zm.y);
-        B.x = (T)0.5 * (Z.y + Zm.y);
-        B.y = (T)-0.5 * (Z.x - Zm.x);
-        const int o0 = 2 * p, o1 = 2 * p + 1;
-        T2* d0 = (o0 < NC ? a.specA : a.specB) + m * NC + (o0 % NC);
-        if (NC % 2 == 0 && o1 < nout && (o0 < NC) == (o1 < NC)) {
-          store_pair(d0, A, B);   // components o0 (even), o1 adjacent in one spectrum: 16-byte aligned
-        } else {
-          *d0 = A;
-          if (o1 < nout) (o1 < NC ? a.specA : a.specB)[m * NC + (o1 % NC)] = B;
+    for (int c = 0; c < NC; ++c)
+      bulk_load(sraw + (uint32_t)(c * cstride * sizeof(T)), a.eps + (long long)c * g.N + l * L1, eb, bar);
+    bulk_load(sph, a.phase + l * L1, (uint32_t)n, bar);
+  };
+  long long l0 = (long long)blockIdx.x * G;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    if (l0 < nlines) issue(l0);
+  }
+  __syncthreads();
+
+  const FastDiv fL = make_fastdiv(L1), fH = make_fastdiv(H);
+  for (uint32_t parity = 0; l0 < nlines; l0 += step, parity ^= 1u) {
+    const int nl = (int)min((long long)G, nlines - l0);
+    bool done = false;
+    for (long long k = 0; k < kBulkWaitRounds && !done; ++k) done = mbar_try_wait(bar, parity);
+    if (__syncthreads_or(!done)) {
+      if (threadIdx.x == 0) {
+        a.ctrl->fault = 1;
+        a.ctrl->state = kStopped;
+      }
+      // the block's own copies: one more bounded wait before it gives up its shared memory
+      for (long long k = 0; k < kBulkWaitRounds && !done; ++k) done = mbar_try_wait(bar, parity);
+      return;
+    }
+    T accf[2 * NC];
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) accf[c] = (T)0;
+    for (int ib = threadIdx.x; ib < nl * L1; ib += VB * blockDim.x) {
+      T ev[VB][NC];
+      int phv[VB];
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+        const int idx = ib + v * blockDim.x;
+        if (idx < nl * L1) {
+          phv[v] = rph[idx];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ev[v][c] = raw[c * cstride + idx];
         }
       }
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+        const int idx = ib + v * blockDim.x;
+        if (idx >= nl * L1) break;
+        const int gl = fdiv(idx, fL), x = idx - gl * L1;
+        fwd_x_voxel<T, DIM, DUAL>(a, ev[v], phv[v], accf, tile + gl * BS + prow(x, 1) * CP);
+      }
     }
+#pragma unroll
+    for (int c = 0; c < 2 * NC; ++c) {
+      T x = accf[c];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) wacc[warp][c] += (double)x;
+    }
+    __syncthreads();  // the staging area is read out: the next batch's copies may overwrite it
+    if (threadIdx.x == 0 && l0 + step < nlines) {
+      fence_async_shared();
+      issue(l0 + step);
+    }
+    tile_fft_ct<CP, NP, true>(tile, nl, BS, pl[0], tws, false);
+    fwd_x_untangle<T, DIM, DUAL>(a, tile, nl, l0, BS, fH);
     __syncthreads();
   }
   __syncthreads();
@@ -460,13 +605,15 @@ __device__ __forceinline__ void k_fwd_x_body(const IterArgs<T>& a, const AxisPla
 
 // GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
 template <typename T, int DIM, bool DUAL, int VB, bool GRP>
-__global__ void __launch_bounds__(256) k_fwd_x(const __grid_constant__ IterArgs<T> a_) {
+__global__ void __launch_bounds__(256, VB == 0 ? 4 : 1) k_fwd_x(const __grid_constant__ IterArgs<T> a_) {
   if constexpr (GRP) {
     IterArgs<T> a = a_;
     at_sample(a, blockIdx.y);
-    k_fwd_x_body<T, DIM, DUAL, VB>(a, a_.pl);
+    if constexpr (VB == 0) k_fwd_x_staged_body<DIM, DUAL>(a, a_.pl);
+    else k_fwd_x_body<T, DIM, DUAL, VB>(a, a_.pl);
   } else {
-    k_fwd_x_body<T, DIM, DUAL, VB>(a_, a_.pl);
+    if constexpr (VB == 0) k_fwd_x_staged_body<DIM, DUAL>(a_, a_.pl);
+    else k_fwd_x_body<T, DIM, DUAL, VB>(a_, a_.pl);
   }
 }
 
@@ -670,8 +817,8 @@ __device__ __forceinline__ void k_mid_y_body(const IterArgs<T>& a, const AxisPla
   const long long base = ((long long)blockIdx.y * n2 * g.H + x0) * NC;
   const long long rstride = (long long)g.H * NC;
   if (!tile_load<C, false>(tile, spec + base, rstride, n2, cols, a.ctrl)) return;
-  if (inv) tile_fft_strided<C, NT, true>(tile, pl[1], tws);
-  else tile_fft_strided<C, NT, false>(tile, pl[1], tws);
+  if (inv) tile_fft_strided<C, NT, true, false>(tile, pl[1], tws);
+  else tile_fft_strided<C, NT, false, true>(tile, pl[1], tws);
   tile_store<C, false>(tile, spec + base, rstride, n2, cols);
 }
 
@@ -1018,7 +1165,7 @@ __device__ __forceinline__ void k_fourier_z_body(const IterArgs<T>& a, const Axi
   const long long base = ((long long)py * g.H + x0) * NC;
   const long long zstride = (long long)g.n2 * g.H * NC;
   if (!tile_load<C, true>(tile, spec + base, zstride, n3, cols, a.ctrl)) return;
-  tile_fft_strided<C, NT, false>(tile, pl[2], tws);
+  tile_fft_strided<C, NT, false, false>(tile, pl[2], tws);
   T eta_acc = (T)0;
   if constexpr (FAST) {
     static_assert(DIM == 3 && NT % W == 0, "fast Fourier pass: 3D, whole modes per thread");
@@ -1064,7 +1211,7 @@ __device__ __forceinline__ void k_fourier_z_body(const IterArgs<T>& a, const Axi
   }
   __syncthreads();
   if (do_green) {
-    tile_fft_strided<C, NT, true>(tile, pl[2], tws);
+    tile_fft_strided<C, NT, true, false>(tile, pl[2], tws);
     tile_store<C, true>(tile, spec + base, zstride, n3, cols);
   }
   if (!a.eta_real) {  // with the real-space eta the x1 pass owns part_eta
@@ -1458,7 +1605,8 @@ cudaError_t launch_fwd_x_t(const IterArgs<T>& a, cudaStream_t s) {
 // FP64 forward passes (the few certification passes of the ladder) load one voxel at a time
 #define FFTLS_FWD_VB(D, U)                                                                              \
   if constexpr (sizeof(T) == 8) FFTLS_FWD(D, U, 1);                                                     \
-  else if (a.x1_vb >= 4) FFTLS_FWD(D, U, 4);                                                            \
+  else if (a.x1_vb == 0 && fwd_x_staged_ok(a)) FFTLS_FWD(D, U, 0);                                      \
+  else if (a.x1_vb >= 4 || a.x1_vb == 0) FFTLS_FWD(D, U, 4);                                            \
   else if (a.x1_vb == 2) FFTLS_FWD(D, U, 2);                                                            \
   else FFTLS_FWD(D, U, 1)
   if (a.dim == 3) {
@@ -1632,6 +1780,12 @@ cudaError_t set_attrs_x_t(size_t smax) {
     FFTLS_ATTR((k_fwd_x<T, 2, false, 1, GRP>));
   }
   if constexpr (sizeof(T) == 4) {
+    FFTLS_ATTR((k_fwd_x<T, 3, true, 0, GRP>));
+    FFTLS_ATTR((k_fwd_x<T, 3, false, 0, GRP>));
+    if constexpr (!GRP) {
+      FFTLS_ATTR((k_fwd_x<T, 2, true, 0, GRP>));
+      FFTLS_ATTR((k_fwd_x<T, 2, false, 0, GRP>));
+    }
     FFTLS_ATTR((k_fwd_x<T, 3, true, 2, GRP>));
     FFTLS_ATTR((k_fwd_x<T, 3, true, 4, GRP>));
     FFTLS_ATTR((k_fwd_x<T, 3, false, 2, GRP>));

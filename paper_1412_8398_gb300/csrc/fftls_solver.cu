@@ -465,8 +465,13 @@ bool apply_plan(const Setup& S, IterArgs<T>& a, bool real_eta, const TilePlan& P
   if (G.twx + G1 * G.line1 > G.lim || G.twx + G5 * G.line5 > G.lim) return false;
   a.x1_lines = G1;
   a.x5_lines = G5;
-  a.x1_vb = P.x1_vb >= 4 ? 4 : P.x1_vb == 2 ? 2 : 1;
+  a.x1_vb = P.x1_vb >= 4 ? 4 : P.x1_vb == 2 ? 2 : P.x1_vb == 0 ? 0 : 1;
   a.x1_smem = G.twx + G1 * G.line1;
+  if (a.x1_vb == 0) {  // staged batches (FP32): the staging area after the tile
+    if (sizeof(T) != 4 || g.n1 % 16 != 0) return false;
+    a.x1_smem = fwd_x_stage_offset(a.x1_smem) + fwd_x_stage_bytes(G1, g.n1, S.nc);
+    if (a.x1_smem > G.lim) return false;
+  }
   a.x5_smem = G.twx + G5 * G.line5;
   a.x_threads = 256;
   a.x1_blocks = (int)std::min<long long>((G.nlines + G1 - 1) / G1, (long long)S.num_sms * 8);
@@ -729,7 +734,8 @@ fftls_status tune_plan(fftls_ctx* c, const Setup& S, IterArgs<T>& a, bool real_e
   {
     float best = INFINITY;
     int bl = P.x1_lines, bv = P.x1_vb;
-    const std::vector<int> vbs = sizeof(T) == 8 ? std::vector<int>{1} : std::vector<int>{1, 2, 4};
+    // (vb = 0: the batches staged in shared memory by bulk copies, FP32)
+    const std::vector<int> vbs = sizeof(T) == 8 ? std::vector<int>{1} : std::vector<int>{1, 2, 4, 0};
     for (int lines : {1, 2, 4, 8})
       for (int vb : vbs) {
         if (err != cudaSuccess) break;
@@ -900,6 +906,50 @@ fftls_status fftls_tile_plans(const fftls_ctx* c, int* rows, int* count) {
     memcpy(rows + (size_t)i * FFTLS_PLAN_FIELDS, row, sizeof(row));
   }
   *count = held;
+  return FFTLS_OK;
+}
+
+fftls_status fftls_set_tile_plans(fftls_ctx* c, const int* rows, int count) {
+  if (!c || count < 0 || (count > 0 && !rows)) return FFTLS_E_INVALID_ARG;
+  std::vector<std::pair<PlanKey, TilePlan>> add;
+  for (int i = 0; i < count; ++i) {
+    const int* r = rows + (size_t)i * FFTLS_PLAN_FIELDS;
+    const int prec = r[0], n1 = r[1], n2 = r[2], n3 = r[3], green = r[4];
+    TilePlan P;
+    P.x1_lines = r[5];
+    P.x1_vb = r[6];
+    P.x5_lines = r[7];
+    P.y_w = r[8];
+    P.z_w = r[9];
+    P.e_planes = r[10];
+    P.y_thr = r[12];
+    P.z_thr = r[13];
+    P.tuned = 1;  // imported schedules are used as they are, never re-tuned
+    auto pow2_16 = [](int w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16; };
+    auto thr_ok = [](int t, int w) { return t == 0 || t == fftls::strided_threads(w); };
+    const bool ok = (prec == 0 || prec == 1) && n1 >= 1 && n2 >= 1 && n3 >= 1 && green >= kMS && green <= kRotated &&
+                    P.x1_lines >= 1 && P.x1_lines <= 8 && P.x5_lines >= 1 && P.x5_lines <= 8 &&
+                    (P.x1_vb == 1 || P.x1_vb == 2 || P.x1_vb == 4 || (P.x1_vb == 0 && prec == 0 && n1 % 16 == 0)) &&
+                    (prec == 0 || P.x1_vb == 1) && pow2_16(P.y_w) && pow2_16(P.z_w) && P.e_planes >= 0 &&
+                    P.e_planes <= n3 && thr_ok(P.y_thr, P.y_w) && thr_ok(P.z_thr, P.z_w);
+    if (!ok) return set_err(c, FFTLS_E_INVALID_ARG, "tile plan row %d is not a valid schedule", i);
+    // a row names the grid, not the dimension: it serves the 3D problem on it and, with n3 = 1, the 2D one
+    for (int dim = 2; dim <= 3; ++dim) {
+      if (dim == 2 && n3 != 1) continue;
+      const bool real_eta = dim == 3 && green != kMS;
+      if (real_eta && P.e_planes < 1) continue;
+      add.push_back({PlanKey{prec, n1, n2, n3, dim, green, real_eta ? 1 : 0}, P});
+    }
+  }
+  for (auto& kv : add) {
+    bool have = false;
+    for (auto& mine : c->plans)
+      if (mine.first == kv.first) {
+        mine.second = kv.second;
+        have = true;
+      }
+    if (!have) c->plans.push_back(kv);
+  }
   return FFTLS_OK;
 }
 

@@ -112,6 +112,7 @@ _SIGNATURES = {
     "fftls_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "fftls_tile_plans": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "fftls_set_tile_plans": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "fftls_solve_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Problem), ctypes.c_int,
                                            ctypes.POINTER(_Options), ctypes.POINTER(_Result),
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -412,6 +413,19 @@ class Solver:
         rows = (ctypes.c_int * (w * max(n.value, 1)))()
         self.lib.fftls_tile_plans(self.handle, rows, ctypes.byref(n))
         return [dict(zip(keys, rows[w * i:w * i + w])) for i in range(n.value)]
+
+    def set_tile_plans(self, plans: list) -> None:
+        """Import schedules (dicts as returned by tile_plans) for later solves (see fftls_set_tile_plans)."""
+        keys = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x1_vb", "x5_lines", "y_w", "z_w", "e_planes",
+                "tuned", "y_threads", "z_threads")
+        w = len(keys)
+        rows = (ctypes.c_int * (w * max(len(plans), 1)))()
+        for i, p in enumerate(plans):
+            for j, k in enumerate(keys):
+                rows[w * i + j] = int(p.get(k, 0))
+        st = self.lib.fftls_set_tile_plans(self.handle, rows, len(plans))
+        if st:
+            raise FftlsError(st, self.last_error())
 
     def profile(self) -> dict:
         """Per-kernel (total ms, launches) of the last solve run with profile=True."""

@@ -44,7 +44,7 @@ def test_tuned_schedule_matches_default(build, green, scheme, shape):
         s_tun.close()
     assert [p["tuned"] for p in plans0] == [0] and [p["tuned"] for p in plans1] == [1]
     p = plans1[0]
-    assert p["x1_lines"] in (1, 2, 4, 8) and p["x5_lines"] in (1, 2, 4, 8) and p["x1_vb"] in (1, 2, 4)
+    assert p["x1_lines"] in (1, 2, 4, 8) and p["x5_lines"] in (1, 2, 4, 8) and p["x1_vb"] in (0, 1, 2, 4)
     assert p["y_w"] in (1, 2, 4, 8, 16) and p["z_w"] in (1, 2, 4, 8, 16)
     assert np.abs(r1.strain - r0.strain).max() < 1e-12
     np.testing.assert_allclose(r1.eta_history, r0.eta_history, rtol=1e-12)
@@ -72,3 +72,57 @@ def test_plan_cached_per_grid_and_precision(build):
     assert sorted(p["precision"] for p in plans) == [0, 1] and all(p["tuned"] for p in plans)
     # the second solve of the same grid does not tune again: far fewer launches than the first
     assert (k2 - k1) < (k1 - k0)
+
+
+@pytest.mark.parametrize("green,shape", [("R", (64, 24, 20)), ("MS", (32, 16, 12)), ("R", (48, 40))])
+def test_imported_schedules_same_bits(build, green, shape):
+    """Schedules imported with set_tile_plans are used as they are: every forward-x1 variant
+    (voxels loaded 1, 2 or 4 at a time, or the batch staged in shared memory by bulk copies)
+    of one batch size gives the same FP32 fields bit for bit (the same voxels per thread, in the
+    same order); eta, normalised by FP32 partial sums of <sigma>, agrees to their rounding."""
+    fftls = build
+    ph, _ = MS.boolean_spheres(tuple(shape), 2.5, 0.3, seed=12)
+    lam, mu = MS.young_poisson_phases([(1.0, 0.3), (30.0, 0.25)])
+    d = ph.ndim
+    eb = np.eye(d)
+    eb[0, 1] = eb[1, 0] = 0.2
+    n = tuple(reversed(ph.shape)) + (1,) * (3 - d)  # (n1, n2, n3) of the solve
+    gcode = {"MS": 0, "C": 1, "W": 2, "R": 3}[green]
+    runs = {}
+    for lines, vb in [(1, 4), (4, 4), (2, 1), (1, 0), (2, 0), (4, 0)]:
+        plan = {"precision": 0, "n1": n[0], "n2": n[1], "n3": n[2], "green": gcode, "x1_lines": lines,
+                "x1_vb": vb, "x5_lines": 2, "y_w": 2, "z_w": 2, "e_planes": 4 if (d == 3 and green != "MS") else 0}
+        s = fftls.Solver(0)
+        try:
+            s.set_tile_plans([plan])
+            r = s.solve(ph, lam, mu, eb, green, "AS", tol=0.0, max_iter=5, precision="fp32")
+            held = [p for p in s.tile_plans() if p["precision"] == 0]
+        finally:
+            s.close()
+        assert len(held) == 1 and held[0]["x1_lines"] == lines and held[0]["x1_vb"] == vb and held[0]["tuned"] == 1
+        runs[(lines, vb)] = r
+    for lines, vb in [(1, 4), (2, 1), (4, 4)]:
+        assert np.array_equal(runs[(lines, 0)].strain, runs[(lines, vb)].strain)
+    # eta's normalisation <sigma> comes from FP32 partial sums, which the compiler may contract
+    # differently per variant and other batch sizes group differently: equal to FP32 rounding
+    ref = runs[(1, 4)]
+    for r in runs.values():
+        assert np.abs(r.strain - ref.strain).max() <= 1e-6 * np.abs(ref.strain).max()
+        np.testing.assert_allclose(r.eta_history, ref.eta_history, rtol=1e-6)
+
+
+def test_set_tile_plans_rejects_invalid_rows(build):
+    fftls = build
+    s = fftls.Solver(0)
+    try:
+        good = {"precision": 0, "n1": 32, "n2": 32, "n3": 32, "green": 3, "x1_lines": 2, "x1_vb": 4,
+                "x5_lines": 2, "y_w": 4, "z_w": 4, "e_planes": 8}
+        for bad in [{"x1_lines": 9}, {"x1_vb": 3}, {"precision": 1, "x1_vb": 0}, {"n1": 40, "x1_vb": 0}, {"y_w": 3},
+                    {"e_planes": 33}, {"y_threads": 64}]:
+            with pytest.raises(fftls.FftlsError):
+                s.set_tile_plans([dict(good, **bad)])
+        assert s.tile_plans() == []
+        s.set_tile_plans([good])
+        assert [p["x1_lines"] for p in s.tile_plans()] == [2]
+    finally:
+        s.close()
