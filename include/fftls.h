@@ -220,10 +220,11 @@ fftls_status fftls_solve_batched(fftls_ctx* ctx, const fftls_problem* probs, int
  * lines per batch of the inverse x1 pass, modes per tile of the x2 pass, of the
  * x3 pass, x3-planes per block of the real-space eta kernel (0: not used),
  * 1 if tuned on the device else 0, threads per block of the x2 pass and of
- * the x3 pass (0: chosen from the tile size)}.  Copies min(*count, held) rows into
+ * the x3 pass (0: chosen from the tile size), how the inverse x1 pass reads eps
+ * (1: loaded by the threads, 0: staged in shared memory by bulk copies, FP32)}.  Copies min(*count, held) rows into
  * `rows` (may be NULL when *count is 0) and returns the number held in *count.
  * The paper has no counterpart (an implementation detail of the GPU path). */
-#define FFTLS_PLAN_FIELDS 14
+#define FFTLS_PLAN_FIELDS 15
 fftls_status fftls_tile_plans(const fftls_ctx* ctx, int* rows, int* count);
 
 /* Imports `count` rows in the layout of fftls_tile_plans (host memory, copied;
@@ -233,8 +234,8 @@ fftls_status fftls_tile_plans(const fftls_ctx* ctx, int* rows, int* count);
  * for the real-space eta kernel serves only the operators that do not use it).
  * Rows replace schedules held for the same key.  FFTLS_E_INVALID_ARG, with
  * nothing imported, for a row outside the values the tuner can choose (lines
- * 1..8, voxels per load 1, 2 or 4, or 0 for FP32 with n1 a multiple of 16;
- * widths 1..16, powers of two;
+ * 1..8, voxels per load 1, 2 or 4, or 0 for FP32 with n1 a multiple of 16,
+ * inverse loads 1, or 0 on the same terms; widths 1..16, powers of two;
  * thread counts 0 or those of the width); a schedule that does not fit shared
  * memory makes the solve that would use it fail with FFTLS_E_UNSUPPORTED_SIZE.
  * Lets a caller reuse the schedules tuned once on another context (the

@@ -127,6 +127,7 @@ struct IterArgs {
   int x1_lines, x1_blocks;  // forward x1 pass: lines per batch, blocks (grid-stride over batches)
   int x1_vb;                // forward x1 pass: voxels per thread loaded together (1, 2 or 4; 0: staged by bulk copies)
   int x5_lines, x5_blocks;  // inverse x1 pass
+  int x5_vb;                // inverse x1 pass: 1 register loads of eps, 0 staged by bulk copies (FP32)
   int x_threads;
   int y_w, y_threads, z_w, z_threads;
   size_t x1_smem, x5_smem, y_smem, z_smem;

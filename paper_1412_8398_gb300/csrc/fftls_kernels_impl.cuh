@@ -1340,7 +1340,11 @@ __global__ void k_reduce_eta(const __grid_constant__ IterArgs<T> a_, int n_eta_p
 // ---------------------------------------------------------------------------
 // K5: inverse x1 transform (half complex -> real) + scheme update
 // ---------------------------------------------------------------------------
-template <typename T, int DIM>
+// STAGED (FP32): the batch's eps and phase ids move into shared memory by bulk copies issued before
+// its packing and transform, so the update reads them from shared memory instead of waiting on L2
+// (completion counted on an mbarrier; a copy lost after kBulkWaitRounds waits stops the solve with
+// ctl->fault).  The arithmetic per voxel is the same: the fields are the same bit for bit.
+template <typename T, int DIM, bool STAGED>
 __device__ __forceinline__ void k_inv_x_body(const IterArgs<T>& a, const AxisPlan* pl) {
   typedef typename Cplx<T>::type T2;
   constexpr int NC = Comp<DIM>::NC;
@@ -1358,10 +1362,40 @@ __device__ __forceinline__ void k_inv_x_body(const IterArgs<T>& a, const AxisPla
   const int G = a.x5_lines;
   double dmax[2] = {0.0, 0.0};
   const FastDiv fL = make_fastdiv(L1), fH = make_fastdiv(H);
+  // staging area after the tile: NC rows of G n1 values, then G n1 phase ids
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar_word;
+  const size_t so = fwd_x_stage_offset((size_t)((const unsigned char*)(tile + G * BS) - smem_raw));
+  const T* raw = reinterpret_cast<const T*>(smem_raw + so);
+  const uint8_t* rph = smem_raw + so + (size_t)NC * G * L1 * sizeof(T);
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_word);
+  const bool stage = STAGED && a.update != kUpdDirectTau;  // the tau form does not read eps
+  if (STAGED) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+  }
+  uint32_t parity = 0;
   for (long long l0 = (long long)blockIdx.x * G; l0 < nlines; l0 += (long long)gridDim.x * G) {
     const int nl = (int)min((long long)G, nlines - l0);
-    // eps and the phase ids are read after the transform: bring them towards L2 now
-    if (a.update != kUpdDirectTau) prefetch_voxels<T>(a.eps, a.phase, g.N, NC, l0 * L1, nl * L1);
+    if (stage) {
+      if (threadIdx.x == 0) {  // the previous batch's update has read the staging area (barrier at loop end)
+        fence_async_shared();
+        const int n = nl * L1;
+        const uint32_t eb = (uint32_t)n * (uint32_t)sizeof(T);
+        const uint32_t sraw = (uint32_t)__cvta_generic_to_shared(raw);
+        mbar_arrive_expect_tx(bar, NC * eb + (uint32_t)n);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          bulk_load(sraw + (uint32_t)(c * G * L1 * sizeof(T)), a.eps + (long long)c * g.N + l0 * L1, eb, bar);
+        bulk_load((uint32_t)__cvta_generic_to_shared(rph), a.phase + l0 * L1, (uint32_t)n, bar);
+      }
+    } else if (a.update != kUpdDirectTau) {
+      // eps and the phase ids are read after the transform: bring them towards L2 now
+      prefetch_voxels<T>(a.eps, a.phase, g.N, NC, l0 * L1, nl * L1);
+    }
     // pack pairs of components into complex lines: one thread per mode k, every component of it
     for (int idx = threadIdx.x; idx < nl * H; idx += blockDim.x) {
       const int gl = fdiv(idx, fH), k = idx - gl * H;
@@ -1405,6 +1439,20 @@ __device__ __forceinline__ void k_inv_x_body(const IterArgs<T>& a, const AxisPla
       }
     }
     tile_fft_ct<CP, NPI, true>(tile, nl, BS, pl[0], tws, true);
+    if (stage) {
+      bool done = false;
+      for (long long k = 0; k < kBulkWaitRounds && !done; ++k) done = mbar_try_wait(bar, parity);
+      if (__syncthreads_or(!done)) {
+        if (threadIdx.x == 0) {
+          a.ctrl->fault = 1;
+          a.ctrl->state = kStopped;
+        }
+        // the block's own copies: one more bounded wait before it gives up its shared memory
+        for (long long k = 0; k < kBulkWaitRounds && !done; ++k) done = mbar_try_wait(bar, parity);
+        return;
+      }
+      parity ^= 1u;
+    }
     for (int idx = threadIdx.x; idx < nl * L1; idx += blockDim.x) {
       const int gl = fdiv(idx, fL), x = idx - gl * L1;
       const long long vox = (l0 + gl) * (long long)L1 + x;
@@ -1415,9 +1463,17 @@ __device__ __forceinline__ void k_inv_x_body(const IterArgs<T>& a, const AxisPla
         e[c] = (c & 1) ? v.y : v.x;
       }
       T o[NC], n[NC];
+      int ph;
+      if (stage) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) o[c] = a.eps[(long long)c * g.N + vox];
-      const T* cf = a.coef + (int)a.phase[vox] * kCoef;
+        for (int c = 0; c < NC; ++c) o[c] = raw[c * G * L1 + idx];
+        ph = rph[idx];
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) o[c] = a.eps[(long long)c * g.N + vox];
+        ph = a.phase[vox];
+      }
+      const T* cf = a.coef + ph * kCoef;
       const int upd = a.update;
       if (upd == kUpdDirectTau) {
 #pragma unroll
@@ -1476,14 +1532,14 @@ __device__ __forceinline__ void k_inv_x_body(const IterArgs<T>& a, const AxisPla
 }
 
 // GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
-template <typename T, int DIM, bool GRP>
+template <typename T, int DIM, bool GRP, bool STAGED>
 __global__ void __launch_bounds__(256) k_inv_x(const __grid_constant__ IterArgs<T> a_) {
   if constexpr (GRP) {
     IterArgs<T> a = a_;
     at_sample(a, blockIdx.y);
-    k_inv_x_body<T, DIM>(a, a_.pl);
+    k_inv_x_body<T, DIM, STAGED>(a, a_.pl);
   } else {
-    k_inv_x_body<T, DIM>(a_, a_.pl);
+    k_inv_x_body<T, DIM, STAGED>(a_, a_.pl);
   }
 }
 
@@ -1699,8 +1755,15 @@ cudaError_t launch_reduce_eta_t(const IterArgs<T>& a, cudaStream_t s) {
 template <typename T, bool GRP>
 cudaError_t launch_inv_x_t(const IterArgs<T>& a, cudaStream_t s) {
   const dim3 grid(a.x5_blocks, GRP ? a.nsmp : 1);
-  if (a.dim == 3) k_inv_x<T, 3, GRP><<<grid, a.x_threads, a.x5_smem, s>>>(a);
-  else if constexpr (!GRP) k_inv_x<T, 2, GRP><<<grid, a.x_threads, a.x5_smem, s>>>(a);
+  // the staged variant (x5_vb == 0, FP32) where the batch's rows are 16-byte aligned, else register loads
+  const bool staged = sizeof(T) == 4 && a.x5_vb == 0 && fwd_x_staged_ok(a);
+  if (a.dim == 3) {
+    if (staged) k_inv_x<T, 3, GRP, sizeof(T) == 4><<<grid, a.x_threads, a.x5_smem, s>>>(a);
+    else k_inv_x<T, 3, GRP, false><<<grid, a.x_threads, a.x5_smem, s>>>(a);
+  } else if constexpr (!GRP) {
+    if (staged) k_inv_x<T, 2, GRP, sizeof(T) == 4><<<grid, a.x_threads, a.x5_smem, s>>>(a);
+    else k_inv_x<T, 2, GRP, false><<<grid, a.x_threads, a.x5_smem, s>>>(a);
+  }
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
@@ -1797,8 +1860,12 @@ cudaError_t set_attrs_x_t(size_t smax) {
       FFTLS_ATTR((k_fwd_x<T, 2, false, 4, GRP>));
     }
   }
-  FFTLS_ATTR((k_inv_x<T, 3, GRP>));
-  if constexpr (!GRP) FFTLS_ATTR((k_inv_x<T, 2, GRP>));
+  FFTLS_ATTR((k_inv_x<T, 3, GRP, false>));
+  if constexpr (!GRP) FFTLS_ATTR((k_inv_x<T, 2, GRP, false>));
+  if constexpr (sizeof(T) == 4) {
+    FFTLS_ATTR((k_inv_x<T, 3, GRP, true>));
+    if constexpr (!GRP) FFTLS_ATTR((k_inv_x<T, 2, GRP, true>));
+  }
   return e;
 }
 #ifdef FFTLS_GROUPED_TU

@@ -183,6 +183,7 @@ void axis_tables(int L, int layout, int green, const int* perm, double* tw, doub
 // reductions changes.
 struct TilePlan {
   int x1_lines, x5_lines, y_w, z_w, e_planes, x1_vb;
+  int x5_vb = 1;  // inverse x1 pass: 1 register loads of eps, 0 staged by bulk copies (FP32)
   int y_thr, z_thr;  // threads per block of the strided passes (0: by tile size)
   int tuned;  // 1: chosen by timing candidates on the device
 };
@@ -472,7 +473,13 @@ bool apply_plan(const Setup& S, IterArgs<T>& a, bool real_eta, const TilePlan& P
     a.x1_smem = fwd_x_stage_offset(a.x1_smem) + fwd_x_stage_bytes(G1, g.n1, S.nc);
     if (a.x1_smem > G.lim) return false;
   }
+  a.x5_vb = P.x5_vb == 0 ? 0 : 1;
   a.x5_smem = G.twx + G5 * G.line5;
+  if (a.x5_vb == 0) {
+    if (sizeof(T) != 4 || g.n1 % 16 != 0) return false;
+    a.x5_smem = fwd_x_stage_offset(a.x5_smem) + fwd_x_stage_bytes(G5, g.n1, S.nc);
+    if (a.x5_smem > G.lim) return false;
+  }
   a.x_threads = 256;
   a.x1_blocks = (int)std::min<long long>((G.nlines + G1 - 1) / G1, (long long)S.num_sms * 8);
   a.x5_blocks = (int)std::min<long long>((G.nlines + G5 - 1) / G5, (long long)S.num_sms * 8);
@@ -786,7 +793,31 @@ fftls_status tune_plan(fftls_ctx* c, const Setup& S, IterArgs<T>& a, bool real_e
   search_wt(&TilePlan::z_w, &TilePlan::z_thr,
             [](const IterArgs<T>& x, cudaStream_t st) { return launch_fourier_z<T>(x, st); });
   a.eps = (T*)c->specB.p;  // scratch target of the inverse pass's update
-  search(&TilePlan::x5_lines, {1, 2, 4, 8}, [](const IterArgs<T>& x, cudaStream_t st) { return launch_inv_x<T>(x, st); });
+  // inverse x1 pass: lines per batch and (FP32) eps loaded by the threads or staged by bulk copies, jointly
+  {
+    float best = INFINITY;
+    int bl = P.x5_lines, bv = P.x5_vb;
+    const std::vector<int> vbs = sizeof(T) == 8 ? std::vector<int>{1} : std::vector<int>{1, 0};
+    for (int lines : {1, 2, 4, 8})
+      for (int vb : vbs) {
+        if (err != cudaSuccess) break;
+        TilePlan Q = P;
+        Q.x5_lines = lines;
+        Q.x5_vb = vb;
+        if (!apply_plan<T>(S, a, real_eta, Q)) continue;
+        float ms = 0.f;
+        err = timed([](const IterArgs<T>& x, cudaStream_t st) { return launch_inv_x<T>(x, st); }, &ms);
+        c->launches += 1 + kReps;
+        if (ms < best) {
+          best = ms;
+          bl = lines;
+          bv = vb;
+        }
+      }
+    P.x5_lines = bl;
+    P.x5_vb = bv;
+    apply_plan<T>(S, a, real_eta, P);
+  }
   a.eps = keep.eps;
   if (real_eta)
     search(&TilePlan::e_planes, {4, 8, 16, 32, 64},
@@ -902,7 +933,7 @@ fftls_status fftls_tile_plans(const fftls_ctx* c, int* rows, int* count) {
     const TilePlan& P = c->plans[i].second;
     const int row[FFTLS_PLAN_FIELDS] = {k.prec,     k.n1,  k.n2,  k.n3, k.green, P.x1_lines, P.x1_vb,
                                         P.x5_lines, P.y_w, P.z_w, k.real_eta ? P.e_planes : 0, P.tuned,
-                                        P.y_thr,    P.z_thr};
+                                        P.y_thr,    P.z_thr, P.x5_vb};
     memcpy(rows + (size_t)i * FFTLS_PLAN_FIELDS, row, sizeof(row));
   }
   *count = held;
@@ -924,13 +955,15 @@ fftls_status fftls_set_tile_plans(fftls_ctx* c, const int* rows, int count) {
     P.e_planes = r[10];
     P.y_thr = r[12];
     P.z_thr = r[13];
+    P.x5_vb = r[14];
     P.tuned = 1;  // imported schedules are used as they are, never re-tuned
     auto pow2_16 = [](int w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16; };
     auto thr_ok = [](int t, int w) { return t == 0 || t == fftls::strided_threads(w); };
     const bool ok = (prec == 0 || prec == 1) && n1 >= 1 && n2 >= 1 && n3 >= 1 && green >= kMS && green <= kRotated &&
                     P.x1_lines >= 1 && P.x1_lines <= 8 && P.x5_lines >= 1 && P.x5_lines <= 8 &&
                     (P.x1_vb == 1 || P.x1_vb == 2 || P.x1_vb == 4 || (P.x1_vb == 0 && prec == 0 && n1 % 16 == 0)) &&
-                    (prec == 0 || P.x1_vb == 1) && pow2_16(P.y_w) && pow2_16(P.z_w) && P.e_planes >= 0 &&
+                    (prec == 0 || P.x1_vb == 1) && (P.x5_vb == 1 || (P.x5_vb == 0 && prec == 0 && n1 % 16 == 0)) &&
+                    pow2_16(P.y_w) && pow2_16(P.z_w) && P.e_planes >= 0 &&
                     P.e_planes <= n3 && thr_ok(P.y_thr, P.y_w) && thr_ok(P.z_thr, P.z_w);
     if (!ok) return set_err(c, FFTLS_E_INVALID_ARG, "tile plan row %d is not a valid schedule", i);
     // a row names the grid, not the dimension: it serves the 3D problem on it and, with n3 = 1, the 2D one

@@ -408,7 +408,7 @@ class Solver:
         n = ctypes.c_int(0)
         self.lib.fftls_tile_plans(self.handle, None, ctypes.byref(n))
         keys = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x1_vb", "x5_lines", "y_w", "z_w", "e_planes",
-                "tuned", "y_threads", "z_threads")
+                "tuned", "y_threads", "z_threads", "x5_vb")
         w = len(keys)
         rows = (ctypes.c_int * (w * max(n.value, 1)))()
         self.lib.fftls_tile_plans(self.handle, rows, ctypes.byref(n))
@@ -417,12 +417,12 @@ class Solver:
     def set_tile_plans(self, plans: list) -> None:
         """Import schedules (dicts as returned by tile_plans) for later solves (see fftls_set_tile_plans)."""
         keys = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x1_vb", "x5_lines", "y_w", "z_w", "e_planes",
-                "tuned", "y_threads", "z_threads")
+                "tuned", "y_threads", "z_threads", "x5_vb")
         w = len(keys)
         rows = (ctypes.c_int * (w * max(len(plans), 1)))()
         for i, p in enumerate(plans):
             for j, k in enumerate(keys):
-                rows[w * i + j] = int(p.get(k, 0))
+                rows[w * i + j] = int(p.get(k, 1 if k == "x5_vb" else 0))
         st = self.lib.fftls_set_tile_plans(self.handle, rows, len(plans))
         if st:
             raise FftlsError(st, self.last_error())
