@@ -554,8 +554,21 @@ def run_batched(args, rank, local, world):
             _, t1 = timed(lambda: solver.solve(s0["phase"], s0["lam"], s0["mu"], s0["eps_bar"], precision="fp32",
                                                want_strain=False, want_stress=False, history=False,
                                                **dict(one, max_iter=105), raise_on_error=False))
+            # stragglers: the same samples as two groups split by contrast (similar iteration counts
+            # within each), one after the other
+            chi = [max(g["mu"]) / min(g["mu"]) for g in grp]
+            order = sorted(range(len(grp)), key=lambda i: chi[i])
+            t_split = 0.0
+            for half in (order[:len(order) // 2], order[len(order) // 2:]):
+                sub = [grp[i] for i in half]
+                solver.solve_batched(sub, precision="fp32_refine64", concurrency=1, **kw)
+                t_split += timed(lambda: solver.solve_batched(sub, precision="fp32_refine64", concurrency=1,
+                                                              **kw))[1]
+            its = [r.iterations for r in rg]
             per_length.append({"L": L, "samples": len(grp), "time_s": tg,
                                "voxel_iters_per_s": sum(L ** 3 * r.iterations for r in rg) / tg,
+                               "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
+                               "two_groups_by_contrast_s": t_split,
                                "single_fp32_ms_per_iteration": 1e3 * t1 / 105})
     its_b = np.array([r.iterations for r in res], dtype=np.float64)
     its_64 = np.array([r.iterations for r in r64], dtype=np.float64)

@@ -604,16 +604,30 @@ __device__ __forceinline__ void k_fwd_x_staged_body(const IterArgs<float>& a, co
 }
 
 // GRP: a grouped launch (fftls_solve_batched), every block working on its sample's view
+// Register budgets: the FP32 four-voxel loads (taken with eight-line batches, two blocks per SM by
+// shared memory) ask for one block per SM, which lets the compiler use 108 registers (its default
+// choice, 80, ran 0.7 % slower at 512^3); every other variant keeps the compiler's default (0).
 template <typename T, int DIM, bool DUAL, int VB, bool GRP>
-__global__ void __launch_bounds__(256, VB == 0 ? 4 : 1) k_fwd_x(const __grid_constant__ IterArgs<T> a_) {
+__global__ void __launch_bounds__(256, (VB == 4 && sizeof(T) == 4) ? 1 : 0) k_fwd_x(const __grid_constant__ IterArgs<T> a_) {
   if constexpr (GRP) {
     IterArgs<T> a = a_;
     at_sample(a, blockIdx.y);
-    if constexpr (VB == 0) k_fwd_x_staged_body<DIM, DUAL>(a, a_.pl);
-    else k_fwd_x_body<T, DIM, DUAL, VB>(a, a_.pl);
+    k_fwd_x_body<T, DIM, DUAL, VB>(a, a_.pl);
   } else {
-    if constexpr (VB == 0) k_fwd_x_staged_body<DIM, DUAL>(a_, a_.pl);
-    else k_fwd_x_body<T, DIM, DUAL, VB>(a_, a_.pl);
+    k_fwd_x_body<T, DIM, DUAL, VB>(a_, a_.pl);
+  }
+}
+
+// The staged variant (x1_vb == 0, FP32) as a kernel of its own: held to 64 registers (four blocks
+// per SM), while the register-loading kernels keep the compiler's own allocation.
+template <int DIM, bool DUAL, bool GRP>
+__global__ void __launch_bounds__(256, 4) k_fwd_x_staged(const __grid_constant__ IterArgs<float> a_) {
+  if constexpr (GRP) {
+    IterArgs<float> a = a_;
+    at_sample(a, blockIdx.y);
+    k_fwd_x_staged_body<DIM, DUAL>(a, a_.pl);
+  } else {
+    k_fwd_x_staged_body<DIM, DUAL>(a_, a_.pl);
   }
 }
 
@@ -1658,10 +1672,11 @@ template <typename T, bool GRP>
 cudaError_t launch_fwd_x_t(const IterArgs<T>& a, cudaStream_t s) {
   const dim3 grid(a.x1_blocks, GRP ? a.nsmp : 1);
 #define FFTLS_FWD(D, U, V) k_fwd_x<T, D, U, V, GRP><<<grid, a.x_threads, a.x1_smem, s>>>(a)
+#define FFTLS_FWD_ST(D, U) k_fwd_x_staged<D, U, GRP><<<grid, a.x_threads, a.x1_smem, s>>>(a)
 // FP64 forward passes (the few certification passes of the ladder) load one voxel at a time
 #define FFTLS_FWD_VB(D, U)                                                                              \
   if constexpr (sizeof(T) == 8) FFTLS_FWD(D, U, 1);                                                     \
-  else if (a.x1_vb == 0 && fwd_x_staged_ok(a)) FFTLS_FWD(D, U, 0);                                      \
+  else if (a.x1_vb == 0 && fwd_x_staged_ok(a)) FFTLS_FWD_ST(D, U);                                      \
   else if (a.x1_vb >= 4 || a.x1_vb == 0) FFTLS_FWD(D, U, 4);                                            \
   else if (a.x1_vb == 2) FFTLS_FWD(D, U, 2);                                                            \
   else FFTLS_FWD(D, U, 1)
@@ -1675,6 +1690,7 @@ cudaError_t launch_fwd_x_t(const IterArgs<T>& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
   }
 #undef FFTLS_FWD_VB
+#undef FFTLS_FWD_ST
 #undef FFTLS_FWD
   return cudaGetLastError();
 }
@@ -1843,11 +1859,11 @@ cudaError_t set_attrs_x_t(size_t smax) {
     FFTLS_ATTR((k_fwd_x<T, 2, false, 1, GRP>));
   }
   if constexpr (sizeof(T) == 4) {
-    FFTLS_ATTR((k_fwd_x<T, 3, true, 0, GRP>));
-    FFTLS_ATTR((k_fwd_x<T, 3, false, 0, GRP>));
+    FFTLS_ATTR((k_fwd_x_staged<3, true, GRP>));
+    FFTLS_ATTR((k_fwd_x_staged<3, false, GRP>));
     if constexpr (!GRP) {
-      FFTLS_ATTR((k_fwd_x<T, 2, true, 0, GRP>));
-      FFTLS_ATTR((k_fwd_x<T, 2, false, 0, GRP>));
+      FFTLS_ATTR((k_fwd_x_staged<2, true, GRP>));
+      FFTLS_ATTR((k_fwd_x_staged<2, false, GRP>));
     }
     FFTLS_ATTR((k_fwd_x<T, 3, true, 2, GRP>));
     FFTLS_ATTR((k_fwd_x<T, 3, true, 4, GRP>));
