@@ -33,6 +33,11 @@ STOP = {"eta": 0, "maxdelta": 1}
 OK, E_INVALID_ARG, E_UNSUPPORTED_SIZE, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED = range(7)
 
 
+# Fields of one tile-schedule row (fftls_tile_plans / fftls_set_tile_plans), FFTLS_PLAN_FIELDS of them.
+PLAN_KEYS = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x1_vb", "x5_lines", "y_w", "z_w", "e_planes",
+             "tuned", "y_threads", "z_threads", "x5_vb")
+
+
 class FftlsError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{status_name(status)}: {message}")
@@ -407,8 +412,7 @@ class Solver:
         """Tile schedules held by this context (see fftls_tile_plans), one dict per grid and precision."""
         n = ctypes.c_int(0)
         self.lib.fftls_tile_plans(self.handle, None, ctypes.byref(n))
-        keys = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x1_vb", "x5_lines", "y_w", "z_w", "e_planes",
-                "tuned", "y_threads", "z_threads", "x5_vb")
+        keys = PLAN_KEYS
         w = len(keys)
         rows = (ctypes.c_int * (w * max(n.value, 1)))()
         self.lib.fftls_tile_plans(self.handle, rows, ctypes.byref(n))
@@ -416,8 +420,7 @@ class Solver:
 
     def set_tile_plans(self, plans: list) -> None:
         """Import schedules (dicts as returned by tile_plans) for later solves (see fftls_set_tile_plans)."""
-        keys = ("precision", "n1", "n2", "n3", "green", "x1_lines", "x1_vb", "x5_lines", "y_w", "z_w", "e_planes",
-                "tuned", "y_threads", "z_threads", "x5_vb")
+        keys = PLAN_KEYS
         w = len(keys)
         rows = (ctypes.c_int * (w * max(len(plans), 1)))()
         for i, p in enumerate(plans):

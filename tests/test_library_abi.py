@@ -69,3 +69,14 @@ def test_host_only_calls(lib):
     with pytest.raises(fftls.FftlsError):
         fftls.reference_medium([0.6, 0.0], [0.6, 0.0], 3, "AS")   # porous: default degenerates
     assert lib.fftls_status_string(5) == b"FFTLS_E_NOT_CONVERGED"
+
+
+def test_plan_rows_match_header(lib):
+    """The binding's tile-schedule row has the header's FFTLS_PLAN_FIELDS fields, and the plan calls
+    refuse a missing context on the host."""
+    from paper_1412_8398_gb300 import fftls
+    text = open(os.path.join(ROOT, "include", "fftls.h")).read()
+    assert len(fftls.PLAN_KEYS) == int(re.search(r"#define FFTLS_PLAN_FIELDS (\d+)", text).group(1))
+    n = ctypes.c_int(0)
+    assert lib.fftls_tile_plans(None, None, ctypes.byref(n)) == 1  # FFTLS_E_INVALID_ARG
+    assert lib.fftls_set_tile_plans(None, None, 0) == 1
