@@ -55,7 +55,9 @@ typedef enum {
   FFTLS_E_OOM = 3,              /* device allocation failed */
   FFTLS_E_CUDA = 4,             /* a CUDA runtime call failed (message in fftls_last_error) */
   FFTLS_E_NOT_CONVERGED = 5,    /* max_iter reached; outputs hold the last iterate */
-  FFTLS_E_DIVERGED = 6          /* eta non-finite or > 1e4 eta_0; outputs hold the last iterate */
+  FFTLS_E_DIVERGED = 6,         /* eta non-finite or > 1e4 eta_0; outputs hold the last iterate */
+  FFTLS_E_TIMEOUT = 7           /* a bounded device wait ran out (a shared-memory tile copy that did not
+                                   complete): the kernels stopped the solve; the context stays usable */
 } fftls_status;
 
 enum { FFTLS_GREEN_MS = 0, FFTLS_GREEN_C = 1, FFTLS_GREEN_W = 2, FFTLS_GREEN_R = 3 };
@@ -134,7 +136,8 @@ void fftls_destroy(fftls_ctx* ctx);
 
 /* Solve one load case (Sec. 3, eq. ds / eq. as with the chosen operator of Sec. 4).
  * Returns FFTLS_OK, FFTLS_E_NOT_CONVERGED or FFTLS_E_DIVERGED with the outputs
- * filled, or an error status with the outputs untouched. */
+ * filled, or an error status with the outputs untouched (FFTLS_E_TIMEOUT when a
+ * kernel's bounded wait for a tile copy ran out). */
 fftls_status fftls_solve(fftls_ctx* ctx, const fftls_problem* prob, const fftls_options* opt, fftls_result* res);
 
 /* Effective stiffness C~ from <sigma> = C~ eps_bar (Sec. 2), as a symmetric

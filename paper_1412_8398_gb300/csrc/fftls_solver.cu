@@ -580,7 +580,7 @@ struct Runner {
     CUDA_TRY(c, cudaStreamSynchronize(S.s));
     for (int i = 0; i < ns; ++i)
       if (hctl[i].fault)
-        return set_err(c, FFTLS_E_CUDA, "%s",
+        return set_err(c, FFTLS_E_TIMEOUT, "%s",
                        "a shared-memory tile copy did not complete within its wait limit; the solve was stopped");
     return FFTLS_OK;
   }
@@ -1058,6 +1058,7 @@ const char* fftls_status_string(fftls_status s) {
     case FFTLS_E_CUDA: return "FFTLS_E_CUDA";
     case FFTLS_E_NOT_CONVERGED: return "FFTLS_E_NOT_CONVERGED";
     case FFTLS_E_DIVERGED: return "FFTLS_E_DIVERGED";
+    case FFTLS_E_TIMEOUT: return "FFTLS_E_TIMEOUT";
   }
   return "unknown";
 }
@@ -1842,7 +1843,7 @@ extern "C" fftls_status fftls_solve_noalloc(const fftls_problem* p, const fftls_
   for (;;) {
     NA_TRY(cudaMemcpyAsync(&ctl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, S.s));
     NA_TRY(cudaStreamSynchronize(S.s));
-    if (ctl.fault) return FFTLS_E_CUDA;  // a tile copy did not complete within its wait limit
+    if (ctl.fault) return FFTLS_E_TIMEOUT;  // a tile copy did not complete within its wait limit
     if (ctl.state != kRunning) break;
     for (int i = 0; i < chunk; ++i) NA_TRY(iteration(dual, upd));
   }

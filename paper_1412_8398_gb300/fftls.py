@@ -30,7 +30,7 @@ SCHEME = {"DS": 0, "AS": 1}
 PRECISION = {"fp64": 0, "fp32_refine64": 1, "fp32": 2}
 STOP = {"eta": 0, "maxdelta": 1}
 
-OK, E_INVALID_ARG, E_UNSUPPORTED_SIZE, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED = range(7)
+OK, E_INVALID_ARG, E_UNSUPPORTED_SIZE, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED, E_TIMEOUT = range(8)
 
 
 # Fields of one tile-schedule row (fftls_tile_plans / fftls_set_tile_plans), FFTLS_PLAN_FIELDS of them.
@@ -153,7 +153,7 @@ def load_library(build_if_missing: bool = False):
 
 def status_name(s: int) -> str:
     names = ["FFTLS_OK", "FFTLS_E_INVALID_ARG", "FFTLS_E_UNSUPPORTED_SIZE", "FFTLS_E_OOM", "FFTLS_E_CUDA",
-             "FFTLS_E_NOT_CONVERGED", "FFTLS_E_DIVERGED"]
+             "FFTLS_E_NOT_CONVERGED", "FFTLS_E_DIVERGED", "FFTLS_E_TIMEOUT"]
     return names[s] if 0 <= s < len(names) else f"status {s}"
 
 

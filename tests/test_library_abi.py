@@ -69,6 +69,8 @@ def test_host_only_calls(lib):
     with pytest.raises(fftls.FftlsError):
         fftls.reference_medium([0.6, 0.0], [0.6, 0.0], 3, "AS")   # porous: default degenerates
     assert lib.fftls_status_string(5) == b"FFTLS_E_NOT_CONVERGED"
+    assert lib.fftls_status_string(7) == b"FFTLS_E_TIMEOUT" and fftls.status_name(7) == "FFTLS_E_TIMEOUT"
+    assert [fftls.status_name(i) == lib.fftls_status_string(i).decode() for i in range(8)] == [True] * 8
 
 
 def test_plan_rows_match_header(lib):
